@@ -1,0 +1,972 @@
+/*
+ * z4c_oracle.c -- plain, slow, FP64 CPU oracle for the Z4c hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may call, link or
+ * load this file; only the tests, the package's smoke check and the CPU
+ * baseline leg of the benchmark do.  It shares no code, header, table or
+ * helper with the CUDA path.  Build: gcc -O2 -ffp-contract=off -fopenmp
+ * (see oracle/oracle.py).  No fused multiply-adds, no reassociation: every
+ * sum is evaluated in the order written below.
+ *
+ * What it computes (paper: Zhu et al., "Performance-Portable Numerical
+ * Relativity with AthenaK"):
+ *   - Sec. 2: the vacuum Z4c system with Bona-Masso lapse and Gamma-driver
+ *     shift.  The paper defers the continuum equations to GR-Athena++
+ *     (Daszuta et al. 2021, Eqs. 8-13 and 22); the forms used here are the
+ *     standard Z4c equations written out in rhs_point() below.
+ *   - Sec. 3: Mesh of MeshBlocks with active + ghost regions; ghost zones
+ *     filled from neighbouring blocks' active cells at every RK stage;
+ *     cell-centred finite differences (Sec. 3.2).
+ *   - Sec. 4.3: Kreiss-Oliger dissipation, constraint damping kappa1/kappa2,
+ *     6th-order differencing and RK4.
+ *
+ * Readings taken where the paper is silent (each also listed in the design doc):
+ *   R1 equation forms: as in rhs_point(); Gamma-tilde damping term is
+ *      -2 alpha kappa1 (Gam - Gam_d); the K-gradient term in the Gam
+ *      equation is -(1/3) gt^ij d_j (2 Khat + Theta); the evolved Gam is used
+ *      only inside its derivative in the Ricci tensor, Gam_d elsewhere.
+ *   R2 RK4 is the classic four-stage method; every stage state (and the
+ *      final state) has the algebraic constraints enforced, then ghosts
+ *      filled before its right-hand side is evaluated.
+ *   R3 KO dissipation per direction: sigma (-1)^(N+1) / (2^(2N) h) times the
+ *      centred 2N-th undivided difference, N = 3 (4th order) or 4 (6th).
+ *   R4 mixed second derivatives are the tensor product of the centred first
+ *      derivative stencils.
+ *   R5 lopsided advection stencils for beta^k >= 0 lean towards +k; for
+ *      beta^k < 0 the mirror image.
+ *   R6 chi_g = max(chi, chi_floor) wherever 1/chi appears; chi itself is
+ *      never clipped.
+ *   R7 Sommerfeld outer boundary: every ghost cell whose centre lies outside
+ *      the domain evolves du/dt = -(x^k d_k u + u - u_inf)/r, v = 1,
+ *      u_inf = 1 for chi, alpha and the diagonal of gt, 0 otherwise, with
+ *      2nd-order one-sided differences along each axis in which the cell
+ *      index lies in the ghost range (pointing into the block), centred
+ *      2nd-order differences otherwise.  Ghost copies never overwrite such a
+ *      cell.
+ *   R8 shift == 0 freezes beta (d_t beta = 0); lapse == 0 is harmonic
+ *      slicing (mu_L = 1), lapse == 1 is 1+log (mu_L = 2/alpha).
+ *
+ * Field order (fixed): chi, gt_xx gt_xy gt_xz gt_yy gt_yz gt_zz, Khat,
+ * At_xx .. At_zz, Gam^x Gam^y Gam^z, Theta, alpha, beta^x beta^y beta^z.
+ *
+ * Storage: for each block (in order) and each field, an (n_z+2g) x (n_y+2g)
+ * x (n_x+2g) array, i fastest.  Blocks are concatenated.
+ *
+ * Parity status: every function below is pinned by tests in tests/ that
+ * check it against closed forms, exact polynomial results, analytic
+ * solutions and symmetries (see tests/test_oracle_*.py).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define NF 22
+enum {
+  F_CHI = 0, F_GXX, F_GXY, F_GXZ, F_GYY, F_GYZ, F_GZZ, F_KHAT,
+  F_AXX, F_AXY, F_AXZ, F_AYY, F_AYZ, F_AZZ, F_GAMX, F_GAMY, F_GAMZ,
+  F_THETA, F_ALPHA, F_BETAX, F_BETAY, F_BETAZ
+};
+
+/* symmetric 3x3 index -> component 0..5 (xx xy xz yy yz zz) */
+static const int SYM[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
+
+typedef struct {
+  int32_t nblocks;
+  int32_t ghosts;
+  int32_t order;     /* 4 or 6 */
+  int32_t periodic;  /* 1: periodic box; 0: Sommerfeld outer boundary */
+  int32_t lapse;     /* 0 harmonic, 1 one-plus-log */
+  int32_t shift;     /* 0 frozen, 1 Gamma-driver */
+  double dom_lo[3];
+  double dom_hi[3];
+  double ko_sigma;
+  double kappa1;
+  double kappa2;
+  double eta;
+  double chi_floor;
+  const int32_t *n;  /* [nblocks][3] interior cells per direction */
+  const double *lo;  /* [nblocks][3] lower corner of each active region */
+  const double *h;   /* [nblocks] grid spacing */
+} orc_mesh;
+
+/* ------------------------------------------------------------------ */
+/* storage geometry                                                    */
+/* ------------------------------------------------------------------ */
+
+static long ext(const orc_mesh *m, int b, int d) { return m->n[3 * b + d] + 2 * m->ghosts; }
+
+static long blk_cells(const orc_mesh *m, int b) { return ext(m, b, 0) * ext(m, b, 1) * ext(m, b, 2); }
+
+static long blk_offset(const orc_mesh *m, int b) {
+  long off = 0;
+  for (int q = 0; q < b; ++q) off += NF * blk_cells(m, q);
+  return off;
+}
+
+long orc_state_size(const orc_mesh *m) { return blk_offset(m, m->nblocks); }
+
+static void cell_centre(const orc_mesh *m, int b, int i, int j, int k, double x[3]) {
+  int idx[3] = {i, j, k};
+  for (int d = 0; d < 3; ++d) x[d] = m->lo[3 * b + d] + (idx[d] - m->ghosts + 0.5) * m->h[b];
+}
+
+static int is_interior(const orc_mesh *m, int b, int i, int j, int k) {
+  int g = m->ghosts;
+  return i >= g && i < m->n[3 * b] + g && j >= g && j < m->n[3 * b + 1] + g && k >= g &&
+         k < m->n[3 * b + 2] + g;
+}
+
+/* centre outside the physical domain (only meaningful for non-periodic meshes) */
+static int is_outside(const orc_mesh *m, const double x[3]) {
+  for (int d = 0; d < 3; ++d)
+    if (x[d] < m->dom_lo[d] || x[d] > m->dom_hi[d]) return 1;
+  return 0;
+}
+
+/* Sommerfeld cell: ghost cell with centre outside a non-periodic domain (R7) */
+static int is_sommerfeld(const orc_mesh *m, int b, int i, int j, int k) {
+  if (m->periodic) return 0;
+  if (is_interior(m, b, i, j, k)) return 0;
+  double x[3];
+  cell_centre(m, b, i, j, k, x);
+  return is_outside(m, x);
+}
+
+/* ------------------------------------------------------------------ */
+/* finite-difference stencils (Sec. 3; coefficients are the standard   */
+/* centred / one-sided Taylor stencils, R3-R5)                         */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+  const double *c;
+  int len;
+  int off; /* offset of c[0] relative to the centre */
+  double den;
+} stencil;
+
+static const double C_D1_4[5] = {1, -8, 0, 8, -1};
+static const double C_D1_6[7] = {-1, 9, -45, 0, 45, -9, 1};
+static const double C_D2_4[5] = {-1, 16, -30, 16, -1};
+static const double C_D2_6[7] = {2, -27, 270, -490, 270, -27, 2};
+static const double C_LP_4[5] = {-3, -10, 18, -6, 1};
+static const double C_LP_6[7] = {2, -24, -35, 80, -30, 8, -1};
+static const double C_KO_4[7] = {1, -6, 15, -20, 15, -6, 1};
+static const double C_KO_6[9] = {1, -8, 28, -56, 70, -56, 28, -8, 1};
+
+static stencil st_d1(int order) {
+  stencil s = order == 4 ? (stencil){C_D1_4, 5, -2, 12.0} : (stencil){C_D1_6, 7, -3, 60.0};
+  return s;
+}
+static stencil st_d2(int order) {
+  stencil s = order == 4 ? (stencil){C_D2_4, 5, -2, 12.0} : (stencil){C_D2_6, 7, -3, 180.0};
+  return s;
+}
+static stencil st_lop(int order) {
+  stencil s = order == 4 ? (stencil){C_LP_4, 5, -1, 12.0} : (stencil){C_LP_6, 7, -2, 60.0};
+  return s;
+}
+/* KO: den = 2^(2N); sign (-1)^(N+1) applied in ko() */
+static stencil st_ko(int order) {
+  stencil s = order == 4 ? (stencil){C_KO_4, 7, -3, 64.0} : (stencil){C_KO_6, 9, -4, 256.0};
+  return s;
+}
+
+static double apply(const double *p, long s, stencil st) {
+  double acc = 0.0;
+  for (int m = 0; m < st.len; ++m) acc += st.c[m] * p[(m + st.off) * s];
+  return acc;
+}
+
+static double d1(const double *p, long s, int order, double h) {
+  stencil st = st_d1(order);
+  return apply(p, s, st) / (st.den * h);
+}
+
+static double d2(const double *p, long s, int order, double h) {
+  stencil st = st_d2(order);
+  return apply(p, s, st) / (st.den * h * h);
+}
+
+static double dmix(const double *p, long sa, long sb, int order, double h) {
+  stencil st = st_d1(order);
+  double acc = 0.0;
+  for (int a = 0; a < st.len; ++a)
+    for (int b = 0; b < st.len; ++b)
+      acc += st.c[a] * st.c[b] * p[(a + st.off) * sa + (b + st.off) * sb];
+  return acc / (st.den * st.den * h * h);
+}
+
+/* lopsided first derivative; upwind side chosen by the sign of beta (R5) */
+static double dlop(const double *p, long s, int order, double h, double beta) {
+  stencil st = st_lop(order);
+  double acc = 0.0;
+  if (beta >= 0.0) {
+    acc = apply(p, s, st);
+  } else {
+    for (int m = 0; m < st.len; ++m) acc -= st.c[m] * p[-(m + st.off) * s];
+  }
+  return acc / (st.den * h);
+}
+
+static double ko(const double *p, long s, int order, double h, double sigma) {
+  stencil st = st_ko(order);
+  int N = order == 4 ? 3 : 4;
+  double sign = (N + 1) % 2 == 0 ? 1.0 : -1.0;
+  return sign * sigma / (st.den * h) * apply(p, s, st);
+}
+
+/* Test hook: one finite-difference operator on an (nz,ny,nx) array.
+ * kind 0: d/dx_dir1, 1: d2/dx_dir1^2, 2: d2/dx_dir1 dx_dir2,
+ * 3: lopsided d/dx_dir1 with upwind sign of `arg`, 4: KO along dir1 with
+ * sigma = `arg`. */
+double orc_fd(int kind, int order, const double *f, int nx, int ny, int nz, int i, int j, int k,
+              int dir1, int dir2, double h, double arg) {
+  long st[3] = {1, nx, (long)nx * ny};
+  const double *p = f + ((long)k * ny + j) * nx + i;
+  (void)nz;
+  switch (kind) {
+    case 0: return d1(p, st[dir1], order, h);
+    case 1: return d2(p, st[dir1], order, h);
+    case 2: return dmix(p, st[dir1], st[dir2], order, h);
+    case 3: return dlop(p, st[dir1], order, h, arg);
+    case 4: return ko(p, st[dir1], order, h, arg);
+    default: return NAN;
+  }
+}
+
+/* ------------------------------------------------------------------ */
+/* small linear algebra                                                */
+/* ------------------------------------------------------------------ */
+
+static double det3(const double g[3][3]) {
+  return g[0][0] * (g[1][1] * g[2][2] - g[1][2] * g[2][1]) -
+         g[0][1] * (g[1][0] * g[2][2] - g[1][2] * g[2][0]) +
+         g[0][2] * (g[1][0] * g[2][1] - g[1][1] * g[2][0]);
+}
+
+/* inverse via adjugate / determinant */
+static void inv3(const double g[3][3], double gi[3][3]) {
+  double det = det3(g);
+  gi[0][0] = (g[1][1] * g[2][2] - g[1][2] * g[2][1]) / det;
+  gi[0][1] = (g[0][2] * g[2][1] - g[0][1] * g[2][2]) / det;
+  gi[0][2] = (g[0][1] * g[1][2] - g[0][2] * g[1][1]) / det;
+  gi[1][0] = (g[1][2] * g[2][0] - g[1][0] * g[2][2]) / det;
+  gi[1][1] = (g[0][0] * g[2][2] - g[0][2] * g[2][0]) / det;
+  gi[1][2] = (g[0][2] * g[1][0] - g[0][0] * g[1][2]) / det;
+  gi[2][0] = (g[1][0] * g[2][1] - g[1][1] * g[2][0]) / det;
+  gi[2][1] = (g[0][1] * g[2][0] - g[0][0] * g[2][1]) / det;
+  gi[2][2] = (g[0][0] * g[1][1] - g[0][1] * g[1][0]) / det;
+}
+
+/* ------------------------------------------------------------------ */
+/* Z4c right-hand side at one interior cell (Sec. 2, R1, R6, R8)       */
+/* ------------------------------------------------------------------ */
+
+typedef struct {
+  /* values */
+  double chi, Khat, Theta, alpha;
+  double g[3][3], A[3][3], Gam[3], beta[3];
+  /* derivatives: d?[k] = d_k ?, dd?[k][l] = d_k d_l ? */
+  double dchi[3], dKhat[3], dTheta[3], dalpha[3];
+  double dg[3][3][3];    /* dg[k][i][j] = d_k gt_ij */
+  double dA[3][3][3];    /* dA[k][i][j] = d_k At_ij (constraints only) */
+  double dbeta[3][3];    /* dbeta[k][i] = d_k beta^i */
+  double dGam[3][3];     /* dGam[k][i] = d_k Gam^i */
+  double ddchi[3][3], ddalpha[3][3];
+  double ddg[3][3][3][3];  /* ddg[k][l][i][j] */
+  double ddbeta[3][3][3];  /* ddbeta[k][l][i] */
+} point_data;
+
+static void gather_point(const orc_mesh *m, const double *c, long S, const long st[3], double h,
+                         point_data *P, int need_dA) {
+  int o = m->order;
+  P->chi = c[F_CHI * S];
+  P->Khat = c[F_KHAT * S];
+  P->Theta = c[F_THETA * S];
+  P->alpha = c[F_ALPHA * S];
+  for (int i = 0; i < 3; ++i) {
+    P->Gam[i] = c[(F_GAMX + i) * S];
+    P->beta[i] = c[(F_BETAX + i) * S];
+    for (int j = 0; j < 3; ++j) {
+      P->g[i][j] = c[(F_GXX + SYM[i][j]) * S];
+      P->A[i][j] = c[(F_AXX + SYM[i][j]) * S];
+    }
+  }
+  for (int k = 0; k < 3; ++k) {
+    P->dchi[k] = d1(c + F_CHI * S, st[k], o, h);
+    P->dKhat[k] = d1(c + F_KHAT * S, st[k], o, h);
+    P->dTheta[k] = d1(c + F_THETA * S, st[k], o, h);
+    P->dalpha[k] = d1(c + F_ALPHA * S, st[k], o, h);
+    for (int i = 0; i < 3; ++i) {
+      P->dbeta[k][i] = d1(c + (F_BETAX + i) * S, st[k], o, h);
+      P->dGam[k][i] = d1(c + (F_GAMX + i) * S, st[k], o, h);
+      for (int j = 0; j < 3; ++j) {
+        P->dg[k][i][j] = d1(c + (F_GXX + SYM[i][j]) * S, st[k], o, h);
+        P->dA[k][i][j] = need_dA ? d1(c + (F_AXX + SYM[i][j]) * S, st[k], o, h) : 0.0;
+      }
+    }
+    for (int l = 0; l < 3; ++l) {
+      if (k == l) {
+        P->ddchi[k][l] = d2(c + F_CHI * S, st[k], o, h);
+        P->ddalpha[k][l] = d2(c + F_ALPHA * S, st[k], o, h);
+      } else {
+        P->ddchi[k][l] = dmix(c + F_CHI * S, st[k], st[l], o, h);
+        P->ddalpha[k][l] = dmix(c + F_ALPHA * S, st[k], st[l], o, h);
+      }
+      for (int i = 0; i < 3; ++i) {
+        const double *pb = c + (F_BETAX + i) * S;
+        P->ddbeta[k][l][i] = k == l ? d2(pb, st[k], o, h) : dmix(pb, st[k], st[l], o, h);
+        for (int j = 0; j < 3; ++j) {
+          const double *pg = c + (F_GXX + SYM[i][j]) * S;
+          P->ddg[k][l][i][j] = k == l ? d2(pg, st[k], o, h) : dmix(pg, st[k], st[l], o, h);
+        }
+      }
+    }
+  }
+}
+
+/* Geometry shared by the right-hand side and the constraints. */
+typedef struct {
+  double gi[3][3];        /* gt^ij */
+  double Gl[3][3][3];     /* Gt_ijk = 1/2 (d_j g_ik + d_k g_ij - d_i g_jk) */
+  double Gu[3][3][3];     /* Gt^i_jk */
+  double Gd[3];           /* Gt_d^i = gt^jk Gt^i_jk */
+  double R[3][3];         /* R_ij = Rt_ij + Rchi_ij */
+  double Rs;              /* R = chi gt^ij R_ij */
+  double Au[3][3];        /* At^ij */
+  double AA;              /* At_ij At^ij */
+  double K;               /* Khat + 2 Theta */
+  double chig;            /* max(chi, chi_floor) */
+} geometry;
+
+static void compute_geometry(const orc_mesh *m, const point_data *P, geometry *G) {
+  inv3(P->g, G->gi);
+  G->chig = P->chi > m->chi_floor ? P->chi : m->chi_floor;
+  G->K = P->Khat + 2.0 * P->Theta;
+
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      for (int k = 0; k < 3; ++k)
+        G->Gl[i][j][k] = 0.5 * (P->dg[j][i][k] + P->dg[k][i][j] - P->dg[i][j][k]);
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      for (int k = 0; k < 3; ++k) {
+        double s = 0.0;
+        for (int l = 0; l < 3; ++l) s += G->gi[i][l] * G->Gl[l][j][k];
+        G->Gu[i][j][k] = s;
+      }
+  for (int i = 0; i < 3; ++i) {
+    double s = 0.0;
+    for (int j = 0; j < 3; ++j)
+      for (int k = 0; k < 3; ++k) s += G->gi[j][k] * G->Gu[i][j][k];
+    G->Gd[i] = s;
+  }
+
+  /* conformal Ricci tensor Rt_ij */
+  double Rt[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double s = 0.0;
+      for (int l = 0; l < 3; ++l)
+        for (int mm = 0; mm < 3; ++mm) s += -0.5 * G->gi[l][mm] * P->ddg[l][mm][i][j];
+      for (int k = 0; k < 3; ++k)
+        s += 0.5 * (P->g[k][i] * P->dGam[j][k] + P->g[k][j] * P->dGam[i][k]);
+      for (int k = 0; k < 3; ++k) s += G->Gd[k] * 0.5 * (G->Gl[i][j][k] + G->Gl[j][i][k]);
+      for (int l = 0; l < 3; ++l)
+        for (int mm = 0; mm < 3; ++mm)
+          for (int k = 0; k < 3; ++k)
+            s += G->gi[l][mm] * (G->Gu[k][l][i] * G->Gl[j][k][mm] + G->Gu[k][l][j] * G->Gl[i][k][mm] +
+                                 G->Gu[k][i][mm] * G->Gl[k][l][j]);
+      Rt[i][j] = s;
+    }
+
+  /* conformal-factor part Rchi_ij */
+  double ichi = 1.0 / G->chig;
+  double DDchi[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double s = P->ddchi[i][j];
+      for (int k = 0; k < 3; ++k) s -= G->Gu[k][i][j] * P->dchi[k];
+      DDchi[i][j] = s;
+    }
+  double trDDchi = 0.0, dchi2 = 0.0;
+  for (int l = 0; l < 3; ++l)
+    for (int mm = 0; mm < 3; ++mm) {
+      trDDchi += G->gi[l][mm] * DDchi[l][mm];
+      dchi2 += G->gi[l][mm] * P->dchi[l] * P->dchi[mm];
+    }
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double Rchi = 0.5 * ichi * DDchi[i][j] + 0.5 * ichi * P->g[i][j] * trDDchi -
+                    0.25 * ichi * ichi * (P->dchi[i] * P->dchi[j] + 3.0 * P->g[i][j] * dchi2);
+      G->R[i][j] = Rt[i][j] + Rchi;
+    }
+  double s = 0.0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) s += G->gi[i][j] * G->R[i][j];
+  G->Rs = P->chi * s;
+
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double a = 0.0;
+      for (int k = 0; k < 3; ++k)
+        for (int l = 0; l < 3; ++l) a += G->gi[i][k] * G->gi[j][l] * P->A[k][l];
+      G->Au[i][j] = a;
+    }
+  double aa = 0.0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) aa += P->A[i][j] * G->Au[i][j];
+  G->AA = aa;
+}
+
+static void rhs_point(const orc_mesh *m, const double *c, long S, const long st[3], double h,
+                      double out[NF]) {
+  point_data P;
+  geometry G;
+  gather_point(m, c, S, st, h, &P, 0);
+  compute_geometry(m, &P, &G);
+  const double al = P.alpha, chi = P.chi, K = G.K;
+  const double k1 = m->kappa1, k2 = m->kappa2;
+  const double ichi = 1.0 / G.chig;
+
+  double divb = P.dbeta[0][0] + P.dbeta[1][1] + P.dbeta[2][2];
+
+  /* physical second covariant derivative of the lapse and its trace */
+  double DDa[3][3];
+  double trgi_dchi_dal = 0.0;
+  for (int k = 0; k < 3; ++k)
+    for (int l = 0; l < 3; ++l) trgi_dchi_dal += G.gi[k][l] * P.dchi[k] * P.dalpha[l];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double s = P.ddalpha[i][j];
+      for (int k = 0; k < 3; ++k) s -= G.Gu[k][i][j] * P.dalpha[k];
+      s += 0.5 * ichi * (P.dchi[i] * P.dalpha[j] + P.dchi[j] * P.dalpha[i] - P.g[i][j] * trgi_dchi_dal);
+      DDa[i][j] = s;
+    }
+  double lapl_a = 0.0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double s = P.ddalpha[i][j];
+      for (int k = 0; k < 3; ++k) s -= G.Gu[k][i][j] * P.dalpha[k];
+      lapl_a += chi * G.gi[i][j] * s;
+    }
+  lapl_a -= 0.5 * trgi_dchi_dal;
+
+  /* chi */
+  out[F_CHI] = 2.0 / 3.0 * chi * (al * K - divb);
+
+  /* conformal metric */
+  for (int i = 0; i < 3; ++i)
+    for (int j = i; j < 3; ++j) {
+      double s = -2.0 * al * P.A[i][j];
+      for (int k = 0; k < 3; ++k) s += P.g[i][k] * P.dbeta[j][k] + P.g[j][k] * P.dbeta[i][k];
+      s -= 2.0 / 3.0 * P.g[i][j] * divb;
+      out[F_GXX + SYM[i][j]] = s;
+    }
+
+  /* Khat */
+  out[F_KHAT] = -lapl_a + al * (G.AA + K * K / 3.0) + k1 * (1.0 - k2) * al * P.Theta;
+
+  /* trace-free At */
+  double X[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) X[i][j] = -DDa[i][j] + al * G.R[i][j];
+  double trX = 0.0;
+  for (int k = 0; k < 3; ++k)
+    for (int l = 0; l < 3; ++l) trX += G.gi[k][l] * X[k][l];
+  for (int i = 0; i < 3; ++i)
+    for (int j = i; j < 3; ++j) {
+      double s = 0.0;
+      for (int k = 0; k < 3; ++k) s += P.A[i][k] * P.dbeta[j][k] + P.A[j][k] * P.dbeta[i][k];
+      s -= 2.0 / 3.0 * P.A[i][j] * divb;
+      s += chi * (X[i][j] - P.g[i][j] * trX / 3.0);
+      double AikAkj = 0.0;
+      for (int k = 0; k < 3; ++k)
+        for (int l = 0; l < 3; ++l) AikAkj += P.A[i][k] * G.gi[k][l] * P.A[l][j];
+      s += al * (K * P.A[i][j] - 2.0 * AikAkj);
+      out[F_AXX + SYM[i][j]] = s;
+    }
+
+  /* Theta */
+  out[F_THETA] = 0.5 * al * (G.Rs - G.AA + 2.0 / 3.0 * K * K) - al * k1 * (2.0 + k2) * P.Theta;
+
+  /* conformal connection functions */
+  for (int i = 0; i < 3; ++i) {
+    double s = 0.0;
+    for (int k = 0; k < 3; ++k) s -= G.Gd[k] * P.dbeta[k][i];
+    s += 2.0 / 3.0 * G.Gd[i] * divb;
+    for (int j = 0; j < 3; ++j)
+      for (int k = 0; k < 3; ++k) s += G.gi[j][k] * P.ddbeta[j][k][i];
+    for (int j = 0; j < 3; ++j)
+      for (int k = 0; k < 3; ++k) s += G.gi[i][j] * P.ddbeta[j][k][k] / 3.0;
+    for (int j = 0; j < 3; ++j) s -= 2.0 * G.Au[i][j] * P.dalpha[j];
+    double t = 0.0;
+    for (int j = 0; j < 3; ++j)
+      for (int k = 0; k < 3; ++k) t += G.Gu[i][j][k] * G.Au[j][k];
+    for (int j = 0; j < 3; ++j) t -= 1.5 * ichi * G.Au[i][j] * P.dchi[j];
+    for (int j = 0; j < 3; ++j) t -= G.gi[i][j] * (2.0 * P.dKhat[j] + P.dTheta[j]) / 3.0;
+    s += 2.0 * al * t;
+    s -= 2.0 * al * k1 * (P.Gam[i] - G.Gd[i]);
+    out[F_GAMX + i] = s;
+  }
+
+  /* lapse (Bona-Masso) */
+  if (m->lapse == 1)
+    out[F_ALPHA] = -2.0 * al * P.Khat;
+  else
+    out[F_ALPHA] = -al * al * P.Khat;
+
+  /* shift (Gamma-driver, integrated form) */
+  for (int i = 0; i < 3; ++i) out[F_BETAX + i] = m->shift ? P.Gam[i] - m->eta * P.beta[i] : 0.0;
+
+  /* advection along the shift (lopsided) and Kreiss-Oliger dissipation */
+  int o = m->order;
+  for (int f = 0; f < NF; ++f) {
+    if (!m->shift && f >= F_BETAX) continue;
+    const double *p = c + f * S;
+    double adv = 0.0, diss = 0.0;
+    for (int k = 0; k < 3; ++k) {
+      adv += P.beta[k] * dlop(p, st[k], o, h, P.beta[k]);
+      diss += ko(p, st[k], o, h, m->ko_sigma);
+    }
+    out[f] += adv + diss;
+  }
+}
+
+/* Sommerfeld cell right-hand side (R7) */
+static const double U_INF[NF] = {1, 1, 0, 0, 1, 0, 1, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 0, 1, 0, 0, 0};
+
+static void sommerfeld_point(const orc_mesh *m, int b, const double *c, long S, const long st[3],
+                             const int idx[3], double h, const double x[3], double out[NF]) {
+  int g = m->ghosts;
+  double r = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+  for (int f = 0; f < NF; ++f) {
+    const double *p = c + f * S;
+    double xdu = 0.0;
+    for (int d = 0; d < 3; ++d) {
+      long s = st[d];
+      double du;
+      if (idx[d] < g)
+        du = (-3.0 * p[0] + 4.0 * p[s] - p[2 * s]) / (2.0 * h);
+      else if (idx[d] >= m->n[3 * b + d] + g)
+        du = (3.0 * p[0] - 4.0 * p[-s] + p[-2 * s]) / (2.0 * h);
+      else
+        du = (p[s] - p[-s]) / (2.0 * h);
+      xdu += x[d] * du;
+    }
+    out[f] = -(xdu + p[0] - U_INF[f]) / r;
+  }
+}
+
+/* Right-hand side of every evolved cell (interior + Sommerfeld) of every
+ * block; other ghost cells get 0.  `u` must have its ghosts filled. */
+void orc_rhs(const orc_mesh *m, const double *u, double *out) {
+  long total = orc_state_size(m);
+  memset(out, 0, sizeof(double) * total);
+  for (int b = 0; b < m->nblocks; ++b) {
+    long e0 = ext(m, b, 0), e1 = ext(m, b, 1), e2 = ext(m, b, 2);
+    long S = e0 * e1 * e2;
+    long st[3] = {1, e0, e0 * e1};
+    const double *base = u + blk_offset(m, b);
+    double *obase = out + blk_offset(m, b);
+    double h = m->h[b];
+#pragma omp parallel for schedule(dynamic, 1)
+    for (long k = 0; k < e2; ++k) {
+      double r[NF];
+      for (long j = 0; j < e1; ++j)
+        for (long i = 0; i < e0; ++i) {
+          long cidx = (k * e1 + j) * e0 + i;
+          if (is_interior(m, b, (int)i, (int)j, (int)k)) {
+            rhs_point(m, base + cidx, S, st, h, r);
+          } else if (is_sommerfeld(m, b, (int)i, (int)j, (int)k)) {
+            double x[3];
+            int idx[3] = {(int)i, (int)j, (int)k};
+            cell_centre(m, b, (int)i, (int)j, (int)k, x);
+            sommerfeld_point(m, b, base + cidx, S, st, idx, h, x, r);
+          } else {
+            continue;
+          }
+          for (int f = 0; f < NF; ++f) obase[f * S + cidx] = r[f];
+        }
+    }
+  }
+}
+
+/* Right-hand side at a list of cells, cells[q] = (block, i, j, k) in storage
+ * indices; out[q*NF + f].  Cells that are neither interior nor Sommerfeld
+ * get 0. */
+void orc_rhs_cells(const orc_mesh *m, const double *u, const int32_t *cells, long ncells, double *out) {
+#pragma omp parallel for schedule(dynamic, 16)
+  for (long q = 0; q < ncells; ++q) {
+    int b = cells[4 * q], i = cells[4 * q + 1], j = cells[4 * q + 2], k = cells[4 * q + 3];
+    long e0 = ext(m, b, 0), e1 = ext(m, b, 1), e2 = ext(m, b, 2);
+    long S = e0 * e1 * e2;
+    long st[3] = {1, e0, e0 * e1};
+    long cidx = ((long)k * e1 + j) * e0 + i;
+    const double *c = u + blk_offset(m, b) + cidx;
+    double r[NF];
+    if (is_interior(m, b, i, j, k)) {
+      rhs_point(m, c, S, st, m->h[b], r);
+    } else if (is_sommerfeld(m, b, i, j, k)) {
+      double x[3];
+      int idx[3] = {i, j, k};
+      cell_centre(m, b, i, j, k, x);
+      sommerfeld_point(m, b, c, S, st, idx, m->h[b], x, r);
+    } else {
+      for (int f = 0; f < NF; ++f) r[f] = 0.0;
+    }
+    for (int f = 0; f < NF; ++f) out[q * NF + f] = r[f];
+  }
+}
+
+/* ------------------------------------------------------------------ */
+/* ghost fill: same-level copies and periodic wrap (Sec. 3)            */
+/* ------------------------------------------------------------------ */
+
+/* owning block and storage index of the cell whose centre is x, or -1 */
+static int find_owner(const orc_mesh *m, const double x[3], int idx[3]) {
+  for (int b = 0; b < m->nblocks; ++b) {
+    int inside = 1;
+    int q[3];
+    for (int d = 0; d < 3; ++d) {
+      double t = (x[d] - m->lo[3 * b + d]) / m->h[b];
+      int c = (int)floor(t);
+      if (c < 0 || c >= m->n[3 * b + d]) {
+        inside = 0;
+        break;
+      }
+      q[d] = c + m->ghosts;
+    }
+    if (inside) {
+      for (int d = 0; d < 3; ++d) idx[d] = q[d];
+      return b;
+    }
+  }
+  return -1;
+}
+
+void orc_fill_ghosts(const orc_mesh *m, double *u) {
+  for (int b = 0; b < m->nblocks; ++b) {
+    long e0 = ext(m, b, 0), e1 = ext(m, b, 1), e2 = ext(m, b, 2);
+    long S = e0 * e1 * e2;
+    double *base = u + blk_offset(m, b);
+    for (long k = 0; k < e2; ++k)
+      for (long j = 0; j < e1; ++j)
+        for (long i = 0; i < e0; ++i) {
+          if (is_interior(m, b, (int)i, (int)j, (int)k)) continue;
+          double x[3];
+          cell_centre(m, b, (int)i, (int)j, (int)k, x);
+          if (m->periodic) {
+            for (int d = 0; d < 3; ++d) {
+              double L = m->dom_hi[d] - m->dom_lo[d];
+              while (x[d] < m->dom_lo[d]) x[d] += L;
+              while (x[d] >= m->dom_hi[d]) x[d] -= L;
+            }
+          } else if (is_outside(m, x)) {
+            continue; /* Sommerfeld cell: evolved, never copied into */
+          }
+          int q[3];
+          int ob = find_owner(m, x, q);
+          if (ob < 0) continue;
+          long f0 = ext(m, ob, 0), f1 = ext(m, ob, 1), f2 = ext(m, ob, 2);
+          long So = f0 * f1 * f2;
+          const double *src = u + blk_offset(m, ob) + ((long)q[2] * f1 + q[1]) * f0 + q[0];
+          long cidx = (k * e1 + j) * e0 + i;
+          for (int f = 0; f < NF; ++f) base[f * S + cidx] = src[f * So];
+        }
+  }
+}
+
+/* ------------------------------------------------------------------ */
+/* algebraic constraint enforcement: det gt = 1, tr At = 0              */
+/* ------------------------------------------------------------------ */
+
+static void enforce_cell(double *c, long S) {
+  double g[3][3], A[3][3], gi[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      g[i][j] = c[(F_GXX + SYM[i][j]) * S];
+      A[i][j] = c[(F_AXX + SYM[i][j]) * S];
+    }
+  double det = det3(g);
+  double scale = pow(det, -1.0 / 3.0);
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) g[i][j] *= scale;
+  inv3(g, gi);
+  double tr = 0.0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) tr += gi[i][j] * A[i][j];
+  for (int i = 0; i < 3; ++i)
+    for (int j = i; j < 3; ++j) {
+      c[(F_GXX + SYM[i][j]) * S] = g[i][j];
+      c[(F_AXX + SYM[i][j]) * S] = A[i][j] - g[i][j] * tr / 3.0;
+    }
+}
+
+static int is_evolved(const orc_mesh *m, int b, int i, int j, int k) {
+  return is_interior(m, b, i, j, k) || is_sommerfeld(m, b, i, j, k);
+}
+
+void orc_enforce(const orc_mesh *m, double *u) {
+  for (int b = 0; b < m->nblocks; ++b) {
+    long e0 = ext(m, b, 0), e1 = ext(m, b, 1), e2 = ext(m, b, 2);
+    long S = e0 * e1 * e2;
+    double *base = u + blk_offset(m, b);
+    for (long k = 0; k < e2; ++k)
+      for (long j = 0; j < e1; ++j)
+        for (long i = 0; i < e0; ++i)
+          if (is_evolved(m, b, (int)i, (int)j, (int)k)) enforce_cell(base + (k * e1 + j) * e0 + i, S);
+  }
+}
+
+/* ------------------------------------------------------------------ */
+/* classic RK4 (R2)                                                    */
+/* ------------------------------------------------------------------ */
+
+/* y = x + a * k on evolved cells */
+static void axpy_evolved(const orc_mesh *m, double *y, const double *x, double a, const double *k) {
+  for (int b = 0; b < m->nblocks; ++b) {
+    long e0 = ext(m, b, 0), e1 = ext(m, b, 1), e2 = ext(m, b, 2);
+    long S = e0 * e1 * e2;
+    long off = blk_offset(m, b);
+    for (long kk = 0; kk < e2; ++kk)
+      for (long j = 0; j < e1; ++j)
+        for (long i = 0; i < e0; ++i) {
+          if (!is_evolved(m, b, (int)i, (int)j, (int)kk)) continue;
+          long c = off + (kk * e1 + j) * e0 + i;
+          for (int f = 0; f < NF; ++f) y[c + f * S] = x[c + f * S] + a * k[c + f * S];
+        }
+  }
+}
+
+int orc_rk4_step(const orc_mesh *m, double *u, double dt, int nsteps) {
+  long n = orc_state_size(m);
+  double *us = malloc(sizeof(double) * n);
+  double *k[4];
+  for (int s = 0; s < 4; ++s) k[s] = malloc(sizeof(double) * n);
+  if (!us || !k[0] || !k[1] || !k[2] || !k[3]) return -1;
+  const double c[4] = {0.0, 0.5, 0.5, 1.0};
+  for (int step = 0; step < nsteps; ++step) {
+    memcpy(us, u, sizeof(double) * n);
+    for (int s = 0; s < 4; ++s) {
+      if (s > 0) {
+        axpy_evolved(m, us, u, c[s] * dt, k[s - 1]);
+        orc_enforce(m, us);
+      }
+      orc_fill_ghosts(m, us);
+      orc_rhs(m, us, k[s]);
+    }
+    /* u+ = u0 + dt/6 (k1 + 2 k2 + 2 k3 + k4) */
+    for (long q = 0; q < n; ++q) {
+      double sum = k[0][q] + 2.0 * k[1][q] + 2.0 * k[2][q] + k[3][q];
+      us[q] = sum;
+    }
+    axpy_evolved(m, u, u, dt / 6.0, us);
+    orc_enforce(m, u);
+  }
+  free(us);
+  for (int s = 0; s < 4; ++s) free(k[s]);
+  return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* constraints H and M^i and their norms                               */
+/* ------------------------------------------------------------------ */
+
+/* norms[0] = ||H||_2, [1] = ||M||_2, [2] = max|H|, [3] = ||H||_2 over
+ * r > r_mask, [4] = ||M||_2 over r > r_mask, [5] = max|M|.
+ * ||X||_2 = sqrt(sum X^2 h^3 / sum h^3) over interior cells.
+ * per_cell (nullable): 4 values per storage cell (H, Mx, My, Mz), field
+ * major like the state (4 "fields"). */
+void orc_constraints(const orc_mesh *m, const double *u, double r_mask, double *per_cell, double norms[6]) {
+  double sH = 0, sM = 0, sV = 0, mH = 0, sHm = 0, sMm = 0, sVm = 0, mM = 0;
+  long pc_off = 0;
+  for (int b = 0; b < m->nblocks; ++b) {
+    long e0 = ext(m, b, 0), e1 = ext(m, b, 1), e2 = ext(m, b, 2);
+    long S = e0 * e1 * e2;
+    long st[3] = {1, e0, e0 * e1};
+    const double *base = u + blk_offset(m, b);
+    double h = m->h[b], vol = h * h * h;
+    for (long k = 0; k < e2; ++k)
+      for (long j = 0; j < e1; ++j)
+        for (long i = 0; i < e0; ++i) {
+          long cidx = (k * e1 + j) * e0 + i;
+          if (!is_interior(m, b, (int)i, (int)j, (int)k)) {
+            if (per_cell)
+              for (int q = 0; q < 4; ++q) per_cell[pc_off + q * S + cidx] = 0.0;
+            continue;
+          }
+          point_data P;
+          geometry G;
+          gather_point(m, base + cidx, S, st, h, &P, 1);
+          compute_geometry(m, &P, &G);
+          double H = G.Rs + 2.0 / 3.0 * G.K * G.K - G.AA;
+          /* d_k gt^ij = - gt^ia gt^jb d_k gt_ab */
+          double dgi[3][3][3];
+          for (int kk = 0; kk < 3; ++kk)
+            for (int a = 0; a < 3; ++a)
+              for (int c2 = 0; c2 < 3; ++c2) {
+                double s = 0.0;
+                for (int p = 0; p < 3; ++p)
+                  for (int q = 0; q < 3; ++q) s -= G.gi[a][p] * G.gi[c2][q] * P.dg[kk][p][q];
+                dgi[kk][a][c2] = s;
+              }
+          double M[3];
+          double dK[3];
+          for (int kk = 0; kk < 3; ++kk) dK[kk] = P.dKhat[kk] + 2.0 * P.dTheta[kk];
+          for (int a = 0; a < 3; ++a) {
+            double s = 0.0;
+            /* d_j At^aj by the product rule */
+            for (int jj = 0; jj < 3; ++jj)
+              for (int p = 0; p < 3; ++p)
+                for (int q = 0; q < 3; ++q)
+                  s += dgi[jj][a][p] * G.gi[jj][q] * P.A[p][q] + G.gi[a][p] * dgi[jj][jj][q] * P.A[p][q] +
+                       G.gi[a][p] * G.gi[jj][q] * P.dA[jj][p][q];
+            for (int jj = 0; jj < 3; ++jj)
+              for (int kk = 0; kk < 3; ++kk) s += G.Gu[a][jj][kk] * G.Au[jj][kk];
+            for (int jj = 0; jj < 3; ++jj) s -= 1.5 / G.chig * G.Au[a][jj] * P.dchi[jj];
+            for (int jj = 0; jj < 3; ++jj) s -= 2.0 / 3.0 * G.gi[a][jj] * dK[jj];
+            M[a] = s;
+          }
+          double M2 = M[0] * M[0] + M[1] * M[1] + M[2] * M[2];
+          sH += H * H * vol;
+          sM += M2 * vol;
+          sV += vol;
+          if (fabs(H) > mH) mH = fabs(H);
+          if (sqrt(M2) > mM) mM = sqrt(M2);
+          double x[3];
+          cell_centre(m, b, (int)i, (int)j, (int)k, x);
+          double r = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+          if (r > r_mask) {
+            sHm += H * H * vol;
+            sMm += M2 * vol;
+            sVm += vol;
+          }
+          if (per_cell) {
+            per_cell[pc_off + cidx] = H;
+            for (int q = 0; q < 3; ++q) per_cell[pc_off + (q + 1) * S + cidx] = M[q];
+          }
+        }
+    pc_off += 4 * S;
+  }
+  norms[0] = sqrt(sH / sV);
+  norms[1] = sqrt(sM / sV);
+  norms[2] = mH;
+  norms[3] = sVm > 0 ? sqrt(sHm / sVm) : 0.0;
+  norms[4] = sVm > 0 ? sqrt(sMm / sVm) : 0.0;
+  norms[5] = mM;
+}
+
+/* ------------------------------------------------------------------ */
+/* analytic initial data on every storage cell (ghosts included)       */
+/* ------------------------------------------------------------------ */
+
+/* kind 0: flat space.
+ * kind 1: gauge wave along x, par = {A, d, t}:  H = 1 - A sin(2 pi (x - t)/d),
+ *         ds^2 = -H dt^2 + H dx^2 + dy^2 + dz^2, zero shift.
+ * kind 2: linear TT wave along x, par = {A, d, t}: gamma_yy = 1 + a,
+ *         gamma_zz = 1 - a, a = A sin(2 pi (x - t)/d), K_ij = -1/2 d_t gamma_ij,
+ *         alpha = 1, zero shift.
+ * kind 3: Schwarzschild in isotropic coordinates at the origin,
+ *         par = {M, lapse_kind}: psi = 1 + M/(2r), chi = psi^-4, gt = delta,
+ *         At = Khat = Theta = Gam = 0, zero shift; alpha = psi^-2
+ *         (lapse_kind 0, "pre-collapsed") or (1 - M/2r)/(1 + M/2r)
+ *         (lapse_kind 1, the static lapse).
+ * kind 4: Brill-Lindquist punctures, par = {np, m_1, x_1, y_1, z_1, ...}:
+ *         psi = 1 + sum m_a / (2 r_a), alpha = psi^-2, otherwise as kind 3. */
+static void id_point(int kind, const double *par, const double x[3], double v[NF]) {
+  for (int f = 0; f < NF; ++f) v[f] = 0.0;
+  v[F_CHI] = 1.0;
+  v[F_GXX] = v[F_GYY] = v[F_GZZ] = 1.0;
+  v[F_ALPHA] = 1.0;
+  const double pi = 3.14159265358979323846;
+  if (kind == 1) {
+    double A = par[0], d = par[1], t = par[2];
+    double ph = 2.0 * pi * (x[0] - t) / d;
+    double H = 1.0 - A * sin(ph);
+    double Kxx = -pi * A / d * cos(ph) / sqrt(H);
+    double K = Kxx / H;
+    double chi = pow(H, -1.0 / 3.0);
+    v[F_CHI] = chi;
+    v[F_GXX] = pow(H, 2.0 / 3.0);
+    v[F_GYY] = chi;
+    v[F_GZZ] = chi;
+    v[F_KHAT] = K;
+    v[F_AXX] = 2.0 / 3.0 * chi * Kxx;
+    v[F_AYY] = -chi * K / 3.0;
+    v[F_AZZ] = -chi * K / 3.0;
+    v[F_GAMX] = -4.0 * pi * A / (3.0 * d) * cos(ph) * pow(H, -5.0 / 3.0);
+    v[F_ALPHA] = sqrt(H);
+  } else if (kind == 2) {
+    double A = par[0], d = par[1], t = par[2];
+    double ph = 2.0 * pi * (x[0] - t) / d;
+    double a = A * sin(ph);
+    double da = 2.0 * pi / d * A * cos(ph);  /* d_x a = -d_t a */
+    double gyy = 1.0 + a, gzz = 1.0 - a;
+    double Kyy = 0.5 * da, Kzz = -0.5 * da; /* -1/2 d_t gamma */
+    double K = Kyy / gyy + Kzz / gzz;
+    double chi = pow(gyy * gzz, -1.0 / 3.0);
+    v[F_CHI] = chi;
+    v[F_GXX] = chi;
+    v[F_GYY] = chi * gyy;
+    v[F_GZZ] = chi * gzz;
+    v[F_KHAT] = K;
+    v[F_AXX] = chi * (0.0 - K / 3.0);
+    v[F_AYY] = chi * (Kyy - gyy * K / 3.0);
+    v[F_AZZ] = chi * (Kzz - gzz * K / 3.0);
+    /* Gam^x = -d_x gt^xx, gt^xx = 1/chi = (1 - a^2)^(1/3) */
+    v[F_GAMX] = 2.0 / 3.0 * a * da * pow(1.0 - a * a, -2.0 / 3.0);
+  } else if (kind == 3 || kind == 4) {
+    double psi = 1.0;
+    double M = 0.0;
+    if (kind == 3) {
+      M = par[0];
+      double r = sqrt(x[0] * x[0] + x[1] * x[1] + x[2] * x[2]);
+      psi += M / (2.0 * r);
+      if ((int)par[1] == 1)
+        v[F_ALPHA] = (1.0 - M / (2.0 * r)) / (1.0 + M / (2.0 * r));
+      else
+        v[F_ALPHA] = 1.0 / (psi * psi);
+    } else {
+      int np = (int)par[0];
+      for (int a = 0; a < np; ++a) {
+        const double *q = par + 1 + 4 * a;
+        double dx = x[0] - q[1], dy = x[1] - q[2], dz = x[2] - q[3];
+        psi += q[0] / (2.0 * sqrt(dx * dx + dy * dy + dz * dz));
+      }
+      v[F_ALPHA] = 1.0 / (psi * psi);
+    }
+    v[F_CHI] = 1.0 / (psi * psi * psi * psi);
+  }
+}
+
+void orc_initial_data(const orc_mesh *m, double *u, int kind, const double *par) {
+  for (int b = 0; b < m->nblocks; ++b) {
+    long e0 = ext(m, b, 0), e1 = ext(m, b, 1), e2 = ext(m, b, 2);
+    long S = e0 * e1 * e2;
+    double *base = u + blk_offset(m, b);
+    for (long k = 0; k < e2; ++k)
+      for (long j = 0; j < e1; ++j)
+        for (long i = 0; i < e0; ++i) {
+          double x[3], v[NF];
+          cell_centre(m, b, (int)i, (int)j, (int)k, x);
+          id_point(kind, par, x, v);
+          long cidx = (k * e1 + j) * e0 + i;
+          for (int f = 0; f < NF; ++f) base[f * S + cidx] = v[f];
+        }
+  }
+}
+
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
+}

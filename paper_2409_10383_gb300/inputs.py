@@ -1,0 +1,102 @@
+"""Seeded synthetic inputs shared by the CUDA path's tests/benchmark and the oracle.
+
+This module holds no arithmetic of the method: only mesh shapes (block
+lists), parameter sets and seeded random perturbations.  Both sides build
+their own meshes from these descriptions; random numbers are drawn here and
+passed to both sides as plain arrays.
+
+Workloads (shapes and values follow the paper's test problems, Secs. 4-5):
+  gauge_wave_32     one 32^3 block, 3 ghosts, periodic [-1/2,1/2]^3, order 4,
+                    KO 0.02, harmonic lapse, frozen zero shift, A = 0.01
+  single_puncture   128^3 as 2x2x2 blocks of 64^3, 4 ghosts, [-16,16]^3,
+                    Sommerfeld outer boundary, order 6, KO 0.5, 1+log,
+                    Gamma-driver eta = 2, kappa1 = 0.02, Schwarzschild M = 1
+                    with pre-collapsed lapse
+  uneven_batch      seeded instances of mixed sizes (see uneven_batch())
+"""
+from __future__ import annotations
+
+import numpy as np
+
+NF = 22
+SEED = 20240916
+
+# initial-data kinds understood by both sides
+ID_FLAT, ID_GAUGE_WAVE, ID_LINEAR_WAVE, ID_SCHWARZSCHILD, ID_BRILL_LINDQUIST = 0, 1, 2, 3, 4
+
+
+def uniform_blocks(nb=(1, 1, 1), n=32, dom_lo=(-0.5,) * 3, dom_hi=(0.5,) * 3):
+    """nb[0] x nb[1] x nb[2] equal blocks covering the box; returns (n, lo, h) arrays."""
+    n3 = np.array((n, n, n) if np.isscalar(n) else n, dtype=np.int64)
+    L = np.array(dom_hi, float) - np.array(dom_lo, float)
+    hs = L / (np.array(nb) * n3)
+    if not np.allclose(hs, hs[0]):
+        raise ValueError("blocks must have cubic cells")
+    h = float(hs[0])
+    ns, los = [], []
+    for kb in range(nb[2]):
+        for jb in range(nb[1]):
+            for ib in range(nb[0]):
+                ns.append(n3.copy())
+                los.append([dom_lo[0] + ib * n3[0] * h, dom_lo[1] + jb * n3[1] * h,
+                            dom_lo[2] + kb * n3[2] * h])
+    return np.array(ns, np.int64), np.array(los, float), np.full(len(ns), h)
+
+
+def workload(name: str) -> dict:
+    """Named workload: mesh + parameters + initial data (no arithmetic of the method)."""
+    if name == "gauge_wave_32":
+        n, lo, h = uniform_blocks((1, 1, 1), 32)
+        return dict(name=name, n=n, lo=lo, h=h, ghosts=3, order=4, periodic=True,
+                    dom_lo=(-0.5,) * 3, dom_hi=(0.5,) * 3, lapse=0, shift=0, ko_sigma=0.02,
+                    kappa1=0.0, kappa2=0.0, eta=0.0, chi_floor=1e-6, cfl=0.25, steps=10,
+                    id_kind=ID_GAUGE_WAVE, id_par=[0.01, 1.0, 0.0])
+    if name == "single_puncture_128":
+        n, lo, h = uniform_blocks((2, 2, 2), 64, (-16.0,) * 3, (16.0,) * 3)
+        return dict(name=name, n=n, lo=lo, h=h, ghosts=4, order=6, periodic=False,
+                    dom_lo=(-16.0,) * 3, dom_hi=(16.0,) * 3, lapse=1, shift=1, ko_sigma=0.5,
+                    kappa1=0.02, kappa2=0.0, eta=2.0, chi_floor=1e-6, cfl=0.25, steps=100,
+                    id_kind=ID_SCHWARZSCHILD, id_par=[1.0, 0.0])
+    if name.startswith("single_puncture_"):
+        # same physics at a smaller size: single_puncture_<N>_<nb>
+        _, _, N, nb = name.split("_")
+        N, nb = int(N), int(nb)
+        n, lo, h = uniform_blocks((nb, nb, nb), N // nb, (-16.0,) * 3, (16.0,) * 3)
+        return dict(name=name, n=n, lo=lo, h=h, ghosts=4, order=6, periodic=False,
+                    dom_lo=(-16.0,) * 3, dom_hi=(16.0,) * 3, lapse=1, shift=1, ko_sigma=0.5,
+                    kappa1=0.02, kappa2=0.0, eta=2.0, chi_floor=1e-6, cfl=0.25, steps=100,
+                    id_kind=ID_SCHWARZSCHILD, id_par=[1.0, 0.0])
+    raise KeyError(name)
+
+
+def noise(size: int, seed: int, amp: float = 1.0) -> np.ndarray:
+    """Uniform noise in [-amp, amp], seeded."""
+    return np.random.default_rng(seed).uniform(-amp, amp, size)
+
+
+def perturbation(shape_per_block, seed: int, amp: float) -> list:
+    """Seeded random perturbation per block: a list of (22, ez, ey, ex) arrays
+    of uniform noise in [-amp, amp].  Adding it to a state keeps gt SPD and
+    chi, alpha positive as long as amp << 1."""
+    rng = np.random.default_rng(seed)
+    return [rng.uniform(-amp, amp, (NF,) + tuple(s)) for s in shape_per_block]
+
+
+def uneven_batch(seed: int = SEED):
+    """64 single-puncture instances with seeded masses in [0.5, 2] and sizes
+    from {24, 48, 64, 96}^3, plus 16 gauge-wave instances with amplitudes in
+    [0.001, 0.1]; order and precision alternate with the instance index."""
+    rng = np.random.default_rng(seed)
+    sizes = (24, 48, 64, 96)
+    out = []
+    for i in range(80):
+        n = int(sizes[rng.integers(0, 4)])
+        if i < 64:
+            mass = float(rng.uniform(0.5, 2.0))
+            out.append(dict(kind="puncture", n=n, mass=mass, order=6 if i % 2 == 0 else 4,
+                            precision=64 if (i // 2) % 2 == 0 else 32))
+        else:
+            amp = float(rng.uniform(0.001, 0.1))
+            out.append(dict(kind="gauge_wave", n=n, amp=amp, order=6 if i % 2 == 0 else 4,
+                            precision=64 if (i // 2) % 2 == 0 else 32))
+    return out

@@ -1,0 +1,91 @@
+"""Closed-form spacetimes, conformally decomposed with sympy (test-only).
+
+Given a lapse alpha, shift beta^i and spatial metric gamma_ij as explicit
+functions of (t, x, y, z), this derives the 22 Z4c variables and their exact
+time derivatives, independently of the oracle's code:
+  K_ij   = -(d_t gamma_ij - D_i beta_j - D_j beta_i) / (2 alpha)
+  chi    = det(gamma)^(-1/3),  gt_ij = chi gamma_ij,  K = gamma^ij K_ij
+  At_ij  = chi (K_ij - gamma_ij K / 3),  Khat = K,  Theta = 0
+  Gam^i  = -d_j gt^ij
+These are the standard conformal decomposition used by the Z4c system
+(Sec. 2 of the paper defers the details to the GR-Athena++ paper).
+"""
+from __future__ import annotations
+
+from functools import lru_cache
+
+import numpy as np
+import sympy as sp
+
+NF = 22
+x, y, z, t = sp.symbols("x y z t", real=True)
+XS = (x, y, z)
+SYM = ((0, 0), (0, 1), (0, 2), (1, 1), (1, 2), (2, 2))
+
+
+def _decompose(alpha, beta_u, gamma):
+    g = sp.Matrix(3, 3, lambda i, j: gamma[i][j])
+    detg = g.det()
+    adj = g.adjugate()
+    gi = adj / detg
+    # Christoffel symbols of gamma
+    dg = [[[sp.diff(g[i, j], XS[k]) for k in range(3)] for j in range(3)] for i in range(3)]
+    Gam = [[[sum(gi[k, l] * (dg[l][i][j] + dg[l][j][i] - dg[i][j][l]) for l in range(3)) / 2
+             for j in range(3)] for i in range(3)] for k in range(3)]
+    beta_d = [sum(g[i, j] * beta_u[j] for j in range(3)) for i in range(3)]
+    Db = [[sp.diff(beta_d[j], XS[i]) - sum(Gam[k][i][j] * beta_d[k] for k in range(3))
+           for j in range(3)] for i in range(3)]
+    K = [[-(sp.diff(g[i, j], t) - Db[i][j] - Db[j][i]) / (2 * alpha) for j in range(3)]
+         for i in range(3)]
+    trK = sum(gi[i, j] * K[i][j] for i in range(3) for j in range(3))
+    chi = detg ** sp.Rational(-1, 3)
+    gt = [[chi * g[i, j] for j in range(3)] for i in range(3)]
+    At = [[chi * (K[i][j] - g[i, j] * trK / 3) for j in range(3)] for i in range(3)]
+    gti = [[gi[i, j] / chi for j in range(3)] for i in range(3)]
+    Gamt = [-sum(sp.diff(gti[i][j], XS[j]) for j in range(3)) for i in range(3)]
+    fields = [chi] + [gt[i][j] for i, j in SYM] + [trK] + [At[i][j] for i, j in SYM] + \
+        Gamt + [sp.Integer(0), alpha] + list(beta_u)
+    return fields
+
+
+@lru_cache(maxsize=None)
+def _compiled(kind: str, params: tuple):
+    if kind == "gauge_wave":
+        A, d = params
+        H = 1 - A * sp.sin(2 * sp.pi * (x - t) / d)
+        fields = _decompose(sp.sqrt(H), [0, 0, 0], [[H, 0, 0], [0, 1, 0], [0, 0, 1]])
+    elif kind == "linear_wave":
+        A, d = params
+        a = A * sp.sin(2 * sp.pi * (x - t) / d)
+        fields = _decompose(sp.Integer(1), [0, 0, 0], [[1, 0, 0], [0, 1 + a, 0], [0, 0, 1 - a]])
+    elif kind == "kerr_schild":
+        (M,) = params
+        r = sp.sqrt(x * x + y * y + z * z)
+        Hs = M / r
+        l = [x / r, y / r, z / r]
+        gamma = [[sp.KroneckerDelta(i, j) + 2 * Hs * l[i] * l[j] for j in range(3)] for i in range(3)]
+        alpha = 1 / sp.sqrt(1 + 2 * Hs)
+        beta_u = [2 * Hs / (1 + 2 * Hs) * l[i] for i in range(3)]
+        fields = _decompose(alpha, beta_u, gamma)
+    else:
+        raise KeyError(kind)
+    dfields = [sp.diff(f, t) for f in fields]
+    fn = sp.lambdify((t, x, y, z), fields, modules="numpy", cse=True)
+    dfn = sp.lambdify((t, x, y, z), dfields, modules="numpy", cse=True)
+    return fn, dfn
+
+
+def evaluate(kind: str, params: tuple, X, Y, Z, time: float = 0.0, dt: bool = False) -> np.ndarray:
+    """(22,) + X.shape array of the fields (or of their time derivatives)."""
+    fn, dfn = _compiled(kind, tuple(params))
+    vals = (dfn if dt else fn)(time, X, Y, Z)
+    return np.stack([np.broadcast_to(np.asarray(v, dtype=float), X.shape) for v in vals])
+
+
+def state_on_mesh(mesh, kind, params, time=0.0, dt=False) -> np.ndarray:
+    """Flat state array in the oracle's layout, every storage cell filled."""
+    u = mesh.zeros()
+    for b, blk in enumerate(mesh.blocks(u)):
+        X, Y, Z = mesh.centres(b)
+        blk[...] = evaluate(kind, params, X, Y, Z, time, dt)
+    return u

@@ -1,0 +1,395 @@
+"""Pins for the oracle's Z4c right-hand side, RK4, ghost fill, constraint
+enforcement, constraints and initial data.
+
+None of these compares the oracle with itself.  Each checks it against
+something fixed by the mathematics or the paper:
+  - flat space is an exact solution: the RHS is exactly zero (Sec. 2);
+  - gauge wave / linear wave / Kerr-Schild: exact solutions derived with
+    sympy from their ADM form in tests/analytic.py; the discrete RHS must
+    converge to their exact time derivatives at the differencing order;
+  - static Schwarzschild in isotropic coordinates: stationary, RHS -> 0;
+  - axis permutations and reflections of a random state permute the RHS;
+  - det gt = 1 and tr At = 0 after enforcement;
+  - Hamiltonian/momentum constraints converge to zero on exact data;
+  - classic RK4 converges at 4th order in dt (Sec. 4.1 uses RK4);
+  - the linear-wave L1_RMS error of Sec. 4.1 converges with resolution;
+  - ghost fill reproduces a periodic wrap and is independent of blocking.
+"""
+import numpy as np
+import pytest
+
+import analytic as an
+from paper_2409_10383_gb300 import inputs
+
+NF = 22
+NONGAUGE = slice(0, 18)
+
+
+def interior(mesh, u, b=0):
+    return mesh.blocks(u)[b][:, mesh.interior_mask(b)]
+
+
+def order_of(errs):
+    errs = np.asarray(errs, float)
+    return np.log2(errs[:-1] / errs[1:])
+
+
+# --------------------------------------------------------------------------
+def test_flat_space_rhs_is_exactly_zero(oracle):
+    for order in (4, 6):
+        for periodic in (True, False):
+            m = oracle.uniform_mesh(nb=(2, 1, 1), n=(8, 12, 10), order=order, periodic=periodic,
+                                    lapse=1, shift=1, ko_sigma=0.5, kappa1=0.02, eta=2.0,
+                                    dom_lo=(-1, -0.75, -0.625), dom_hi=(1, 0.75, 0.625))
+            u = m.initial_data(inputs.ID_FLAT, [])
+            m.fill_ghosts(u)
+            k = m.rhs(u)
+            assert np.all(k == 0.0)
+            u0 = u.copy()
+            m.rk4(u, 0.01, 2)
+            for b in range(m.nblocks):
+                ev = m.evolved_mask(b)
+                assert np.all(m.blocks(u)[b][:, ev] == m.blocks(u0)[b][:, ev])
+
+
+# --------------------------------------------------------------------------
+def test_initial_data_matches_closed_forms(oracle):
+    m = oracle.uniform_mesh(n=(16, 6, 4), order=4, periodic=True,
+                            dom_lo=(-0.5, -3 / 16, -0.125), dom_hi=(0.5, 3 / 16, 0.125))
+    for kind, name, par in [(inputs.ID_GAUGE_WAVE, "gauge_wave", (0.1, 1.0)),
+                            (inputs.ID_LINEAR_WAVE, "linear_wave", (1e-3, 1.0))]:
+        for t in (0.0, 0.3):
+            u = m.initial_data(kind, list(par) + [t])
+            ua = an.state_on_mesh(m, name, par, time=t)
+            assert np.abs(u - ua).max() < 1e-14
+    # Schwarzschild / Brill-Lindquist: chi = psi^-4, alpha = psi^-2
+    ms = oracle.uniform_mesh(n=8, order=6, periodic=False, dom_lo=(0.3, -1, 0.2), dom_hi=(2.3, 1, 2.2))
+    X, Y, Z = ms.centres(0)
+    r = np.sqrt(X * X + Y * Y + Z * Z)
+    B = ms.blocks(ms.initial_data(inputs.ID_SCHWARZSCHILD, [1.3, 0]))[0]
+    psi = 1 + 1.3 / (2 * r)
+    assert np.allclose(B[0], psi ** -4, rtol=1e-14) and np.allclose(B[18], psi ** -2, rtol=1e-14)
+    B = ms.blocks(ms.initial_data(inputs.ID_SCHWARZSCHILD, [1.3, 1]))[0]
+    assert np.allclose(B[18], (1 - 1.3 / (2 * r)) / (1 + 1.3 / (2 * r)), rtol=1e-14)
+    B = ms.blocks(ms.initial_data(inputs.ID_BRILL_LINDQUIST, [2, 0.5, 3, 0, 0, 0.7, -3, 0.5, 0]))[0]
+    psi = 1 + 0.5 / (2 * np.sqrt((X - 3) ** 2 + Y ** 2 + Z ** 2)) + \
+        0.7 / (2 * np.sqrt((X + 3) ** 2 + (Y - 0.5) ** 2 + Z ** 2))
+    assert np.allclose(B[0], psi ** -4, rtol=1e-14)
+    for f in list(range(1, 18)) + [19, 20, 21]:
+        assert np.all(B[f] == (1.0 if f in (1, 4, 6) else 0.0))
+
+
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("order", [4, 6])
+def test_gauge_wave_rhs_converges_to_exact_time_derivative(oracle, order):
+    errs = []
+    for n in (16, 32, 64):
+        w = 4.0 / n
+        m = oracle.uniform_mesh(n=(n, 4, 4), order=order, periodic=True, lapse=0, shift=0,
+                                dom_lo=(-0.5, -w / 2, -w / 2), dom_hi=(0.5, w / 2, w / 2))
+        u = an.state_on_mesh(m, "gauge_wave", (0.1, 1.0), time=0.2)
+        m.fill_ghosts(u)
+        k = interior(m, m.rhs(u))
+        dt = interior(m, an.state_on_mesh(m, "gauge_wave", (0.1, 1.0), time=0.2, dt=True))
+        errs.append(np.abs(k - dt).max(axis=1))
+    errs = np.array(errs)
+    e = errs.max(axis=1)
+    assert np.all(order_of(e)[-1:] > order - 0.3), e
+    # Theta stays a pure truncation error and every field converges
+    assert errs[-1, 17] < 1e-4
+
+
+@pytest.mark.parametrize("order", [4, 6])
+def test_static_schwarzschild_rhs_converges_to_zero(oracle, order):
+    """Isotropic Schwarzschild with the static lapse is stationary: with
+    1+log slicing and K = 0 every RHS must vanish in the continuum (pins the
+    Ricci tensor, the chi terms and D_i D_j alpha)."""
+    errs = []
+    for n in (16, 32, 64):
+        m = oracle.uniform_mesh(n=n, order=order, periodic=False, lapse=1, shift=1, kappa1=0.02,
+                                dom_lo=(0.5, 0.5, 0.5), dom_hi=(4.5, 4.5, 4.5))
+        u = m.initial_data(inputs.ID_SCHWARZSCHILD, [1.0, 1])
+        X, Y, Z = m.centres(0)
+        r = np.sqrt(X * X + Y * Y + Z * Z)
+        sel = m.interior_mask(0) & (r > 1.5) & (r < 3.5)
+        k = m.blocks(m.rhs(u))[0]
+        errs.append(np.abs(k[:, sel]).max())
+    assert np.all(order_of(errs) > order - 1.0), errs
+    assert order_of(errs)[-1] > order - 0.5, errs
+
+
+@pytest.mark.parametrize("order,ns,box", [(4, (8, 16, 32), (2.5, 3.5)), (6, (6, 12, 24), (2.0, 3.5))])
+def test_kerr_schild_rhs_converges_to_zero(oracle, order, ns, box):
+    """Schwarzschild in Kerr-Schild form is stationary with non-zero shift:
+    with its own lapse and shift every non-gauge RHS vanishes in the
+    continuum.  Pins every shift term (advection, Lie-derivative terms,
+    d d beta in the Gam equation) and the At / K algebra."""
+    errs = []
+    for n in ns:
+        lo = (box[0], box[0] - 0.2, box[0] - 0.1)
+        hi = tuple(v + box[1] - box[0] for v in lo)
+        m = oracle.uniform_mesh(n=n, order=order, periodic=False, lapse=1, shift=1, kappa1=0.02,
+                                dom_lo=lo, dom_hi=hi)
+        u = an.state_on_mesh(m, "kerr_schild", (1.0,))
+        k = interior(m, m.rhs(u))
+        errs.append(np.abs(k[NONGAUGE]).max(axis=1))
+    errs = np.array(errs)
+    ords = order_of(errs.max(axis=1))
+    assert np.all(ords > order - 0.6), (ords, errs)
+    assert np.all(errs[-1] < 1e-6 if order == 4 else errs[-1] < 1e-8)
+
+
+# --------------------------------------------------------------------------
+def random_state(oracle, m, seed, amp=2e-3):
+    u = m.initial_data(inputs.ID_FLAT, [])
+    for blk, p in zip(m.blocks(u), inputs.perturbation([m.ext(b)[::-1] for b in range(m.nblocks)], seed, amp)):
+        blk += p
+    return u
+
+
+def transform_state(m_from, u, m_to, perm, flip):
+    """Apply x'_a = s_a x_{perm[a]} to a single-block state; returns the state
+    on mesh m_to.  Tensor components transform with the same map."""
+    src = m_from.blocks(u)[0]
+    out = m_to.zeros()
+    dst = m_to.blocks(out)[0]
+    sgn = np.array([-1.0 if flip[a] else 1.0 for a in range(3)])
+    # spatial axes of arrays are (z, y, x) = (2, 1, 0)
+    arr = src
+    for a in range(3):
+        if flip[a]:
+            arr = np.flip(arr, axis=3 - perm[a])
+    axes = [0] + [3 - perm[2 - q] for q in range(3)]
+    arr = np.transpose(arr, axes)
+    sym = {(0, 0): 0, (0, 1): 1, (0, 2): 2, (1, 1): 3, (1, 2): 4, (2, 2): 5}
+    sym.update({(j, i): v for (i, j), v in list(sym.items())})
+    dst[0] = arr[0]
+    dst[7] = arr[7]
+    dst[17] = arr[17]
+    dst[18] = arr[18]
+    for a in range(3):
+        dst[14 + a] = sgn[a] * arr[14 + perm[a]]
+        dst[19 + a] = sgn[a] * arr[19 + perm[a]]
+        for c in range(a, 3):
+            s = sgn[a] * sgn[c]
+            dst[1 + sym[(a, c)]] = s * arr[1 + sym[(perm[a], perm[c])]]
+            dst[8 + sym[(a, c)]] = s * arr[8 + sym[(perm[a], perm[c])]]
+    return out
+
+
+@pytest.mark.parametrize("order", [4, 6])
+@pytest.mark.parametrize("perm,flip", [((1, 2, 0), (0, 0, 0)), ((0, 2, 1), (0, 0, 0)),
+                                       ((0, 1, 2), (1, 0, 0)), ((2, 0, 1), (0, 1, 1))])
+def test_symmetry_of_rhs_under_axis_maps(oracle, order, perm, flip):
+    n = np.array([10, 12, 14])
+    L = n / 16.0
+    m = oracle.uniform_mesh(n=tuple(n), order=order, periodic=True, lapse=1, shift=1,
+                            ko_sigma=0.3, kappa1=0.05, kappa2=0.1, eta=1.5,
+                            dom_lo=tuple(-L / 2), dom_hi=tuple(L / 2))
+    u = random_state(oracle, m, seed=7 + order)
+    m.fill_ghosts(u)
+    k = m.rhs(u)
+    n2 = n[list(perm)]
+    m2 = oracle.uniform_mesh(n=tuple(n2), order=order, periodic=True, lapse=1, shift=1,
+                             ko_sigma=0.3, kappa1=0.05, kappa2=0.1, eta=1.5,
+                             dom_lo=tuple(-n2 / 32.0), dom_hi=tuple(n2 / 32.0))
+    u2 = transform_state(m, u, m2, perm, flip)
+    m2.fill_ghosts(u2)
+    k2 = m2.rhs(u2)
+    kt = transform_state(m, k, m2, perm, flip)
+    a, b = interior(m2, k2), interior(m2, kt)
+    scale = np.abs(b).max(axis=1, keepdims=True) + 1e-300
+    assert (np.abs(a - b) / scale).max() < 1e-11
+
+
+# --------------------------------------------------------------------------
+def test_enforcement_invariants(oracle):
+    m = oracle.uniform_mesh(n=(6, 5, 4), order=4, periodic=True,
+                            dom_lo=(-0.375, -0.3125, -0.25), dom_hi=(0.375, 0.3125, 0.25))
+    u = random_state(oracle, m, seed=3, amp=0.2)
+    B = m.blocks(u)[0]
+    B[8:14] += np.random.default_rng(4).uniform(-1, 1, B[8:14].shape)
+    m.enforce(u)
+    B = m.blocks(u)[0]
+    mk = m.interior_mask(0)
+    g = np.zeros((3, 3) + B.shape[1:])
+    A = np.zeros_like(g)
+    for q, (i, j) in enumerate(an.SYM):
+        g[i, j] = g[j, i] = B[1 + q]
+        A[i, j] = A[j, i] = B[8 + q]
+    gm = np.moveaxis(g, (0, 1), (-2, -1))[mk]
+    Am = np.moveaxis(A, (0, 1), (-2, -1))[mk]
+    det = np.linalg.det(gm)
+    assert np.abs(det - 1).max() < 1e-14
+    tr = np.einsum("nij,nij->n", np.linalg.inv(gm), Am)
+    assert np.abs(tr).max() < 1e-14 * np.abs(Am).max() * 10
+    # enforcing again changes nothing beyond rounding
+    v = u.copy()
+    m.enforce(v)
+    assert np.abs(v - u).max() < 1e-14
+
+
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("order", [4, 6])
+def test_constraints_converge_on_exact_data(oracle, order):
+    """Kerr-Schild data (non-zero At and K) satisfies H = M^i = 0."""
+    errs = []
+    for n in (8, 16, 32) if order == 4 else (6, 12, 24):
+        m = oracle.uniform_mesh(n=n, order=order, periodic=False, dom_lo=(2.0, 1.8, 1.9),
+                                dom_hi=(3.5, 3.3, 3.4))
+        u = an.state_on_mesh(m, "kerr_schild", (1.0,))
+        norms, pc = m.constraints(u, per_cell=True)
+        errs.append([norms[0], norms[1], norms[2], norms[5]])
+    ords = order_of(np.array(errs))
+    assert np.all(ords > order - 1.0), (ords, errs)
+    assert np.all(ords[-1, :2] > order - 0.3), (ords, errs)
+    # momentum constraint is identically zero on time-symmetric data
+    m = oracle.uniform_mesh(n=8, order=order, periodic=False, dom_lo=(1, 1, 1), dom_hi=(3, 3, 3))
+    u = m.initial_data(inputs.ID_BRILL_LINDQUIST, [2, 0.5, 0, 0, 0, 0.5, 4, 4, 4])
+    norms, _ = m.constraints(u)
+    assert norms[1] == 0.0 and norms[5] == 0.0 and norms[0] > 0
+
+
+def test_hamiltonian_constraint_schwarzschild_convergence(oracle):
+    errs = []
+    for n in (16, 32, 64):
+        m = oracle.uniform_mesh(n=n, order=6, periodic=False, dom_lo=(0.5, 0.5, 0.5),
+                                dom_hi=(4.5, 4.5, 4.5))
+        u = m.initial_data(inputs.ID_SCHWARZSCHILD, [1.0, 0])
+        norms, _ = m.constraints(u, r_mask=1.5)
+        errs.append(norms[3])
+    assert np.all(order_of(errs) > 5.0), errs
+
+
+# --------------------------------------------------------------------------
+def test_gauge_wave_evolution_matches_exact_solution(oracle):
+    """10 RK4 steps of the gauge wave (config: 4th order, CFL 0.25) track the
+    exact solution, with errors falling at ~4th order."""
+    errs = []
+    for n in (16, 32):
+        w = 4.0 / n
+        m = oracle.uniform_mesh(n=(n, 4, 4), order=4, periodic=True, lapse=0, shift=0, ko_sigma=0.0,
+                                dom_lo=(-0.5, -w / 2, -w / 2), dom_hi=(0.5, w / 2, w / 2))
+        u = m.initial_data(inputs.ID_GAUGE_WAVE, [0.01, 1.0, 0.0])
+        dt = 0.25 / n
+        nsteps = 10 * n // 16
+        m.rk4(u, dt, nsteps)
+        ua = m.initial_data(inputs.ID_GAUGE_WAVE, [0.01, 1.0, dt * nsteps])
+        errs.append(np.abs(interior(m, u) - interior(m, ua)).max())
+    assert errs[-1] < 1e-5 and order_of(errs)[0] > 3.5, errs
+
+
+def test_rk4_is_fourth_order_in_time(oracle):
+    w = 0.25
+    m = oracle.uniform_mesh(n=(8, 2, 2), order=4, periodic=True, lapse=0, shift=0,
+                            dom_lo=(-0.5, -w / 2, -w / 2), dom_hi=(0.5, w / 2, w / 2))
+    T = 0.25
+    base = m.initial_data(inputs.ID_GAUGE_WAVE, [0.05, 1.0, 0.0])
+    sols = {}
+    for ns in (2, 4, 8, 64):
+        u = base.copy()
+        m.rk4(u, T / ns, ns)
+        sols[ns] = interior(m, u)
+    errs = [np.abs(sols[ns] - sols[64]).max() for ns in (2, 4, 8)]
+    assert np.all(order_of(errs) > 3.6) and np.all(order_of(errs) < 4.6), errs
+
+
+def test_linear_wave_l1_rms_convergence(oracle):
+    """Sec. 4.1: periodic linear wave, amplitude 1e-8, one period, 6th-order
+    differencing + RK4; L1_RMS of g_ab(T) - g_ab(0) converges (>= 4th order,
+    the RK4 limit; the paper observes 6th where space dominates)."""
+    res = []
+    for n in (8, 16, 32):
+        w = 4.0 / n
+        m = oracle.uniform_mesh(n=(n, 4, 4), order=6, periodic=True, lapse=1, shift=1,
+                                ko_sigma=0.0, eta=2.0,
+                                dom_lo=(-0.5, -w / 2, -w / 2), dom_hi=(0.5, w / 2, w / 2))
+        u = m.initial_data(inputs.ID_LINEAR_WAVE, [1e-8, 1.0, 0.0])
+        u0 = u.copy()
+        dt = 0.25 / n
+        m.rk4(u, dt, int(round(1.0 / dt)))
+        B, B0 = m.blocks(u)[0], m.blocks(u0)[0]
+        mk = m.interior_mask(0)
+        tot = 0.0
+        for a in range(3):
+            for b in range(3):
+                q = an.SYM.index((min(a, b), max(a, b)))
+                g = B[1 + q][mk] / B[0][mk]
+                g0 = B0[1 + q][mk] / B0[0][mk]
+                tot += np.mean(np.abs(g - g0)) ** 2
+        res.append(np.sqrt(tot))
+    ords = order_of(res)
+    assert res[0] > 1e-12 and np.all(ords > 4.0), (res, ords)
+
+
+# --------------------------------------------------------------------------
+def test_sommerfeld_cells(oracle):
+    """Constant asymptotic state is a fixed point; an outgoing spherical
+    wave u_inf + f(r - t)/r is reproduced to 2nd order."""
+    m = oracle.uniform_mesh(nb=(2, 2, 2), n=8, order=6, periodic=False, dom_lo=(-4,) * 3,
+                            dom_hi=(4,) * 3)
+    u = m.initial_data(inputs.ID_FLAT, [])
+    k = m.rhs(u)
+    assert np.all(k == 0)
+    errs = []
+    for n in (8, 16, 32):
+        m = oracle.uniform_mesh(n=n, order=6, periodic=False, dom_lo=(2.0, -1, -1), dom_hi=(4.0, 1, 1))
+        u = m.zeros()
+        B = m.blocks(u)[0]
+        X, Y, Z = m.centres(0)
+        r = np.sqrt(X * X + Y * Y + Z * Z)
+        prof = np.exp(-((r - 3.0) ** 2)) / r
+        for f in range(NF):
+            B[f] = (1.0 if f in (0, 1, 4, 6, 18) else 0.0) + (f + 1) * 1e-3 * prof
+        k = m.blocks(m.rhs(u))[0]
+        sm = m.sommerfeld_mask(0)
+        dprof = 2 * (r - 3.0) * np.exp(-((r - 3.0) ** 2)) / r  # d/dt of f(r-t)/r
+        errs.append(max(np.abs(k[f][sm] - (f + 1) * 1e-3 * dprof[sm]).max() for f in range(NF)))
+    assert np.all(order_of(errs) > 1.6), errs
+
+
+# --------------------------------------------------------------------------
+def test_ghost_fill_periodic_wrap(oracle):
+    m = oracle.uniform_mesh(n=(6, 7, 8), order=6, periodic=True,
+                            dom_lo=(-0.375, -0.4375, -0.5), dom_hi=(0.375, 0.4375, 0.5))
+    u = m.zeros() + inputs.noise(m.size(), 11)
+    B = m.blocks(u)[0]
+    g = m.ghosts
+    inner = B[:, g:-g, g:-g, g:-g].copy()
+    m.fill_ghosts(u)
+    ref = np.pad(inner, ((0, 0), (g, g), (g, g), (g, g)), mode="wrap")
+    assert np.array_equal(m.blocks(u)[0], ref)
+
+
+@pytest.mark.parametrize("periodic", [True, False])
+def test_blocking_does_not_change_the_rhs(oracle, periodic):
+    """One 16x12x8 block vs the same cells as 2x2x2 blocks (plus Sommerfeld
+    cells when not periodic): identical RHS on every interior cell."""
+    kw = dict(order=4, periodic=periodic, lapse=1, shift=1, ko_sigma=0.2, kappa1=0.02,
+              dom_lo=(-1, -0.75, -0.5), dom_hi=(1, 0.75, 0.5))
+    big = oracle.uniform_mesh(nb=(1, 1, 1), n=(16, 12, 8), **kw)
+    small = oracle.uniform_mesh(nb=(2, 2, 2), n=(8, 6, 4), **kw)
+    ub = big.initial_data(inputs.ID_BRILL_LINDQUIST, [1, 0.4, 0.05, 0.02, 0.01])
+    ub += inputs.noise(big.size(), 5, 1e-3) * (0 if not periodic else 1)
+    us = small.zeros()
+    g = big.ghosts
+    Bb = big.blocks(ub)[0]
+    for b, blk in enumerate(small.blocks(us)):
+        i0 = int(round((small.lo[b, 0] - kw["dom_lo"][0]) / small.h[b]))
+        j0 = int(round((small.lo[b, 1] - kw["dom_lo"][1]) / small.h[b]))
+        k0 = int(round((small.lo[b, 2] - kw["dom_lo"][2]) / small.h[b]))
+        blk[:, g:-g, g:-g, g:-g] = Bb[:, g + k0:g + k0 + 4, g + j0:g + j0 + 6, g + i0:g + i0 + 8]
+        if not periodic:
+            # Sommerfeld cells carry evolved data: copy them too
+            sm = small.sommerfeld_mask(b)
+            sub = Bb[:, k0:k0 + 4 + 2 * g, j0:j0 + 6 + 2 * g, i0:i0 + 8 + 2 * g]
+            blk[:, sm] = sub[:, sm]
+    big.fill_ghosts(ub)
+    small.fill_ghosts(us)
+    kb = big.blocks(big.rhs(ub))[0]
+    for b, blk in enumerate(small.blocks(small.rhs(us))):
+        i0 = int(round((small.lo[b, 0] - kw["dom_lo"][0]) / small.h[b]))
+        j0 = int(round((small.lo[b, 1] - kw["dom_lo"][1]) / small.h[b]))
+        k0 = int(round((small.lo[b, 2] - kw["dom_lo"][2]) / small.h[b]))
+        assert np.array_equal(blk[:, g:-g, g:-g, g:-g],
+                              kb[:, g + k0:g + k0 + 4, g + j0:g + j0 + 6, g + i0:g + i0 + 8])
