@@ -1,0 +1,310 @@
+#!/usr/bin/env python3
+"""Zone-cycles/s of the Z4c RHS + RK4 hot path on GB300 (paper Sec. 5 metric).
+
+Workload (default): single puncture, 128^3 cells as 2x2x2 MeshBlocks of 64^3
+with 4 ghosts, [-16,16]^3, Sommerfeld outer boundary, 6th-order FD, KO 0.5,
+1+log lapse, Gamma-driver (eta = 2), kappa1 = 0.02, Schwarzschild M = 1
+(pre-collapsed lapse), RK4 at CFL 0.25.  A step is one full RK4 step (4
+stages: ghost fill, fused RHS + stage update + enforcement, Sommerfeld
+cells), replayed from a CUDA graph.  One zone-cycle = one interior cell
+advanced by one RK4 step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--variant fp64|fp32]
+  python bench.py --impl reference ...   (the FP64 CPU oracle as the reference arm)
+
+Multi-GPU: one process per GPU, each evolving its own independent instance
+(weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2409_10383_gb300 import inputs  # noqa: E402
+
+METRIC = "Z4c zone-cycles/s per RK4 step on 1 GB300, FP64 vs FP32-RHS; % of roofline"
+UNIT = "zone-cycles/s"
+NOMINAL_FP64 = 1.25e12     # GB300 FP64, nominal (profiling recipe)
+L2_BYTES = 129 * 2 ** 20
+
+# Executed FP64 flops per interior cell per RHS stage of the fused interior
+# kernel (dadd + dmul + 2 dfma), from the ncu instruction counters of a
+# 2x2x2 x 32^3 order-6 capture (profiles/interior_fp64_single_puncture.md).
+FP64_FLOPS_PER_CELL_STAGE = {6: None, 4: None}
+# FP32-RHS kernel: FP32 flops and FP64 residue flops per cell per stage
+FP32_FLOPS_PER_CELL_STAGE = {6: None, 4: None}
+FP32_F64_RESIDUE_PER_CELL_STAGE = {6: None, 4: None}
+# algorithmic HBM bytes per zone-cycle (fused 3-register RK4, 22 FP64 fields)
+ALG_BYTES_PER_ZONE_CYCLE = 352 * 8
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def oracle_sample(workload, steps, warmup):
+    """The FP64 CPU oracle on a bounded sample of the workload: one 64^3
+    block of the same physics (order 6, KO 0.5, Sommerfeld boundary,
+    puncture data), RK4 steps at CFL 0.25, on all host cores."""
+    from oracle import oracle
+    oracle.build()
+    cores = host_cores()
+    oracle.set_threads(cores)
+    w = workload
+    n0 = int(w["n"][0][0])
+    lo = -float(w["h"][0]) * n0 / 2
+    m = oracle.Mesh(n=[[n0] * 3], lo=[[lo] * 3], h=[float(w["h"][0])], ghosts=w["ghosts"],
+                    order=w["order"], dom_lo=(lo,) * 3, dom_hi=(-lo,) * 3, periodic=w["periodic"],
+                    lapse=w["lapse"], shift=w["shift"], ko_sigma=w["ko_sigma"], kappa1=w["kappa1"],
+                    kappa2=w["kappa2"], eta=w["eta"], chi_floor=w["chi_floor"])
+    u = m.initial_data(w["id_kind"], w["id_par"])
+    dt = w["cfl"] * float(w["h"][0])
+    for _ in range(warmup):
+        m.rk4(u, dt, 1)
+    times = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        m.rk4(u, dt, 1)
+        times.append(time.perf_counter() - t0)
+    cells = n0 ** 3
+    return dict(value=cells * steps / sum(times), unit=UNIT, cores=cores, kind="oracle",
+                sample=f"{steps} RK4 step(s) of one {n0}^3 block (order {w['order']}, "
+                       f"KO {w['ko_sigma']}, Sommerfeld, puncture data) after {warmup} warm-up",
+                ms_per_step=1e3 * sum(times) / steps)
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None:
+            return None
+        self.file.flush()
+        rows = []
+        with open(self.file.name) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) >= 9:
+                    rows.append(p)
+        os.unlink(self.file.name)
+        if not rows:
+            return None
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return float("nan")
+        sm = np.array([num(r[1]) for r in rows])
+        mx = np.nanmax([num(r[2]) for r in rows])
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[q] for r in rows for q in range(4) if r[5 + q].lower().startswith("active")})
+        return {"sm_mhz": float(np.nanmedian(sm)), "sm_max_mhz": float(mx), "reasons": reasons,
+                "samples": len(rows), "power_w_max": float(np.nanmax([num(r[3]) for r in rows]))}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def run_reference(args, workload):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    res = oracle_sample(workload, max(1, args.steps), max(0, args.warmup))
+    line = {"impl": "reference", "metric": METRIC, "value": res["value"], "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": res["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload["name"], "sample": res["sample"]},
+            "cpu_baseline": {"value": res["value"], "unit": UNIT, "cores": res["cores"],
+                             "kind": "oracle", "sample": res["sample"]},
+            "e2e": {"value": res["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--variant", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--workload", default="single_puncture_128")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-steps", type=int, default=2)
+    args = ap.parse_args()
+    workload = inputs.workload(args.workload)
+
+    if args.impl == "reference":
+        run_reference(args, workload)
+        return
+
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    from paper_2409_10383_gb300 import z4c
+
+    prec = 64 if args.variant == "fp64" else 32
+    g = z4c.Z4c.from_workload(workload, precision=prec)
+    cells = int(np.prod(workload["n"], axis=1).sum())
+    dt = workload["cfl"] * float(workload["h"][0])
+    g.z4c_set_initial_data(workload["id_kind"], workload["id_par"])
+    st = g.stream
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+
+    # warm-up (also captures the CUDA graph of one RK4 step)
+    g.z4c_rk4_step(dt, max(3, args.warmup))
+    barrier()
+
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        e0.record(st)
+        g.z4c_rk4_step(dt, args.steps)
+        e1.record(st)
+        barrier()
+    ms = e0.elapsed_time(e1)
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    ms_per_step = ms / args.steps
+    value = cells * args.steps * ws / (ms * 1e-3)
+
+    # live per-kernel timing (CUDA events around each launch on the context's
+    # stream, plain launches of the same kernels) for the roofline
+    prof_steps = 2
+    kms = g.z4c_profile_steps(dt, prof_steps)
+    interior_ms = kms[1] / 4.0  # per launch (4 stages per step)
+    peak64 = z4c.z4c_peak_fma(True, st)
+    peak32 = z4c.z4c_peak_fma(False, st)
+    peaks = measured_peaks()
+    order = workload["order"]
+    if prec == 64 and FP64_FLOPS_PER_CELL_STAGE.get(order):
+        flops = FP64_FLOPS_PER_CELL_STAGE[order] * cells
+        achieved = flops / (interior_ms * 1e-3)
+        roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak64 / 1e12, "unit": "TFLOP/s",
+                "frac": achieved / peak64, "traffic": None,
+                "kernel": "interior_kernel<6,false> (fused RHS + RK stage + enforcement)",
+                "peak_source": "measured DFMA throughput (z4c_peak_fma)",
+                "peak_nominal": NOMINAL_FP64 / 1e12}
+    else:
+        bytes_launch = ALG_BYTES_PER_ZONE_CYCLE / 4 * cells
+        hbm = peaks.get("hbm_gbs", 6800.0)
+        achieved = bytes_launch / (interior_ms * 1e-3) / 1e9
+        roof = {"bound": "alu" if prec == 64 else "hbm", "achieved": achieved, "peak": hbm,
+                "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                "kernel": f"interior_kernel<{order},{'true' if prec == 32 else 'false'}>",
+                "note": "per-cell flop count not yet measured; HBM view shown"}
+    roof["kernel_ms_per_launch"] = interior_ms
+    roof["step_share"] = {"ghost": kms[0] / kms.sum(), "interior": kms[1] / kms.sum(),
+                          "sommerfeld": kms[2] / kms.sum()}
+    roof["fp64_fma_peak_tflops"] = peak64 / 1e12
+    roof["fp32_fma_peak_tflops"] = peak32 / 1e12
+
+    # end to end through the C ABI with pinned host buffers: H2D of the state,
+    # one RK4 step, D2H of the state, every step
+    nbytes = g.state_bytes
+    hin = torch.empty(nbytes // 8, dtype=torch.float64, pin_memory=True)
+    hout = torch.empty(nbytes // 8, dtype=torch.float64, pin_memory=True)
+    hin.numpy()[:] = g.z4c_get_state()
+    g.z4c_evolve_host(hin, hout, dt, 1)
+    e2e_steps = max(2, min(args.steps, 10))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        g.z4c_evolve_host(hin, hout, dt, 1)
+    t1 = time.perf_counter()
+    barrier()
+    e2e = {"value": cells * e2e_steps * ws / (t1 - t0), "unit": UNIT, "h2d_bytes_per_step": nbytes,
+           "d2h_bytes_per_step": nbytes}
+
+    if rank != 0:
+        if ws > 1:
+            torch.distributed.destroy_process_group()
+        return
+    cpu = None
+    if ws == 1 and not args.no_cpu_baseline:
+        r = oracle_sample(workload, args.cpu_steps, 0)
+        cpu = {k: r[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    launches = g.z4c_launches_per_step() * args.steps
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == 64 else "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": workload["name"], "variant": args.variant, "cells": cells,
+                       "blocks": int(len(workload["n"])), "block": list(map(int, workload["n"][0])),
+                       "ghosts": workload["ghosts"], "fd_order": order, "dt": dt,
+                       "l2": f"inputs larger than L2 ({4 * nbytes / 2**30:.2f} GiB of registers "
+                             f"vs {L2_BYTES / 2**20:.0f} MiB L2)",
+                       "parallelism": f"{ws} independent instance(s)"},
+            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,205 @@
+/*
+ * z4c.h -- C ABI of the GB300 (sm_103a) Z4c right-hand-side + RK4 library.
+ *
+ * The library evolves the vacuum Z4c system (paper Sec. 2: Z4c with
+ * Bona-Masso lapse and Gamma-driver shift) on a pack of MeshBlocks
+ * (Sec. 3: a Mesh of rectangular MeshBlocks, each an active region plus a
+ * ghost region; blocks batched into one pack to cut kernel launches) with
+ * cell-centred 4th/6th-order finite differences (Sec. 3.2), Kreiss-Oliger
+ * dissipation and constraint damping (Sec. 4.3), and classic RK4 whose
+ * ghost zones are refilled at every stage (Sec. 3).  Throughput is counted
+ * in zone-cycles per second (Sec. 5).
+ *
+ * Conventions shared by every call
+ *   - 22 evolved fields in this order:
+ *       0 chi, 1..6 gt_xx gt_xy gt_xz gt_yy gt_yz gt_zz, 7 Khat,
+ *       8..13 At_xx At_xy At_xz At_yy At_yz At_zz, 14..16 Gam^x Gam^y Gam^z,
+ *       17 Theta, 18 alpha, 19..21 beta^x beta^y beta^z.
+ *   - A "register" is one full copy of the state in FP64: for each block in
+ *     creation order and each field, an (n_z+2g) x (n_y+2g) x (n_x+2g)
+ *     array with i fastest; blocks are concatenated.  z4c_state_bytes()
+ *     gives its size.
+ *   - Every device buffer (registers, scratch, outputs) is allocated and
+ *     owned by the caller; the library never allocates device memory.  The
+ *     library owns only host-side descriptors and CUDA graphs.
+ *   - All GPU work is enqueued on the stream given to z4c_bind().  Calls
+ *     return after enqueueing unless stated otherwise.
+ *   - Every call returns a z4c_status (0 = success, negative = error);
+ *     nothing throws across the ABI.  z4c_last_error() describes the last
+ *     failure of a context.
+ */
+#ifndef Z4C_GB300_H
+#define Z4C_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define Z4C_NFIELDS 22
+
+typedef enum z4c_status {
+  Z4C_OK = 0,
+  Z4C_ERR_BAD_ARG = -1,      /* null pointer, out-of-range index, bad size */
+  Z4C_ERR_BAD_MESH = -2,     /* blocks overlap, leave the mesh, or leave gaps */
+  Z4C_ERR_UNSUPPORTED = -3,  /* order not 4/6, ghosts < order/2 + 1, odd storage extent */
+  Z4C_ERR_CUDA = -4,         /* a CUDA runtime call failed */
+  Z4C_ERR_TIMEOUT = -5,      /* a bounded device-side wait gave up */
+  Z4C_ERR_NAN = -6,          /* a constraint norm came out NaN */
+  Z4C_ERR_NOT_BOUND = -7     /* z4c_bind() has not been called */
+} z4c_status;
+
+/* Mesh (Sec. 3): the physical domain [lo, hi].  periodic = 1 wraps every
+ * direction; periodic = 0 uses the Sommerfeld outer boundary (outer_bc = 1):
+ * each ghost cell whose centre lies outside the domain evolves
+ * d_t u = -(x^k d_k u + u - u_inf)/r with 2nd-order one-sided differences. */
+typedef struct z4c_mesh {
+  double lo[3];
+  double hi[3];
+  int32_t periodic;
+  int32_t outer_bc;
+} z4c_mesh;
+
+/* One MeshBlock (Sec. 3): n interior cells per direction, lower corner lo of
+ * the active region, cubic cell spacing h.  level and instance are reserved
+ * for refinement levels and independent problems (must be 0 here). */
+typedef struct z4c_block {
+  int32_t level;
+  int32_t n[3];
+  double lo[3];
+  double h;
+  int32_t instance;
+  int32_t reserved;
+} z4c_block;
+
+/* Physical and numerical parameters (Sec. 2, Sec. 4.3).
+ *   ko_sigma      Kreiss-Oliger strength sigma (0.5 or 0.02 in the paper)
+ *   kappa1/2      Z4c constraint damping (kappa1 = 0.02, kappa2 = 0)
+ *   eta           Gamma-driver damping
+ *   chi_floor     floor applied to chi wherever 1/chi appears
+ *   cfl           Courant factor, informational (callers pass dt)
+ *   lapse         0 harmonic (d_t alpha = -alpha^2 Khat), 1 1+log (-2 alpha Khat)
+ *   shift         0 frozen (d_t beta = 0), 1 Gamma-driver (Gam - eta beta)
+ *   rhs_precision 64: everything FP64; 32: stencils and RHS algebra in FP32,
+ *                 state, RK accumulation, 1/chi, constraint enforcement and
+ *                 constraint norms in FP64 */
+typedef struct z4c_params {
+  double ko_sigma;
+  double kappa1;
+  double kappa2;
+  double eta;
+  double chi_floor;
+  double cfl;
+  int32_t lapse;
+  int32_t shift;
+  int32_t rhs_precision;
+  int32_t reserved;
+} z4c_params;
+
+typedef struct z4c_ctx z4c_ctx;
+
+/* Register indices for z4c_fill_ghosts / z4c_rhs / z4c_get_state. */
+#define Z4C_REG_U0 0     /* evolved state */
+#define Z4C_REG_STAGE_A 1
+#define Z4C_REG_STAGE_B 2
+#define Z4C_REG_ACC 3
+
+/* Initial-data kinds for z4c_set_initial_data. */
+#define Z4C_ID_FLAT 0
+#define Z4C_ID_GAUGE_WAVE 1        /* params {A, d, t}: H = 1 - A sin(2 pi (x - t)/d) */
+#define Z4C_ID_LINEAR_WAVE 2       /* params {A, d, t}: gamma_yy,zz = 1 +- A sin(2 pi (x - t)/d) */
+#define Z4C_ID_SCHWARZSCHILD 3     /* params {M, lapse_kind}: isotropic; 0 alpha = psi^-2, 1 static */
+#define Z4C_ID_BRILL_LINDQUIST 4   /* params {np, m_1, x_1, y_1, z_1, ...}, alpha = psi^-2 */
+
+/* Create a context for one pack of blocks on one mesh (Sec. 3).
+ * blocks: nblocks entries (host memory, copied).  ghosts >= fd_order/2 + 1,
+ * fd_order 4 or 6, every storage extent n+2*ghosts even.  Blocks must tile
+ * the mesh exactly with equal n along shared faces.  Makes no CUDA call.
+ * On success *out owns the context (release with z4c_destroy). */
+int z4c_create(const z4c_mesh *mesh, const z4c_block *blocks, int nblocks, int ghosts,
+               int fd_order, const z4c_params *params, z4c_ctx **out);
+
+/* Bytes of one FP64 register (see conventions). */
+int z4c_state_bytes(const z4c_ctx *ctx, size_t *bytes_per_register);
+
+/* Bytes of device scratch the context needs: descriptor tables, work lists,
+ * FP32 shadow copies (rhs_precision 32) and reduction partials. */
+int z4c_scratch_bytes(const z4c_ctx *ctx, size_t *bytes);
+
+/* Attach caller-owned device buffers and the CUDA stream (cudaStream_t
+ * passed as void*; a non-default stream enables CUDA-graph replay in
+ * z4c_rk4_step).  u0, stage_a, stage_b, acc: z4c_state_bytes() each, 256-byte
+ * aligned.  scratch: z4c_scratch_bytes(), 256-byte aligned.  Uploads the
+ * descriptor tables into scratch (asynchronously on the stream). */
+int z4c_bind(z4c_ctx *ctx, void *u0, void *stage_a, void *stage_b, void *acc, void *scratch,
+             void *cuda_stream);
+
+/* Analytic initial data of the given kind into every storage cell of U0. */
+int z4c_set_initial_data(z4c_ctx *ctx, int kind, const double *params, int nparams);
+
+/* Fill the ghost cells of register reg from neighbouring blocks' active
+ * cells (same level) or by periodic wrap (Sec. 3).  Sommerfeld cells are
+ * evolved, never overwritten. */
+int z4c_fill_ghosts(z4c_ctx *ctx, int reg);
+
+/* Raw right-hand side of register reg (ghosts must be filled) into rhs_out
+ * (device, z4c_state_bytes(), FP64, same layout).  Interior and Sommerfeld
+ * cells are written, other ghost cells set to 0. */
+int z4c_rhs(z4c_ctx *ctx, int reg, void *rhs_out);
+
+/* nsteps classic RK4 steps of size dt on U0 (Sec. 3, Sec. 4.3): per stage,
+ * ghost fill, then one fused kernel computing the RHS and the stage update
+ * with det gt = 1 / tr At = 0 enforcement.  On a non-default stream the
+ * step is captured once into a CUDA graph and replayed. */
+int z4c_rk4_step(z4c_ctx *ctx, double dt, int nsteps);
+
+/* Hamiltonian and momentum constraints of U0 (ghosts are filled first).
+ * norms (host, 6 doubles): ||H||_2, ||M||_2, max|H|, ||H||_2 and ||M||_2
+ * over cells with r > r_mask, max|M|; ||X||_2 = sqrt(sum X^2 h^3 / sum h^3)
+ * over interior cells.  per_cell_out (device, nullable): 4 values per
+ * storage cell (H, M^x, M^y, M^z) laid out like a 4-field register.
+ * Synchronises the stream.  Returns Z4C_ERR_NAN if a norm is NaN. */
+int z4c_constraints(z4c_ctx *ctx, double r_mask, double *norms, void *per_cell_out);
+
+/* Copy register reg to / from host memory (bytes = z4c_state_bytes()).
+ * Synchronous.  Pinned host memory makes the copy faster. */
+int z4c_get_state(z4c_ctx *ctx, int reg, void *host, size_t bytes);
+int z4c_set_state(z4c_ctx *ctx, int reg, const void *host, size_t bytes);
+
+/* End-to-end call on host buffers: copy host_in into U0, run nsteps RK4
+ * steps, copy U0 into host_out; synchronous. */
+int z4c_evolve_host(z4c_ctx *ctx, const void *host_in, void *host_out, size_t bytes, double dt,
+                    int nsteps);
+
+/* Wait for the stream; reports any CUDA error. */
+int z4c_sync(z4c_ctx *ctx);
+
+/* Measurement aid: run nsteps RK4 steps with plain (not graph) launches,
+ * each bracketed by CUDA events on the context's stream, and return the
+ * average milliseconds per step spent in each kernel kind:
+ * ms[0] ghost fill, ms[1] fused interior RHS + stage update, ms[2]
+ * Sommerfeld cells.  Advances U0 exactly like z4c_rk4_step.  Synchronous. */
+int z4c_profile_steps(z4c_ctx *ctx, double dt, int nsteps, double *ms);
+
+/* Measurement aid: FP64 (fp64 = 1) or FP32 (fp64 = 0) fused multiply-add
+ * throughput of the current device in FLOP/s, from independent FMA chains
+ * with no memory traffic (the ALU roofline of the RHS kernels).  Enqueued on
+ * cuda_stream and synchronised.  Allocates nothing. */
+int z4c_peak_fma(int fp64, void *cuda_stream, double *flops_per_s);
+
+/* Number of kernel launches one RK4 step enqueues. */
+int z4c_launches_per_step(const z4c_ctx *ctx);
+
+/* Text of the last error of ctx (never NULL; "" when none). */
+const char *z4c_last_error(const z4c_ctx *ctx);
+
+/* Release the context (not the caller's buffers). */
+void z4c_destroy(z4c_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* Z4C_GB300_H */

@@ -1,0 +1,103 @@
+// Internal definitions shared by the translation units of the CUDA library.
+// Not part of the C ABI (include/z4c.h is).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace z4c {
+
+constexpr int NF = 22;
+enum Field {
+  CHI = 0, GXX, GXY, GXZ, GYY, GYZ, GZZ, KHAT, AXX, AXY, AXZ, AYY, AYZ, AZZ,
+  GAMX, GAMY, GAMZ, THETA, ALPHA, BETAX, BETAY, BETAZ
+};
+
+// Symmetric 3x3 index -> component 0..5 (xx xy xz yy yz zz).
+__host__ __device__ constexpr int S6(int i, int j) {
+  return i == j ? (i == 0 ? 0 : (i == 1 ? 3 : 5))
+                : ((i + j) == 1 ? 1 : ((i + j) == 2 ? 2 : 4));
+}
+
+// Per-block descriptor, resident in device memory (caller scratch).
+struct DevBlock {
+  int32_t n[3];   // interior cells
+  int32_t e[3];   // storage extents n + 2g
+  int32_t g;      // ghost width
+  int32_t order;  // 4 or 6
+  int32_t S;      // cells per field = e0 e1 e2
+  int32_t pad;
+  int64_t off;    // element offset of the block's field 0 within a register
+  double lo[3];   // lower corner of the active region
+  double h;       // spacing
+  // finite-difference scale factors (1 / (denominator * h^p)); FP64 and FP32
+  double s1, s2, smix, slop, sko;
+  float s1f, s2f, smixf, slopf, skof;
+  float hf;
+  // physics parameters of the block's problem instance (Sec. 2, Sec. 4.3)
+  double kappa1, kappa2, eta, chi_floor;
+  int32_t lapse, shift;  // 0 harmonic / 1 one-plus-log; 0 frozen / 1 Gamma-driver
+};
+
+// One interior tile: TX x TY cells of one z-plane of one block.
+struct Tile {
+  int32_t block, i0, j0, k0;  // interior-relative origin
+};
+
+// One storage cell of one block.
+struct CellRef {
+  int32_t block, cidx;
+};
+
+// One same-level ghost copy: dst cell <- src cell, all fields.
+struct GhostCopy {
+  int32_t dst_block, dst_cidx, src_block, src_cidx;
+};
+
+// Which update the stage kernel applies after computing k = RHS(x):
+//   MODE_RHS:  rhs_out = k
+//   MODE_S1:   acc = u0 + cb k;  next = enforce(u0 + ca k)
+//   MODE_S23:  acc = acc + cb k; next = enforce(u0 + ca k)
+//   MODE_S4:   next = enforce(acc + cb k)
+enum StageMode { MODE_RHS = 0, MODE_S1 = 1, MODE_S23 = 2, MODE_S4 = 3 };
+
+struct StageArgs {
+  const DevBlock *blocks;
+  const double *x64;  // stage state (FP64): stencil source in FP64 mode, chi source in FP32 mode
+  const float *x32;   // FP32 shadow of the stage state (FP32 mode)
+  const double *u0;
+  double *acc;
+  double *next;       // next stage state (FP64)
+  float *next32;      // FP32 shadow of the next stage state (FP32 mode)
+  double *rhs_out;    // MODE_RHS output
+  double ca, cb;
+  int32_t mode;
+  int32_t next_full;  // FP32 mode: 1 = write every field of next in FP64, 0 = chi only
+};
+
+// Interior tile shape of the RHS kernels.
+constexpr int TX = 16;
+constexpr int TY = 8;
+
+// ---- launchers (defined in the kernel translation units) ----
+cudaError_t launch_interior_f64(int order, const StageArgs &a, const Tile *tiles, int ntiles,
+                                cudaStream_t st);
+cudaError_t launch_interior_f32(int order, const StageArgs &a, const Tile *tiles, int ntiles,
+                                cudaStream_t st);
+cudaError_t launch_sommerfeld(bool f32, const StageArgs &a, const CellRef *cells, int ncells,
+                              cudaStream_t st);
+cudaError_t launch_ghosts_f64(double *reg, const DevBlock *blocks, const GhostCopy *list, int n,
+                              cudaStream_t st);
+cudaError_t launch_ghosts_f32(float *reg, const DevBlock *blocks, const GhostCopy *list, int n,
+                              cudaStream_t st);
+cudaError_t launch_initial_data(double *u0, const DevBlock *blocks, int nblocks, int max_S, int kind,
+                                const double *par, int npar, cudaStream_t st);
+cudaError_t launch_to_shadow(const double *src, float *dst, const DevBlock *blocks, int nblocks,
+                             int max_S, cudaStream_t st);
+cudaError_t launch_constraints(int order, const double *u0, const DevBlock *blocks,
+                               const Tile *tiles, int ntiles, double r_mask, double *per_cell,
+                               double *partials, double *result, cudaStream_t st);
+
+cudaError_t peak_fma(bool f64, cudaStream_t st, double *flops_per_s);
+
+}  // namespace z4c

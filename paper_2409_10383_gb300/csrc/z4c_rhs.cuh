@@ -1,0 +1,635 @@
+// Device-side finite differences and the Z4c right-hand side at one cell.
+//
+// Paper Sec. 2: vacuum Z4c with Bona-Masso lapse and Gamma-driver shift (the
+// continuum equations are those of GR-Athena++, which the paper adopts
+// unchanged); Sec. 3.2: cell-centred finite differences; Sec. 4.3:
+// Kreiss-Oliger dissipation and kappa1/kappa2 constraint damping.
+//
+// Templated on the differencing order (4 or 6) and on the arithmetic type R
+// of the stencils and algebra (double, or float for the FP32-RHS variant).
+// Every stencil is evaluated as a sum over symmetric / antisymmetric pairs
+// with small integer weights (exact in either precision), followed by one
+// multiply with a per-block scale 1/(denominator h^p): this is the fewest
+// FP64 operations per derivative on a part whose FP64 pipe is the bound.
+#pragma once
+
+#include "z4c_internal.cuh"
+
+namespace z4c {
+
+template <class R>
+__device__ __forceinline__ R ldg_(const R *p) {
+  return __ldg(p);
+}
+
+// Stencil source: field f of the centre cell is at base[f * S].  Offsets
+// are in elements.  For the FP32 shadow the diagonal of gt is stored minus
+// one, so centre values add it back.
+template <class R, bool SHIFTED_DIAG>
+struct Src {
+  const R *__restrict__ base;
+  int32_t S;
+  __device__ __forceinline__ R at(int f, int off) const { return ldg_(base + f * S + off); }
+  __device__ __forceinline__ R val(int f) const {
+    R v = at(f, 0);
+    if (SHIFTED_DIAG && (f == GXX || f == GYY || f == GZZ)) v += R(1);
+    return v;
+  }
+};
+
+template <int ORD>
+struct FD;
+
+// 4th order: d1 = (8 (f1 - f-1) - (f2 - f-2)) / 12h
+//            d2 = (16 (f1 + f-1) - (f2 + f-2) - 30 f0) / 12h^2
+//            lopsided (beta > 0), offsets -1..3: (-3, -10, 18, -6, 1) / 12h
+//            KO: N = 3, (+1) sigma / (64 h) * (1 -6 15 -20 15 -6 1)
+template <>
+struct FD<4> {
+  static constexpr int W = 2;
+  template <class S_>
+  __device__ static auto d1(const S_ &s, int f, int st) {
+    auto a = s.at(f, st) - s.at(f, -st);
+    auto b = s.at(f, 2 * st) - s.at(f, -2 * st);
+    return fma(a, decltype(a)(8), -b);
+  }
+  template <class S_>
+  __device__ static auto d2(const S_ &s, int f, int st) {
+    auto c = s.at(f, 0);
+    auto a = s.at(f, st) + s.at(f, -st);
+    auto b = s.at(f, 2 * st) + s.at(f, -2 * st);
+    return fma(a, decltype(a)(16), fma(c, decltype(c)(-30), -b));
+  }
+  template <class S_>
+  __device__ static auto mix(const S_ &s, int f, int sa, int sb) {
+    // sum_{a,b=1..2} c_a c_b [(f(a,b) - f(-a,b)) - (f(a,-b) - f(-a,-b))], c = (8, -1)
+    auto q = [&](int a, int b) {
+      return (s.at(f, a * sa + b * sb) - s.at(f, -a * sa + b * sb)) -
+             (s.at(f, a * sa - b * sb) - s.at(f, -a * sa - b * sb));
+    };
+    auto q11 = q(1, 1), q12 = q(1, 2), q21 = q(2, 1), q22 = q(2, 2);
+    using R = decltype(q11);
+    return fma(q11, R(64), fma(q12 + q21, R(-8), q22));
+  }
+  // upwind-signed stride: sst = +st for beta >= 0, -st otherwise; result
+  // times sign(beta) is the lopsided derivative
+  template <class S_>
+  __device__ static auto lop(const S_ &s, int f, int sst) {
+    auto fm1 = s.at(f, -sst), f0 = s.at(f, 0), f1 = s.at(f, sst), f2 = s.at(f, 2 * sst),
+         f3 = s.at(f, 3 * sst);
+    using R = decltype(f0);
+    return fma(fm1, R(-3), fma(f0, R(-10), fma(f1, R(18), fma(f2, R(-6), f3))));
+  }
+  // sum over the three directions of the 6th undivided difference
+  template <class S_>
+  __device__ static auto ko3(const S_ &s, int f, int sx, int sy, int sz) {
+    auto c = s.at(f, 0);
+    using R = decltype(c);
+    R p1 = (s.at(f, sx) + s.at(f, -sx)) + (s.at(f, sy) + s.at(f, -sy)) + (s.at(f, sz) + s.at(f, -sz));
+    R p2 = (s.at(f, 2 * sx) + s.at(f, -2 * sx)) + (s.at(f, 2 * sy) + s.at(f, -2 * sy)) +
+           (s.at(f, 2 * sz) + s.at(f, -2 * sz));
+    R p3 = (s.at(f, 3 * sx) + s.at(f, -3 * sx)) + (s.at(f, 3 * sy) + s.at(f, -3 * sy)) +
+           (s.at(f, 3 * sz) + s.at(f, -3 * sz));
+    return fma(c, R(-60), fma(p1, R(15), fma(p2, R(-6), p3)));
+  }
+};
+
+// 6th order: d1 = (45 (f1 - f-1) - 9 (f2 - f-2) + (f3 - f-3)) / 60h
+//            d2 = (270 (f1 + f-1) - 27 (f2 + f-2) + 2 (f3 + f-3) - 490 f0) / 180h^2
+//            lopsided (beta > 0), offsets -2..4: (2, -24, -35, 80, -30, 8, -1) / 60h
+//            KO: N = 4, (-1) sigma / (256 h) * (1 -8 28 -56 70 -56 28 -8 1)
+template <>
+struct FD<6> {
+  static constexpr int W = 3;
+  template <class S_>
+  __device__ static auto d1(const S_ &s, int f, int st) {
+    auto a = s.at(f, st) - s.at(f, -st);
+    auto b = s.at(f, 2 * st) - s.at(f, -2 * st);
+    auto c = s.at(f, 3 * st) - s.at(f, -3 * st);
+    using R = decltype(a);
+    return fma(a, R(45), fma(b, R(-9), c));
+  }
+  template <class S_>
+  __device__ static auto d2(const S_ &s, int f, int st) {
+    auto c0 = s.at(f, 0);
+    auto a = s.at(f, st) + s.at(f, -st);
+    auto b = s.at(f, 2 * st) + s.at(f, -2 * st);
+    auto c = s.at(f, 3 * st) + s.at(f, -3 * st);
+    using R = decltype(a);
+    return fma(a, R(270), fma(b, R(-27), fma(c, R(2), c0 * R(-490))));
+  }
+  template <class S_>
+  __device__ static auto mix(const S_ &s, int f, int sa, int sb) {
+    auto q = [&](int a, int b) {
+      return (s.at(f, a * sa + b * sb) - s.at(f, -a * sa + b * sb)) -
+             (s.at(f, a * sa - b * sb) - s.at(f, -a * sa - b * sb));
+    };
+    auto q11 = q(1, 1), q12 = q(1, 2), q13 = q(1, 3);
+    auto q21 = q(2, 1), q22 = q(2, 2), q23 = q(2, 3);
+    auto q31 = q(3, 1), q32 = q(3, 2), q33 = q(3, 3);
+    using R = decltype(q11);
+    // c = (45, -9, 1): weights c_a c_b
+    R r = q11 * R(2025);
+    r = fma(q12 + q21, R(-405), r);
+    r = fma(q13 + q31, R(45), r);
+    r = fma(q22, R(81), r);
+    r = fma(q23 + q32, R(-9), r);
+    return r + q33;
+  }
+  template <class S_>
+  __device__ static auto lop(const S_ &s, int f, int sst) {
+    auto fm2 = s.at(f, -2 * sst), fm1 = s.at(f, -sst), f0 = s.at(f, 0), f1 = s.at(f, sst),
+         f2 = s.at(f, 2 * sst), f3 = s.at(f, 3 * sst), f4 = s.at(f, 4 * sst);
+    using R = decltype(f0);
+    return fma(fm2, R(2), fma(fm1, R(-24), fma(f0, R(-35), fma(f1, R(80),
+               fma(f2, R(-30), fma(f3, R(8), -f4))))));
+  }
+  template <class S_>
+  __device__ static auto ko3(const S_ &s, int f, int sx, int sy, int sz) {
+    auto c = s.at(f, 0);
+    using R = decltype(c);
+    R p[4];
+#pragma unroll
+    for (int m = 1; m <= 4; ++m)
+      p[m - 1] = (s.at(f, m * sx) + s.at(f, -m * sx)) + (s.at(f, m * sy) + s.at(f, -m * sy)) +
+                 (s.at(f, m * sz) + s.at(f, -m * sz));
+    return fma(c, R(210), fma(p[0], R(-56), fma(p[1], R(28), fma(p[2], R(-8), p[3]))));
+  }
+};
+
+// Scale factors of one block in precision R.
+template <class R>
+struct Scales {
+  R s1, s2, smix, slop, sko;
+};
+__device__ __forceinline__ Scales<double> scales_of(const DevBlock &b, double) {
+  return {b.s1, b.s2, b.smix, b.slop, b.sko};
+}
+__device__ __forceinline__ Scales<float> scales_of(const DevBlock &b, float) {
+  return {b.s1f, b.s2f, b.smixf, b.slopf, b.skof};
+}
+
+template <class R>
+struct Phys {
+  R kappa1, kappa2, eta;
+  int lapse, shift;
+};
+
+template <class R>
+__device__ __forceinline__ R trsym(const R gi[6], const R X[6]) {  // gt^ij X_ij
+  return gi[0] * X[0] + gi[3] * X[3] + gi[5] * X[5] + R(2) * (gi[1] * X[1] + gi[2] * X[2] + gi[4] * X[4]);
+}
+template <class R>
+__device__ __forceinline__ R quad(const R gi[6], const R a[3], const R b[3]) {  // gt^lm a_l b_m
+  return gi[0] * a[0] * b[0] + gi[3] * a[1] * b[1] + gi[5] * a[2] * b[2] +
+         gi[1] * (a[0] * b[1] + a[1] * b[0]) + gi[2] * (a[0] * b[2] + a[2] * b[0]) +
+         gi[4] * (a[1] * b[2] + a[2] * b[1]);
+}
+
+// gt^ij = adj(gt) / det(gt)
+template <class R>
+__device__ __forceinline__ void inverse_metric(const R g[6], R gi[6]) {
+  R axx = g[3] * g[5] - g[4] * g[4];
+  R axy = g[2] * g[4] - g[1] * g[5];
+  R axz = g[1] * g[4] - g[2] * g[3];
+  R ayy = g[0] * g[5] - g[2] * g[2];
+  R ayz = g[1] * g[2] - g[0] * g[4];
+  R azz = g[0] * g[3] - g[1] * g[1];
+  R idet = R(1) / (g[0] * axx + g[1] * axy + g[2] * axz);
+  gi[0] = axx * idet; gi[1] = axy * idet; gi[2] = axz * idet;
+  gi[3] = ayy * idet; gi[4] = ayz * idet; gi[5] = azz * idet;
+}
+
+// Gl[i][jk] = Gt_ijk = (d_j gt_ik + d_k gt_ij - d_i gt_jk)/2, Gu[i][jk] = Gt^i_jk,
+// Gd^i = gt^jk Gt^i_jk.  dg[d][q] = d_d gt_q.
+template <class R>
+__device__ __forceinline__ void christoffel(const R gi[6], const R dg[3][6], R Gl[3][6], R Gu[3][6],
+                                            R Gd[3]) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+      for (int k2 = j; k2 < 3; ++k2)
+        Gl[i][S6(j, k2)] = R(0.5) * (dg[j][S6(i, k2)] + dg[k2][S6(i, j)] - dg[i][S6(j, k2)]);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int q = 0; q < 6; ++q)
+      Gu[i][q] = gi[S6(i, 0)] * Gl[0][q] + gi[S6(i, 1)] * Gl[1][q] + gi[S6(i, 2)] * Gl[2][q];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) Gd[i] = trsym(gi, Gu[i]);
+}
+
+// Ricci tensor R_ij = Rt_ij + Rchi_ij of the physical metric gt_ij / chi:
+//   Rt_ij   = -1/2 gt^lm d_l d_m gt_ij + gt_k(i d_j) Gam^k + Gd^k Gt_(ij)k
+//             + gt^lm (2 Gt^k_l(i Gt_j)km + Gt^k_im Gt_klj)
+//   Rchi_ij = (DDchi_ij + gt_ij gt^lm DDchi_lm) / (2 chi)
+//             - (d_i chi d_j chi + 3 gt_ij gt^lm d_l chi d_m chi) / (4 chi^2)
+// with DDchi_ij = d_i d_j chi - Gt^k_ij d_k chi and 1/chi -> ichi.
+template <int ORD, class R, class SRC>
+__device__ __forceinline__ void ricci(const SRC &s, const int st[3], const Scales<R> &sc, R ichi,
+                                      const R g[6], const R gi[6], const R dchi[3],
+                                      const R dGam[3][3], const R Gl[3][6], const R Gu[3][6],
+                                      const R Gd[3], const R DDchi[6], R Ric[6]) {
+  using F = FD<ORD>;
+  // U[k][m][i] = gt^lm Gt^k_li ; V[k][m][j] = gt^lm Gt_klj
+  R U[3][3][3], V[3][3][3];
+#pragma unroll
+  for (int k2 = 0; k2 < 3; ++k2)
+#pragma unroll
+    for (int m = 0; m < 3; ++m)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        U[k2][m][i] = gi[S6(0, m)] * Gu[k2][S6(0, i)] + gi[S6(1, m)] * Gu[k2][S6(1, i)] +
+                      gi[S6(2, m)] * Gu[k2][S6(2, i)];
+        V[k2][m][i] = gi[S6(0, m)] * Gl[k2][S6(0, i)] + gi[S6(1, m)] * Gl[k2][S6(1, i)] +
+                      gi[S6(2, m)] * Gl[k2][S6(2, i)];
+      }
+  const R trDDchi = trsym(gi, DDchi);
+  const R dchi2 = quad(gi, dchi, dchi);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = i; j < 3; ++j) {
+      const int q = S6(i, j);
+      R dd[6];
+      dd[0] = F::d2(s, GXX + q, st[0]) * sc.s2;
+      dd[3] = F::d2(s, GXX + q, st[1]) * sc.s2;
+      dd[5] = F::d2(s, GXX + q, st[2]) * sc.s2;
+      dd[1] = F::mix(s, GXX + q, st[0], st[1]) * sc.smix;
+      dd[2] = F::mix(s, GXX + q, st[0], st[2]) * sc.smix;
+      dd[4] = F::mix(s, GXX + q, st[1], st[2]) * sc.smix;
+      R r = R(-0.5) * trsym(gi, dd);
+      R t = R(0);
+#pragma unroll
+      for (int k2 = 0; k2 < 3; ++k2) t += g[S6(k2, i)] * dGam[j][k2] + g[S6(k2, j)] * dGam[i][k2];
+      r += R(0.5) * t;
+      t = R(0);
+#pragma unroll
+      for (int k2 = 0; k2 < 3; ++k2) t += Gd[k2] * (Gl[i][S6(j, k2)] + Gl[j][S6(i, k2)]);
+      r += R(0.5) * t;
+      t = R(0);
+#pragma unroll
+      for (int k2 = 0; k2 < 3; ++k2)
+#pragma unroll
+        for (int m = 0; m < 3; ++m)
+          t += U[k2][m][i] * Gl[j][S6(k2, m)] + U[k2][m][j] * Gl[i][S6(k2, m)] +
+               Gu[k2][S6(i, m)] * V[k2][m][j];
+      r += t;
+      R rc = R(0.5) * ichi * (DDchi[q] + g[q] * trDDchi) -
+             R(0.25) * ichi * ichi * (dchi[i] * dchi[j] + R(3) * g[q] * dchi2);
+      Ric[q] = r + rc;
+    }
+}
+
+// Z4c right-hand side at one interior cell.  ichi = 1 / max(chi, chi_floor)
+// (computed by the caller in FP64).  st = element strides (1, e0, e0 e1).
+template <int ORD, class R, class SRC>
+__device__ __forceinline__ void rhs_point(const SRC &s, const int st[3], const Scales<R> &sc,
+                                          const Phys<R> &p, R ichi, R k[NF]) {
+  using F = FD<ORD>;
+  const R chi = s.val(CHI), Khat = s.val(KHAT), Theta = s.val(THETA), al = s.val(ALPHA);
+  R g[6], A[6], Gam[3], beta[3];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    g[q] = s.val(GXX + q);
+    A[q] = s.val(AXX + q);
+  }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    Gam[i] = s.val(GAMX + i);
+    beta[i] = s.val(BETAX + i);
+  }
+  R gi[6];
+  inverse_metric(g, gi);
+
+  // first derivatives
+  R dchi[3], dal[3], dKhat[3], dTheta[3], dbeta[3][3], dGam[3][3], dg[3][6];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    dchi[d] = F::d1(s, CHI, st[d]) * sc.s1;
+    dal[d] = F::d1(s, ALPHA, st[d]) * sc.s1;
+    dKhat[d] = F::d1(s, KHAT, st[d]) * sc.s1;
+    dTheta[d] = F::d1(s, THETA, st[d]) * sc.s1;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      dbeta[d][i] = F::d1(s, BETAX + i, st[d]) * sc.s1;
+      dGam[d][i] = F::d1(s, GAMX + i, st[d]) * sc.s1;
+    }
+#pragma unroll
+    for (int q = 0; q < 6; ++q) dg[d][q] = F::d1(s, GXX + q, st[d]) * sc.s1;
+  }
+
+  R Gl[3][6], Gu[3][6], Gd[3];
+  christoffel(gi, dg, Gl, Gu, Gd);
+
+  // second derivatives of chi and alpha, covariant parts
+  R DDchi[6], DDa0[6];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = i; j < 3; ++j) {
+      const int q = S6(i, j);
+      R ddc, dda;
+      if (i == j) {
+        ddc = F::d2(s, CHI, st[i]) * sc.s2;
+        dda = F::d2(s, ALPHA, st[i]) * sc.s2;
+      } else {
+        ddc = F::mix(s, CHI, st[i], st[j]) * sc.smix;
+        dda = F::mix(s, ALPHA, st[i], st[j]) * sc.smix;
+      }
+      DDchi[q] = ddc - (Gu[0][q] * dchi[0] + Gu[1][q] * dchi[1] + Gu[2][q] * dchi[2]);
+      DDa0[q] = dda - (Gu[0][q] * dal[0] + Gu[1][q] * dal[1] + Gu[2][q] * dal[2]);
+    }
+  auto trsym = [&](const R *X) { return z4c::trsym(gi, X); };
+  auto quad = [&](const R *a, const R *b) { return z4c::quad(gi, a, b); };
+
+  R Ric[6];
+  ricci<ORD>(s, st, sc, ichi, g, gi, dchi, dGam, Gl, Gu, Gd, DDchi, Ric);
+  const R Rs = chi * trsym(Ric);
+
+  // D_i D_j alpha and its trace
+  const R dchi_dal = quad(dchi, dal);
+  R DDa[6];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = i; j < 3; ++j) {
+      const int q = S6(i, j);
+      DDa[q] = DDa0[q] + R(0.5) * ichi * (dchi[i] * dal[j] + dchi[j] * dal[i] - g[q] * dchi_dal);
+    }
+  const R lapl_a = chi * trsym(DDa0) - R(0.5) * dchi_dal;
+
+  // At^ij, At_ij At^ij, At_ik gt^kl At_lj
+  R M[3][3];  // M[i][l] = gt^ik At_kl
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int l = 0; l < 3; ++l)
+      M[i][l] = gi[S6(i, 0)] * A[S6(0, l)] + gi[S6(i, 1)] * A[S6(1, l)] + gi[S6(i, 2)] * A[S6(2, l)];
+  R Au[6], AA2[6];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = i; j < 3; ++j) {
+      const int q = S6(i, j);
+      Au[q] = M[i][0] * gi[S6(0, j)] + M[i][1] * gi[S6(1, j)] + M[i][2] * gi[S6(2, j)];
+      AA2[q] = M[0][i] * A[S6(0, j)] + M[1][i] * A[S6(1, j)] + M[2][i] * A[S6(2, j)];
+    }
+  const R AA = A[0] * Au[0] + A[3] * Au[3] + A[5] * Au[5] + R(2) * (A[1] * Au[1] + A[2] * Au[2] + A[4] * Au[4]);
+
+  const R K = Khat + R(2) * Theta;
+  const R divb = dbeta[0][0] + dbeta[1][1] + dbeta[2][2];
+  const R two3 = R(2) / R(3), third = R(1) / R(3);
+
+  k[CHI] = two3 * chi * (al * K - divb);
+
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = i; j < 3; ++j) {
+      const int q = S6(i, j);
+      R t = R(-2) * al * A[q] - two3 * g[q] * divb;
+#pragma unroll
+      for (int k2 = 0; k2 < 3; ++k2) t += g[S6(i, k2)] * dbeta[j][k2] + g[S6(j, k2)] * dbeta[i][k2];
+      k[GXX + q] = t;
+    }
+
+  k[KHAT] = -lapl_a + al * (AA + third * K * K) + p.kappa1 * (R(1) - p.kappa2) * al * Theta;
+
+  {
+    R X[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) X[q] = al * Ric[q] - DDa[q];
+    const R trX = trsym(X);
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = i; j < 3; ++j) {
+        const int q = S6(i, j);
+        R t = chi * (X[q] - third * g[q] * trX) + al * (K * A[q] - R(2) * AA2[q]) - two3 * A[q] * divb;
+#pragma unroll
+        for (int k2 = 0; k2 < 3; ++k2) t += A[S6(i, k2)] * dbeta[j][k2] + A[S6(j, k2)] * dbeta[i][k2];
+        k[AXX + q] = t;
+      }
+  }
+
+  k[THETA] = R(0.5) * al * (Rs - AA + two3 * K * K) - al * p.kappa1 * (R(2) + p.kappa2) * Theta;
+
+  {
+    // d_j d_k beta^i, and d_j (d_k beta^k)
+    R ddb[3][6];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      ddb[i][0] = F::d2(s, BETAX + i, st[0]) * sc.s2;
+      ddb[i][3] = F::d2(s, BETAX + i, st[1]) * sc.s2;
+      ddb[i][5] = F::d2(s, BETAX + i, st[2]) * sc.s2;
+      ddb[i][1] = F::mix(s, BETAX + i, st[0], st[1]) * sc.smix;
+      ddb[i][2] = F::mix(s, BETAX + i, st[0], st[2]) * sc.smix;
+      ddb[i][4] = F::mix(s, BETAX + i, st[1], st[2]) * sc.smix;
+    }
+    R ddivb[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) ddivb[j] = ddb[0][S6(j, 0)] + ddb[1][S6(j, 1)] + ddb[2][S6(j, 2)];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      R t = trsym(ddb[i]) + two3 * Gd[i] * divb;
+      t -= Gd[0] * dbeta[0][i] + Gd[1] * dbeta[1][i] + Gd[2] * dbeta[2][i];
+      R u = R(0), w = R(0), v = R(0), z = R(0);
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        u += Au[S6(i, j)] * dal[j];
+        w += Au[S6(i, j)] * dchi[j];
+        v += gi[S6(i, j)] * (R(2) * dKhat[j] + dTheta[j]);
+        z += gi[S6(i, j)] * ddivb[j];
+      }
+      R GA = Gu[i][0] * Au[0] + Gu[i][3] * Au[3] + Gu[i][5] * Au[5] +
+             R(2) * (Gu[i][1] * Au[1] + Gu[i][2] * Au[2] + Gu[i][4] * Au[4]);
+      t += third * z - R(2) * u;
+      t += R(2) * al * (GA - R(1.5) * ichi * w - third * v);
+      t -= R(2) * al * p.kappa1 * (Gam[i] - Gd[i]);
+      k[GAMX + i] = t;
+    }
+  }
+
+  k[ALPHA] = p.lapse == 1 ? R(-2) * al * Khat : -al * al * Khat;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) k[BETAX + i] = p.shift ? Gam[i] - p.eta * beta[i] : R(0);
+
+  // lopsided advection along the shift and Kreiss-Oliger dissipation
+  int sst[3];
+  R ab[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    sst[d] = beta[d] >= R(0) ? st[d] : -st[d];
+    ab[d] = fabs(beta[d]) * sc.slop;
+  }
+#pragma unroll 1
+  for (int f = 0; f < NF; ++f) {
+    if (!p.shift && f >= BETAX) continue;
+    R adv = ab[0] * F::lop(s, f, sst[0]);
+    adv = fma(ab[1], F::lop(s, f, sst[1]), adv);
+    adv = fma(ab[2], F::lop(s, f, sst[2]), adv);
+    R ko = F::ko3(s, f, st[0], st[1], st[2]);
+    k[f] += fma(ko, sc.sko, adv);
+  }
+}
+
+// Hamiltonian and momentum constraints at one interior cell (FP64):
+//   H   = R + 2/3 K^2 - At_ij At^ij,   K = Khat + 2 Theta
+//   M^i = d_j At^ij + Gt^i_jk At^jk - 3/2 At^ij d_j chi / chi - 2/3 gt^ij d_j K
+// with d_j At^ij expanded by the product rule and
+// d_k gt^ij = -gt^ia gt^jb d_k gt_ab.
+template <int ORD, class SRC>
+__device__ __forceinline__ void constraints_point(const SRC &s, const int st[3],
+                                                  const Scales<double> &sc, double ichi,
+                                                  double out[4]) {
+  using F = FD<ORD>;
+  using R = double;
+  const R chi = s.val(CHI), K = s.val(KHAT) + 2.0 * s.val(THETA);
+  R g[6], A[6], gi[6];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    g[q] = s.val(GXX + q);
+    A[q] = s.val(AXX + q);
+  }
+  inverse_metric(g, gi);
+  R dchi[3], dK[3], dGam[3][3], dg[3][6], dA[3][6];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    dchi[d] = F::d1(s, CHI, st[d]) * sc.s1;
+    dK[d] = (F::d1(s, KHAT, st[d]) + 2.0 * F::d1(s, THETA, st[d])) * sc.s1;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) dGam[d][i] = F::d1(s, GAMX + i, st[d]) * sc.s1;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      dg[d][q] = F::d1(s, GXX + q, st[d]) * sc.s1;
+      dA[d][q] = F::d1(s, AXX + q, st[d]) * sc.s1;
+    }
+  }
+  R Gl[3][6], Gu[3][6], Gd[3];
+  christoffel(gi, dg, Gl, Gu, Gd);
+  R DDchi[6];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = i; j < 3; ++j) {
+      const int q = S6(i, j);
+      R ddc = i == j ? F::d2(s, CHI, st[i]) * sc.s2 : F::mix(s, CHI, st[i], st[j]) * sc.smix;
+      DDchi[q] = ddc - (Gu[0][q] * dchi[0] + Gu[1][q] * dchi[1] + Gu[2][q] * dchi[2]);
+    }
+  R Ric[6];
+  ricci<ORD>(s, st, sc, ichi, g, gi, dchi, dGam, Gl, Gu, Gd, DDchi, Ric);
+  // At^ij and At_ij At^ij
+  R M[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int l = 0; l < 3; ++l)
+      M[i][l] = gi[S6(i, 0)] * A[S6(0, l)] + gi[S6(i, 1)] * A[S6(1, l)] + gi[S6(i, 2)] * A[S6(2, l)];
+  R Au[6];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = i; j < 3; ++j)
+      Au[S6(i, j)] = M[i][0] * gi[S6(0, j)] + M[i][1] * gi[S6(1, j)] + M[i][2] * gi[S6(2, j)];
+  const R AA = A[0] * Au[0] + A[3] * Au[3] + A[5] * Au[5] +
+               2.0 * (A[1] * Au[1] + A[2] * Au[2] + A[4] * Au[4]);
+  out[0] = chi * trsym(gi, Ric) + 2.0 / 3.0 * K * K - AA;
+  // d_k gt^ij
+  R dgi[3][6];
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = i; j < 3; ++j) {
+        R t = 0.0;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+          for (int b = 0; b < 3; ++b) t += gi[S6(i, a)] * gi[S6(j, b)] * dg[d][S6(a, b)];
+        dgi[d][S6(i, j)] = -t;
+      }
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    R t = 0.0;
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int b = 0; b < 3; ++b)
+          t += (dgi[j][S6(i, a)] * gi[S6(j, b)] + gi[S6(i, a)] * dgi[j][S6(j, b)]) * A[S6(a, b)] +
+               gi[S6(i, a)] * gi[S6(j, b)] * dA[j][S6(a, b)];
+    t += trsym(Au, Gu[i]);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) t -= 1.5 * ichi * Au[S6(i, j)] * dchi[j] + 2.0 / 3.0 * gi[S6(i, j)] * dK[j];
+    out[1 + i] = t;
+  }
+}
+
+// ---- FP64 stage epilogue: RK update and algebraic constraint enforcement ----
+
+// gt <- gt det(gt)^(-1/3); At <- At - gt tr(At)/3 with tr over the new gt^ij.
+__device__ __forceinline__ void enforce(double v[NF]) {
+  double g0 = v[GXX], g1 = v[GXY], g2 = v[GXZ], g3 = v[GYY], g4 = v[GYZ], g5 = v[GZZ];
+  double det = g0 * (g3 * g5 - g4 * g4) + g1 * (g2 * g4 - g1 * g5) + g2 * (g1 * g4 - g2 * g3);
+  double sc = rcbrt(det);
+  g0 *= sc; g1 *= sc; g2 *= sc; g3 *= sc; g4 *= sc; g5 *= sc;
+  // inverse of a unit-determinant matrix is its adjugate
+  double i0 = g3 * g5 - g4 * g4, i1 = g2 * g4 - g1 * g5, i2 = g1 * g4 - g2 * g3;
+  double i3 = g0 * g5 - g2 * g2, i4 = g1 * g2 - g0 * g4, i5 = g0 * g3 - g1 * g1;
+  double idet = 1.0 / (g0 * i0 + g1 * i1 + g2 * i2);
+  double tr = (i0 * v[AXX] + i3 * v[AYY] + i5 * v[AZZ] +
+               2.0 * (i1 * v[AXY] + i2 * v[AXZ] + i4 * v[AYZ])) * idet;
+  double t3 = tr * (1.0 / 3.0);
+  v[GXX] = g0; v[GXY] = g1; v[GXZ] = g2; v[GYY] = g3; v[GYZ] = g4; v[GZZ] = g5;
+  v[AXX] -= g0 * t3; v[AXY] -= g1 * t3; v[AXZ] -= g2 * t3;
+  v[AYY] -= g3 * t3; v[AYZ] -= g4 * t3; v[AZZ] -= g5 * t3;
+}
+
+template <class R>
+__device__ __forceinline__ void stage_epilogue(const StageArgs &a, int64_t off, int32_t S, const R k[NF]) {
+  if (a.mode == MODE_RHS) {
+#pragma unroll
+    for (int f = 0; f < NF; ++f) a.rhs_out[off + (int64_t)f * S] = double(k[f]);
+    return;
+  }
+  double v[NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    const int64_t o = off + (int64_t)f * S;
+    const double kd = double(k[f]);
+    if (a.mode == MODE_S1) {
+      const double u = a.u0[o];
+      a.acc[o] = fma(a.cb, kd, u);
+      v[f] = fma(a.ca, kd, u);
+    } else if (a.mode == MODE_S23) {
+      a.acc[o] = fma(a.cb, kd, a.acc[o]);
+      v[f] = fma(a.ca, kd, a.u0[o]);
+    } else {
+      v[f] = fma(a.cb, kd, a.acc[o]);
+    }
+  }
+  enforce(v);
+  if (a.next32 == nullptr) {
+#pragma unroll
+    for (int f = 0; f < NF; ++f) a.next[off + (int64_t)f * S] = v[f];
+  } else {
+    if (a.next_full) {
+#pragma unroll
+      for (int f = 0; f < NF; ++f) a.next[off + (int64_t)f * S] = v[f];
+    } else {
+      a.next[off] = v[CHI];
+    }
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      const double w = (f == GXX || f == GYY || f == GZZ) ? v[f] - 1.0 : v[f];
+      a.next32[off + (int64_t)f * S] = __double2float_rn(w);
+    }
+  }
+}
+
+}  // namespace z4c

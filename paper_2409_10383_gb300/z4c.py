@@ -1,0 +1,233 @@
+"""Thin ctypes binding of the C ABI in include/z4c.h (same names).
+
+Argument marshalling only: every step of the hot path runs in the CUDA
+library.  If the library is missing this module raises on import of the
+library (no fallback of any kind).  ``Z4c`` allocates the caller-owned
+device buffers with PyTorch and binds them with a dedicated CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+NF = 22
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libz4c_gb300.so")
+
+Z4C_OK, Z4C_ERR_BAD_ARG, Z4C_ERR_BAD_MESH, Z4C_ERR_UNSUPPORTED = 0, -1, -2, -3
+Z4C_ERR_CUDA, Z4C_ERR_TIMEOUT, Z4C_ERR_NAN, Z4C_ERR_NOT_BOUND = -4, -5, -6, -7
+REG_U0, REG_STAGE_A, REG_STAGE_B, REG_ACC = 0, 1, 2, 3
+
+# every entry point declared in include/z4c.h
+EXPORTS = ("z4c_create", "z4c_state_bytes", "z4c_scratch_bytes", "z4c_bind",
+           "z4c_set_initial_data", "z4c_fill_ghosts", "z4c_rhs", "z4c_rk4_step",
+           "z4c_constraints", "z4c_get_state", "z4c_set_state", "z4c_evolve_host",
+           "z4c_sync", "z4c_profile_steps", "z4c_peak_fma", "z4c_launches_per_step",
+           "z4c_last_error", "z4c_destroy")
+
+
+class z4c_mesh(ctypes.Structure):
+    _fields_ = [("lo", ctypes.c_double * 3), ("hi", ctypes.c_double * 3),
+                ("periodic", ctypes.c_int32), ("outer_bc", ctypes.c_int32)]
+
+
+class z4c_block(ctypes.Structure):
+    _fields_ = [("level", ctypes.c_int32), ("n", ctypes.c_int32 * 3), ("lo", ctypes.c_double * 3),
+                ("h", ctypes.c_double), ("instance", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class z4c_params(ctypes.Structure):
+    _fields_ = [("ko_sigma", ctypes.c_double), ("kappa1", ctypes.c_double),
+                ("kappa2", ctypes.c_double), ("eta", ctypes.c_double),
+                ("chi_floor", ctypes.c_double), ("cfl", ctypes.c_double),
+                ("lapse", ctypes.c_int32), ("shift", ctypes.c_int32),
+                ("rhs_precision", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run __graft_entry__.build() "
+                               "(there is no fallback implementation)")
+        L = ctypes.CDLL(LIB_PATH)
+        P, I, D, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+        sig = {
+            "z4c_create": (I, [ctypes.POINTER(z4c_mesh), ctypes.POINTER(z4c_block), I, I, I,
+                               ctypes.POINTER(z4c_params), ctypes.POINTER(P)]),
+            "z4c_state_bytes": (I, [P, ctypes.POINTER(S)]),
+            "z4c_scratch_bytes": (I, [P, ctypes.POINTER(S)]),
+            "z4c_bind": (I, [P, P, P, P, P, P, P]),
+            "z4c_set_initial_data": (I, [P, I, P, I]),
+            "z4c_fill_ghosts": (I, [P, I]),
+            "z4c_rhs": (I, [P, I, P]),
+            "z4c_rk4_step": (I, [P, D, I]),
+            "z4c_constraints": (I, [P, D, P, P]),
+            "z4c_get_state": (I, [P, I, P, S]),
+            "z4c_set_state": (I, [P, I, P, S]),
+            "z4c_evolve_host": (I, [P, P, P, S, D, I]),
+            "z4c_sync": (I, [P]),
+            "z4c_profile_steps": (I, [P, D, I, P]),
+            "z4c_peak_fma": (I, [I, P, P]),
+            "z4c_launches_per_step": (I, [P]),
+            "z4c_last_error": (ctypes.c_char_p, [P]),
+            "z4c_destroy": (None, [P]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype, fn.argtypes = res, args
+        _lib = L
+    return _lib
+
+
+class Z4cError(RuntimeError):
+    pass
+
+
+def _check(rc, ctx=None, what=""):
+    if rc != Z4C_OK:
+        msg = lib().z4c_last_error(ctx).decode() if ctx else ""
+        raise Z4cError(f"{what} failed with status {rc}: {msg}")
+
+
+def z4c_create(mesh: z4c_mesh, blocks, ghosts: int, fd_order: int, params: z4c_params):
+    arr = (z4c_block * len(blocks))(*blocks)
+    out = ctypes.c_void_p()
+    rc = lib().z4c_create(ctypes.byref(mesh), arr, len(blocks), ghosts, fd_order,
+                          ctypes.byref(params), ctypes.byref(out))
+    return rc, out
+
+
+class Z4c:
+    """One context plus its caller-owned device buffers (torch tensors)."""
+
+    def __init__(self, n, lo, h, ghosts, order, dom_lo, dom_hi, periodic, ko_sigma=0.0,
+                 kappa1=0.0, kappa2=0.0, eta=2.0, chi_floor=1e-6, lapse=1, shift=1, precision=64,
+                 device="cuda", stream=None, **_):
+        import torch
+        self.torch = torch
+        n = np.asarray(n).reshape(-1, 3)
+        lo = np.asarray(lo, float).reshape(-1, 3)
+        h = np.broadcast_to(np.asarray(h, float), (len(n),))
+        self.mesh = z4c_mesh()
+        self.mesh.lo[:] = [float(v) for v in dom_lo]
+        self.mesh.hi[:] = [float(v) for v in dom_hi]
+        self.mesh.periodic = int(bool(periodic))
+        self.mesh.outer_bc = 0 if periodic else 1
+        self.blocks = []
+        for b in range(len(n)):
+            B = z4c_block()
+            B.level, B.instance = 0, 0
+            B.n[:] = [int(v) for v in n[b]]
+            B.lo[:] = [float(v) for v in lo[b]]
+            B.h = float(h[b])
+            self.blocks.append(B)
+        self.params = z4c_params(ko_sigma, kappa1, kappa2, eta, chi_floor, 0.25, lapse, shift,
+                                 precision, 0)
+        self.n, self.ghosts, self.order = n, ghosts, order
+        rc, self.ctx = z4c_create(self.mesh, self.blocks, ghosts, order, self.params)
+        _check(rc, None, "z4c_create")
+        sb, sc = ctypes.c_size_t(), ctypes.c_size_t()
+        _check(lib().z4c_state_bytes(self.ctx, ctypes.byref(sb)), self.ctx, "z4c_state_bytes")
+        _check(lib().z4c_scratch_bytes(self.ctx, ctypes.byref(sc)), self.ctx, "z4c_scratch_bytes")
+        self.state_bytes, self.scratch_bytes = sb.value, sc.value
+        self.nelem = self.state_bytes // 8
+        dev = torch.device(device)
+        self.regs = [torch.empty(self.nelem, dtype=torch.float64, device=dev) for _ in range(4)]
+        self.scratch = torch.empty(max(256, self.scratch_bytes), dtype=torch.uint8, device=dev)
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=dev)
+        _check(lib().z4c_bind(self.ctx, *[r.data_ptr() for r in self.regs], self.scratch.data_ptr(),
+                              self.stream.cuda_stream), self.ctx, "z4c_bind")
+
+    @classmethod
+    def from_workload(cls, w: dict, **kw):
+        args = dict(w)
+        args.update(kw)
+        args.setdefault("precision", 64)
+        return cls(**args)
+
+    # --- C ABI calls (same names) ---
+    def z4c_set_initial_data(self, kind, par):
+        p = np.ascontiguousarray(np.asarray(par, dtype=np.float64).reshape(-1))
+        _check(lib().z4c_set_initial_data(self.ctx, int(kind), p.ctypes.data if p.size else None,
+                                          int(p.size)), self.ctx, "z4c_set_initial_data")
+
+    def z4c_fill_ghosts(self, reg=REG_U0):
+        _check(lib().z4c_fill_ghosts(self.ctx, int(reg)), self.ctx, "z4c_fill_ghosts")
+
+    def z4c_rhs(self, reg=REG_U0, out=None):
+        if out is None:
+            out = self.torch.empty(self.nelem, dtype=self.torch.float64, device=self.regs[0].device)
+        _check(lib().z4c_rhs(self.ctx, int(reg), out.data_ptr()), self.ctx, "z4c_rhs")
+        return out
+
+    def z4c_rk4_step(self, dt, nsteps=1):
+        _check(lib().z4c_rk4_step(self.ctx, float(dt), int(nsteps)), self.ctx, "z4c_rk4_step")
+
+    def z4c_constraints(self, r_mask=0.0, per_cell=False):
+        norms = np.zeros(6)
+        pc = None
+        if per_cell:
+            pc = self.torch.empty(self.nelem // NF * 4, dtype=self.torch.float64,
+                                  device=self.regs[0].device)
+        rc = lib().z4c_constraints(self.ctx, float(r_mask), norms.ctypes.data,
+                                   pc.data_ptr() if pc is not None else None)
+        if rc not in (Z4C_OK, Z4C_ERR_NAN):
+            _check(rc, self.ctx, "z4c_constraints")
+        return norms, pc, rc
+
+    def z4c_get_state(self, reg=REG_U0, out: np.ndarray | None = None) -> np.ndarray:
+        if out is None:
+            out = np.empty(self.nelem, dtype=np.float64)
+        _check(lib().z4c_get_state(self.ctx, int(reg), out.ctypes.data, self.state_bytes),
+               self.ctx, "z4c_get_state")
+        return out
+
+    def z4c_set_state(self, host: np.ndarray, reg=REG_U0):
+        host = np.ascontiguousarray(host, dtype=np.float64)
+        _check(lib().z4c_set_state(self.ctx, int(reg), host.ctypes.data, self.state_bytes),
+               self.ctx, "z4c_set_state")
+
+    def z4c_evolve_host(self, host_in, host_out, dt, nsteps):
+        """host_in/host_out: numpy arrays or pinned CPU torch tensors."""
+        pin = host_in.ctypes.data if isinstance(host_in, np.ndarray) else host_in.data_ptr()
+        pout = host_out.ctypes.data if isinstance(host_out, np.ndarray) else host_out.data_ptr()
+        _check(lib().z4c_evolve_host(self.ctx, pin, pout, self.state_bytes, float(dt), int(nsteps)),
+               self.ctx, "z4c_evolve_host")
+
+    def z4c_sync(self):
+        _check(lib().z4c_sync(self.ctx), self.ctx, "z4c_sync")
+
+    def z4c_profile_steps(self, dt, nsteps):
+        ms = np.zeros(3)
+        _check(lib().z4c_profile_steps(self.ctx, float(dt), int(nsteps), ms.ctypes.data), self.ctx,
+               "z4c_profile_steps")
+        return ms
+
+    def z4c_launches_per_step(self) -> int:
+        return int(lib().z4c_launches_per_step(self.ctx))
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            lib().z4c_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def z4c_peak_fma(fp64: bool, stream=None) -> float:
+    """FP64/FP32 FMA throughput of the current GPU in FLOP/s."""
+    out = ctypes.c_double()
+    st = stream.cuda_stream if stream is not None else None
+    _check(lib().z4c_peak_fma(int(bool(fp64)), st, ctypes.byref(out)), None, "z4c_peak_fma")
+    return out.value

@@ -1,0 +1,84 @@
+"""Host-side checks of the C ABI (no GPU needed): the library loads, exports
+every entry point declared in include/z4c.h, and rejects bad arguments with
+the documented status codes without touching the GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2409_10383_gb300 import z4c
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2409_10383_gb300 import build
+    build.build()
+    return z4c.lib()
+
+
+def declared():
+    src = open(os.path.join(ROOT, "include", "z4c.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(z4c_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(L):
+    names = declared()
+    assert len(names) >= 16
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(names) == set(z4c.EXPORTS)
+
+
+def _mesh(per=1):
+    m = z4c.z4c_mesh()
+    m.lo[:] = [-0.5] * 3
+    m.hi[:] = [0.5] * 3
+    m.periodic = per
+    return m
+
+
+def _block(n=32, lo=(-0.5, -0.5, -0.5), h=1 / 32):
+    b = z4c.z4c_block()
+    b.n[:] = [n] * 3
+    b.lo[:] = list(lo)
+    b.h = h
+    return b
+
+
+def _params(prec=64):
+    return z4c.z4c_params(0.02, 0, 0, 0, 1e-6, 0.25, 0, 0, prec, 0)
+
+
+def test_create_validates_arguments(L):
+    ok, ctx = z4c.z4c_create(_mesh(), [_block()], 3, 4, _params())
+    assert ok == 0 and ctx.value
+    L.z4c_destroy(ctx)
+    assert z4c.z4c_create(_mesh(), [_block()], 3, 5, _params())[0] == z4c.Z4C_ERR_UNSUPPORTED
+    assert z4c.z4c_create(_mesh(), [_block()], 2, 4, _params())[0] == z4c.Z4C_ERR_UNSUPPORTED
+    assert z4c.z4c_create(_mesh(), [_block()], 3, 6, _params())[0] == z4c.Z4C_ERR_UNSUPPORTED
+    assert z4c.z4c_create(_mesh(), [_block()], 4, 4, _params(16))[0] == z4c.Z4C_ERR_UNSUPPORTED
+    # block does not tile the mesh
+    assert z4c.z4c_create(_mesh(), [_block(n=16)], 3, 4, _params())[0] == z4c.Z4C_ERR_BAD_MESH
+    # overlapping blocks
+    b = _block(n=16, h=1 / 32)
+    assert z4c.z4c_create(_mesh(), [b] * 8, 3, 4, _params())[0] == z4c.Z4C_ERR_BAD_MESH
+    # off-lattice block
+    assert z4c.z4c_create(_mesh(), [_block(lo=(-0.49, -0.5, -0.5))], 3, 4,
+                          _params())[0] == z4c.Z4C_ERR_BAD_MESH
+
+
+def test_sizes_and_unbound_calls(L):
+    rc, ctx = z4c.z4c_create(_mesh(), [_block()], 3, 4, _params(32))
+    sb, sc = ctypes.c_size_t(), ctypes.c_size_t()
+    assert L.z4c_state_bytes(ctx, ctypes.byref(sb)) == 0
+    assert sb.value == 22 * 38 ** 3 * 8
+    assert L.z4c_scratch_bytes(ctx, ctypes.byref(sc)) == 0
+    assert sc.value >= 2 * 22 * 38 ** 3 * 4  # two FP32 shadows
+    assert L.z4c_rk4_step(ctx, 0.01, 1) == z4c.Z4C_ERR_NOT_BOUND
+    assert b"z4c_bind" in L.z4c_last_error(ctx)
+    assert L.z4c_launches_per_step(ctx) == 8  # periodic: ghost fill + interior per stage
+    L.z4c_destroy(ctx)

@@ -1,0 +1,185 @@
+"""GPU parity: the sm_103a kernels (through the C ABI) against the FP64 oracle.
+
+Tolerances (relative, per field, err_f = max|gpu - oracle| / D_f with
+D_f = max(||oracle_f||_inf, 1e-3 max_g ||oracle_g||_inf)):
+  - FP64 RHS per call:            1e-12
+  - FP64 state after RK4 steps:   1e-10
+  - initial data:                 1e-14 (libm vs CUDA math, a few ulp)
+  - ghost fill:                   bit-exact
+"""
+import numpy as np
+import pytest
+
+import helpers as H
+from paper_2409_10383_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+RHS_TOL = 1e-12
+STEP_TOL = 1e-10
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2409_10383_gb300 import z4c
+    z4c.lib()
+
+
+CASES = [
+    ("gauge_wave", 4, (1, 1, 1), 32, None),            # config-1 mesh
+    ("puncture", 6, (2, 2, 2), 16, None),              # config-2 physics, small
+    ("puncture", 4, (2, 1, 1), (20, 12, 10), None),    # ragged tiles, Sommerfeld
+    ("gauge_wave", 6, (1, 2, 1), (24, 12, 18), None),  # ragged, periodic, two blocks
+]
+
+
+@pytest.mark.parametrize("kind,order,nb,n,per", CASES)
+def test_initial_data_parity(oracle, kind, order, nb, n, per):
+    w = H.small_workload(kind, order, nb, n, per)
+    m = H.oracle_mesh(oracle, w)
+    g = H.gpu_ctx(w)
+    for id_kind, par in [(w["id_kind"], w["id_par"]), (inputs.ID_LINEAR_WAVE, [1e-3, 1.0, 0.2]),
+                         (inputs.ID_BRILL_LINDQUIST, [2, 0.5, 1.1, 0.2, 0.05, 0.7, -1.3, 0.1, 0.3]),
+                         (inputs.ID_SCHWARZSCHILD, [1.0, 1])]:
+        g.z4c_set_initial_data(id_kind, par)
+        got = g.z4c_get_state()
+        ref = m.initial_data(id_kind, par)
+        scale = max(1.0, np.abs(ref).max())
+        assert np.abs(got - ref).max() <= 1e-14 * scale * 10, id_kind
+
+
+@pytest.mark.parametrize("kind,order,nb,n,per", CASES)
+def test_fill_ghosts_bit_exact(oracle, kind, order, nb, n, per):
+    w = H.small_workload(kind, order, nb, n, per)
+    m = H.oracle_mesh(oracle, w)
+    g = H.gpu_ctx(w)
+    u = m.zeros() + inputs.noise(m.size(), 21)
+    g.z4c_set_state(u, reg=2)
+    g.z4c_fill_ghosts(2)
+    got = g.z4c_get_state(2)
+    m.fill_ghosts(u)
+    assert np.array_equal(got, u)
+
+
+def _random_generic_state(m, w, seed):
+    u = m.initial_data(w["id_kind"], w["id_par"])
+    H.perturb(m, u, seed, 1e-3)
+    m.fill_ghosts(u)
+    return u
+
+
+@pytest.mark.parametrize("kind,order,nb,n,per", CASES)
+def test_rhs_parity_fp64(oracle, kind, order, nb, n, per):
+    w = H.small_workload(kind, order, nb, n, per, lapse=1, shift=1, kappa1=0.05, kappa2=0.1,
+                         eta=1.5, ko_sigma=0.3)
+    m = H.oracle_mesh(oracle, w)
+    g = H.gpu_ctx(w)
+    u = _random_generic_state(m, w, seed=5 + order)
+    g.z4c_set_state(u, reg=1)
+    ref = m.rhs(u)
+    got = g.z4c_rhs(1).cpu().numpy()
+    rel, absd = H.field_errors(m, ref, got)
+    assert rel.max() <= RHS_TOL, (rel, absd)
+    # non-evolved ghost cells are zero on both sides
+    for b in range(m.nblocks):
+        ng = ~m.evolved_mask(b)
+        assert np.all(m.blocks(got)[b][:, ng] == 0)
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_flat_space_is_exactly_static(oracle, precision):
+    w = H.small_workload("puncture", 6, (2, 1, 1), 12, id_kind=inputs.ID_FLAT, id_par=[])
+    g = H.gpu_ctx(w, precision)
+    g.z4c_set_initial_data(inputs.ID_FLAT, [])
+    g.z4c_fill_ghosts(0)
+    assert np.all(g.z4c_rhs(0).cpu().numpy() == 0.0)
+    u0 = g.z4c_get_state()
+    g.z4c_rk4_step(0.01, 3)
+    u1 = g.z4c_get_state()
+    m = H.oracle_mesh(oracle, w)
+    for b in range(m.nblocks):
+        ev = m.evolved_mask(b)
+        assert np.array_equal(m.blocks(u0)[b][:, ev], m.blocks(u1)[b][:, ev])
+
+
+def test_gauge_wave_config_ten_steps(oracle):
+    """Gauge wave on one 32^3 block, 3 ghosts, order 4, KO 0.02, harmonic
+    lapse, zero shift, CFL 0.25, 10 RK4 steps: every field within 1e-10."""
+    w = inputs.workload("gauge_wave_32")
+    m = H.oracle_mesh(oracle, w)
+    g = H.gpu_ctx(w)
+    g.z4c_set_initial_data(w["id_kind"], w["id_par"])
+    u = m.initial_data(w["id_kind"], w["id_par"])
+    dt = w["cfl"] * float(w["h"][0])
+    g.z4c_rk4_step(dt, w["steps"])
+    m.rk4(u, dt, w["steps"])
+    rel, absd = H.field_errors(m, u, g.z4c_get_state())
+    assert rel.max() <= STEP_TOL, (rel, absd)
+
+
+@pytest.mark.parametrize("order,nb,n", [(6, (2, 2, 2), 16), (4, (1, 2, 1), (12, 10, 16))])
+def test_puncture_rk4_parity(oracle, order, nb, n):
+    w = H.small_workload("puncture", order, nb, n)
+    m = H.oracle_mesh(oracle, w)
+    g = H.gpu_ctx(w)
+    g.z4c_set_initial_data(w["id_kind"], w["id_par"])
+    u = m.initial_data(w["id_kind"], w["id_par"])
+    dt = 0.25 * float(w["h"][0])
+    g.z4c_rk4_step(dt, 5)
+    m.rk4(u, dt, 5)
+    rel, absd = H.field_errors(m, u, g.z4c_get_state())
+    assert rel.max() <= STEP_TOL, (rel, absd)
+
+
+def test_constraints_parity(oracle):
+    w = H.small_workload("puncture", 6, (2, 2, 2), 16)
+    m = H.oracle_mesh(oracle, w)
+    g = H.gpu_ctx(w)
+    u = _random_generic_state(m, w, seed=9)
+    g.z4c_set_state(u)
+    norms, pc, rc = g.z4c_constraints(r_mask=1.0, per_cell=True)
+    assert rc == 0
+    ref, refpc = m.constraints(u, r_mask=1.0, per_cell=True)
+    assert np.allclose(norms, ref, rtol=1e-10, atol=0), (norms, ref)
+    got = pc.cpu().numpy()
+    scale = np.abs(refpc).max()
+    assert np.abs(got - refpc).max() <= 1e-11 * scale
+
+
+def test_full_size_single_puncture_one_step(oracle):
+    """The benchmark workload at full size (128^3 as 8 blocks of 64^3, 4
+    ghosts, order 6, Sommerfeld, KO 0.5, 1+log, Gamma-driver): one RK4 step
+    through the same CUDA-graph path the benchmark times, every evolved cell
+    against the oracle."""
+    w = inputs.workload("single_puncture_128")
+    m = H.oracle_mesh(oracle, w)
+    g = H.gpu_ctx(w)
+    g.z4c_set_initial_data(w["id_kind"], w["id_par"])
+    u = m.initial_data(w["id_kind"], w["id_par"])
+    dt = w["cfl"] * float(w["h"][0])
+    g.z4c_rk4_step(dt, 1)
+    m.rk4(u, dt, 1)
+    rel, absd = H.field_errors(m, u, g.z4c_get_state())
+    assert rel.max() <= STEP_TOL, (rel, absd)
+
+
+def test_fp32_rhs_error_budget(oracle):
+    """FP32 stencils/algebra against the FP64 oracle, per RHS call and after
+    steps on the puncture problem: bounded by FP32 rounding of the inputs."""
+    w = H.small_workload("puncture", 6, (2, 2, 2), 16)
+    m = H.oracle_mesh(oracle, w)
+    g = H.gpu_ctx(w, precision=32)
+    u = m.initial_data(w["id_kind"], w["id_par"])
+    m.fill_ghosts(u)
+    g.z4c_set_state(u, reg=1)
+    rel, _ = H.field_errors(m, m.rhs(u), g.z4c_rhs(1).cpu().numpy())
+    assert rel.max() < 1e-4, rel
+    g.z4c_set_initial_data(w["id_kind"], w["id_par"])
+    dt = 0.25 * float(w["h"][0])
+    g.z4c_rk4_step(dt, 5)
+    m.rk4(u, dt, 5)
+    rel, _ = H.field_errors(m, u, g.z4c_get_state())
+    assert rel.max() < 1e-4, rel
