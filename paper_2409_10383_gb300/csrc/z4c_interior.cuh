@@ -36,15 +36,4 @@ __global__ void __launch_bounds__(TX * TY) interior_kernel(StageArgs a, const Ti
   stage_epilogue<R>(a, off, b.S, k);
 }
 
-template <bool F32>
-cudaError_t launch_interior(int order, const StageArgs &a, const Tile *tiles, int ntiles, cudaStream_t st) {
-  if (ntiles <= 0) return cudaSuccess;
-  dim3 block(TX, TY);
-  if (order == 4)
-    interior_kernel<4, F32><<<ntiles, block, 0, st>>>(a, tiles);
-  else
-    interior_kernel<6, F32><<<ntiles, block, 0, st>>>(a, tiles);
-  return cudaGetLastError();
-}
-
 }  // namespace z4c

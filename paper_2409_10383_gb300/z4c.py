@@ -152,6 +152,22 @@ class Z4c:
         args.setdefault("precision", 64)
         return cls(**args)
 
+    # --- stream ordering between torch's current stream and the context's ---
+    def _enter(self):
+        """Work queued by torch on its current stream (e.g. writes into an
+        output tensor) must finish before the context's kernels read it."""
+        if self.regs[0].is_cuda:
+            self.stream.wait_stream(self.torch.cuda.current_stream())
+
+    def _leave(self, *tensors):
+        """Results written on the context's stream become visible to torch's
+        current stream (e.g. a following .cpu())."""
+        if self.regs[0].is_cuda:
+            self.torch.cuda.current_stream().wait_stream(self.stream)
+            for t in tensors:
+                if t is not None:
+                    t.record_stream(self.stream)
+
     # --- C ABI calls (same names) ---
     def z4c_set_initial_data(self, kind, par):
         p = np.ascontiguousarray(np.asarray(par, dtype=np.float64).reshape(-1))
@@ -159,16 +175,21 @@ class Z4c:
                                           int(p.size)), self.ctx, "z4c_set_initial_data")
 
     def z4c_fill_ghosts(self, reg=REG_U0):
+        self._enter()
         _check(lib().z4c_fill_ghosts(self.ctx, int(reg)), self.ctx, "z4c_fill_ghosts")
+        self._leave()
 
     def z4c_rhs(self, reg=REG_U0, out=None):
         if out is None:
             out = self.torch.empty(self.nelem, dtype=self.torch.float64, device=self.regs[0].device)
+        self._enter()
         _check(lib().z4c_rhs(self.ctx, int(reg), out.data_ptr()), self.ctx, "z4c_rhs")
+        self._leave(out)
         return out
 
     def z4c_rk4_step(self, dt, nsteps=1):
         _check(lib().z4c_rk4_step(self.ctx, float(dt), int(nsteps)), self.ctx, "z4c_rk4_step")
+        self._leave()
 
     def z4c_constraints(self, r_mask=0.0, per_cell=False):
         norms = np.zeros(6)
@@ -176,8 +197,10 @@ class Z4c:
         if per_cell:
             pc = self.torch.empty(self.nelem // NF * 4, dtype=self.torch.float64,
                                   device=self.regs[0].device)
+        self._enter()
         rc = lib().z4c_constraints(self.ctx, float(r_mask), norms.ctypes.data,
                                    pc.data_ptr() if pc is not None else None)
+        self._leave(pc)
         if rc not in (Z4C_OK, Z4C_ERR_NAN):
             _check(rc, self.ctx, "z4c_constraints")
         return norms, pc, rc

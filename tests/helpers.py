@@ -31,8 +31,12 @@ def small_workload(kind, order, nb=(1, 1, 1), n=16, periodic=None, **over):
     if periodic is not None:
         w["periodic"] = periodic
     w.update(over)
-    n3 = (n, n, n) if np.isscalar(n) else tuple(n)
-    w["n"], w["lo"], w["h"] = inputs.uniform_blocks(nb, n3, w["dom_lo"], w["dom_hi"])
+    n3 = np.array((n, n, n) if np.isscalar(n) else tuple(n))
+    # spacing from the x extent; the box is centred on the origin
+    h = (w["dom_hi"][0] - w["dom_lo"][0]) / (nb[0] * n3[0])
+    half = np.array(nb) * n3 * h / 2
+    w["dom_lo"], w["dom_hi"] = tuple(-half), tuple(half)
+    w["n"], w["lo"], w["h"] = inputs.uniform_blocks(nb, tuple(n3), w["dom_lo"], w["dom_hi"])
     return w
 
 

@@ -166,20 +166,48 @@ def test_full_size_single_puncture_one_step(oracle):
     assert rel.max() <= STEP_TOL, (rel, absd)
 
 
+def _round_like_shadow(m, u):
+    """The FP64 state rounded to FP32 the way the FP32-RHS path stores it
+    (diagonal of gt minus one), back in FP64."""
+    v = u.copy()
+    for blk in m.blocks(v):
+        for f in range(22):
+            off = 1.0 if f in (1, 4, 6) else 0.0
+            blk[f] = (blk[f] - off).astype(np.float32).astype(np.float64) + off
+    return v
+
+
 def test_fp32_rhs_error_budget(oracle):
-    """FP32 stencils/algebra against the FP64 oracle, per RHS call and after
-    steps on the puncture problem: bounded by FP32 rounding of the inputs."""
+    """FP32 stencils and algebra (FP64 state, RK accumulation, 1/chi,
+    enforcement).  Bounds, stated against what FP32 storage alone causes:
+      - one RHS call: per-field error <= 8x the error of the FP64 oracle fed
+        the FP32-rounded state (the input-rounding floor);
+      - 5 RK4 steps of the puncture: per-field |u32 - u64| <= 1e-3 of the
+        change |u64(t) - u64(0)|, and ||H||_2 within 1e-5 (relative) of FP64."""
     w = H.small_workload("puncture", 6, (2, 2, 2), 16)
     m = H.oracle_mesh(oracle, w)
     g = H.gpu_ctx(w, precision=32)
     u = m.initial_data(w["id_kind"], w["id_par"])
     m.fill_ghosts(u)
+    ref = m.rhs(u)
+    floor, _ = H.field_errors(m, ref, m.rhs(_round_like_shadow(m, u)))
     g.z4c_set_state(u, reg=1)
-    rel, _ = H.field_errors(m, m.rhs(u), g.z4c_rhs(1).cpu().numpy())
-    assert rel.max() < 1e-4, rel
+    err, _ = H.field_errors(m, ref, g.z4c_rhs(1).cpu().numpy())
+    assert np.all(err <= 8 * floor + 1e-12), (err, floor)
+
     g.z4c_set_initial_data(w["id_kind"], w["id_par"])
+    u0 = m.initial_data(w["id_kind"], w["id_par"])
+    u = u0.copy()
     dt = 0.25 * float(w["h"][0])
     g.z4c_rk4_step(dt, 5)
     m.rk4(u, dt, 5)
-    rel, _ = H.field_errors(m, u, g.z4c_get_state())
-    assert rel.max() < 1e-4, rel
+    v = g.z4c_get_state()
+    for f in range(22):
+        d = np.concatenate([(m.blocks(v)[b][f] - m.blocks(u)[b][f])[m.evolved_mask(b)] for b in range(m.nblocks)])
+        c = np.concatenate([(m.blocks(u)[b][f] - m.blocks(u0)[b][f])[m.evolved_mask(b)] for b in range(m.nblocks)])
+        assert np.abs(d).max() <= 1e-3 * np.abs(c).max(), f
+    m.fill_ghosts(u)
+    m.fill_ghosts(v)
+    n64, _ = m.constraints(u)
+    n32, _ = m.constraints(v)
+    assert abs(n32[0] / n64[0] - 1) <= 1e-5, (n32[0], n64[0])
