@@ -37,10 +37,13 @@ UNIT = "zone-cycles/s"
 NOMINAL_FP64 = 1.25e12     # GB300 FP64, nominal (profiling recipe)
 L2_BYTES = 129 * 2 ** 20
 
-# Executed FP64 flops per interior cell per RHS stage of the fused interior
-# kernel (dadd + dmul + 2 dfma), from the ncu instruction counters of a
-# 2x2x2 x 32^3 order-6 capture (profiles/interior_fp64_single_puncture.md).
-FP64_FLOPS_PER_CELL_STAGE = {6: None, 4: None}
+# Executed FP64 operations per interior cell per stage of the fused interior
+# kernel, from the ncu instruction counters (dadd, dfma, dmul; exact integers
+# per cell) of an 8 x 32^3 order-6 capture of this kernel version
+# (profiles/interior_fp64_single_puncture.md): flops = dadd + dmul + 2 dfma.
+FP64_OPS_PER_CELL_STAGE = {6: dict(dadd=1927, dfma=1655, dmul=551)}
+# DRAM bytes per launch of that capture (read + write) per interior cell
+FP64_DRAM_BYTES_PER_CELL = {6: (335411584 + 1546907136) / 262144}
 # FP32-RHS kernel: FP32 flops and FP64 residue flops per cell per stage
 FP32_FLOPS_PER_CELL_STAGE = {6: None, 4: None}
 FP32_F64_RESIDUE_PER_CELL_STAGE = {6: None, 4: None}
@@ -173,13 +176,106 @@ def run_reference(args, workload):
     print(json.dumps(line), flush=True)
 
 
+def measure(z4c, torch, workload, prec, args, ws, local):
+    """Device-timed RK4 steps (CUDA graph replays) of one context, plus the
+    live per-kernel timing, the roofline of the dominant kernel and the
+    end-to-end host-buffer throughput."""
+    g = z4c.Z4c.from_workload(workload, precision=prec)
+    cells = int(np.prod(workload["n"], axis=1).sum())
+    dt = workload["cfl"] * float(workload["h"][0])
+    g.z4c_set_initial_data(workload["id_kind"], workload["id_par"])
+    st = g.stream
+
+    def barrier():
+        torch.cuda.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+
+    # warm-up (also captures the CUDA graph of one RK4 step)
+    g.z4c_rk4_step(dt, max(3, args.warmup))
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        barrier()
+        e0.record(st)
+        g.z4c_rk4_step(dt, args.steps)
+        e1.record(st)
+        barrier()
+    ms = e0.elapsed_time(e1)
+    if ws > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = cells * args.steps * ws / (ms * 1e-3)
+
+    # live per-kernel timing: CUDA events around each launch on the context's
+    # stream (plain launches of the same kernels on the same state)
+    kms = g.z4c_profile_steps(dt, 2)
+    interior_ms = kms[1] / 4.0  # per launch (4 stages per step)
+    peak64 = z4c.z4c_peak_fma(True, st)
+    peak32 = z4c.z4c_peak_fma(False, st)
+    order = workload["order"]
+    if prec == 64 and order in FP64_OPS_PER_CELL_STAGE:
+        ops = FP64_OPS_PER_CELL_STAGE[order]
+        flops = (ops["dadd"] + ops["dmul"] + 2 * ops["dfma"]) * cells
+        insts = (ops["dadd"] + ops["dmul"] + ops["dfma"]) * cells
+        achieved = flops / (interior_ms * 1e-3)
+        roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak64 / 1e12, "unit": "TFLOP/s",
+                "frac": achieved / peak64,
+                "traffic": FP64_DRAM_BYTES_PER_CELL[order] * cells,
+                "traffic_note": "ncu dram bytes of an 8 x 32^3 capture scaled by cells",
+                "kernel": f"interior_kernel<{order},false> (fused RHS + RK stage + enforcement)",
+                "peak_source": "measured DFMA throughput (z4c_peak_fma), FMA = 2 flops",
+                "peak_nominal": NOMINAL_FP64 / 1e12,
+                "fp64_issue_frac": insts / (interior_ms * 1e-3) / (peak64 / 2),
+                "flops_per_cell_stage": flops / cells}
+    else:
+        bytes_launch = ALG_BYTES_PER_ZONE_CYCLE / 4 * cells
+        hbm = measured_peaks().get("hbm_gbs", 6800.0)
+        achieved = bytes_launch / (interior_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                "traffic": None, "kernel": f"interior_kernel<{order},{'true' if prec == 32 else 'false'}>",
+                "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
+                "note": "algorithmic bytes view; the per-cell FP32/FP64 op mix is in profiles/"}
+    roof["kernel_ms_per_launch"] = interior_ms
+    roof["step_share"] = {"ghost": kms[0] / kms.sum(), "interior": kms[1] / kms.sum(),
+                          "sommerfeld": kms[2] / kms.sum()}
+    roof["fp64_fma_peak_tflops"] = peak64 / 1e12
+    roof["fp32_fma_peak_tflops"] = peak32 / 1e12
+
+    # end to end through the C ABI with pinned host buffers: every step copies
+    # the state host -> device, runs one RK4 step and copies it back
+    nbytes = g.state_bytes
+    hin = torch.empty(nbytes // 8, dtype=torch.float64, pin_memory=True)
+    hout = torch.empty(nbytes // 8, dtype=torch.float64, pin_memory=True)
+    hin.numpy()[:] = g.z4c_get_state()
+    g.z4c_evolve_host(hin, hout, dt, 1)
+    e2e_steps = max(2, min(args.steps, 10))
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        g.z4c_evolve_host(hin, hout, dt, 1)
+    t1 = time.perf_counter()
+    barrier()
+    e2e = {"value": cells * e2e_steps * ws / (t1 - t0), "unit": UNIT, "h2d_bytes_per_step": nbytes,
+           "d2h_bytes_per_step": nbytes}
+    out = dict(value=value, ms_per_step=ms / args.steps, roofline=roof, e2e=e2e,
+               gpu_launches=g.z4c_launches_per_step() * args.steps, clocks=clk.summary(),
+               cells=cells, dt=dt, state_bytes=nbytes)
+    g.close()
+    del g
+    torch.cuda.empty_cache()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--variant", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--variant", default="both", choices=["fp64", "fp32", "both"])
     ap.add_argument("--workload", default="single_puncture_128")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-steps", type=int, default=2)
@@ -200,85 +296,13 @@ def main():
         torch.cuda.set_device(0)
     from paper_2409_10383_gb300 import z4c
 
-    prec = 64 if args.variant == "fp64" else 32
-    g = z4c.Z4c.from_workload(workload, precision=prec)
-    cells = int(np.prod(workload["n"], axis=1).sum())
-    dt = workload["cfl"] * float(workload["h"][0])
-    g.z4c_set_initial_data(workload["id_kind"], workload["id_par"])
-    st = g.stream
-
-    def barrier():
-        torch.cuda.synchronize()
-        if ws > 1:
-            torch.distributed.barrier()
-
-    # warm-up (also captures the CUDA graph of one RK4 step)
-    g.z4c_rk4_step(dt, max(3, args.warmup))
-    barrier()
-
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    with ClockSampler(local) as clk:
-        barrier()
-        e0.record(st)
-        g.z4c_rk4_step(dt, args.steps)
-        e1.record(st)
-        barrier()
-    ms = e0.elapsed_time(e1)
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    ms_per_step = ms / args.steps
-    value = cells * args.steps * ws / (ms * 1e-3)
-
-    # live per-kernel timing (CUDA events around each launch on the context's
-    # stream, plain launches of the same kernels) for the roofline
-    prof_steps = 2
-    kms = g.z4c_profile_steps(dt, prof_steps)
-    interior_ms = kms[1] / 4.0  # per launch (4 stages per step)
-    peak64 = z4c.z4c_peak_fma(True, st)
-    peak32 = z4c.z4c_peak_fma(False, st)
-    peaks = measured_peaks()
-    order = workload["order"]
-    if prec == 64 and FP64_FLOPS_PER_CELL_STAGE.get(order):
-        flops = FP64_FLOPS_PER_CELL_STAGE[order] * cells
-        achieved = flops / (interior_ms * 1e-3)
-        roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak64 / 1e12, "unit": "TFLOP/s",
-                "frac": achieved / peak64, "traffic": None,
-                "kernel": "interior_kernel<6,false> (fused RHS + RK stage + enforcement)",
-                "peak_source": "measured DFMA throughput (z4c_peak_fma)",
-                "peak_nominal": NOMINAL_FP64 / 1e12}
-    else:
-        bytes_launch = ALG_BYTES_PER_ZONE_CYCLE / 4 * cells
-        hbm = peaks.get("hbm_gbs", 6800.0)
-        achieved = bytes_launch / (interior_ms * 1e-3) / 1e9
-        roof = {"bound": "alu" if prec == 64 else "hbm", "achieved": achieved, "peak": hbm,
-                "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
-                "kernel": f"interior_kernel<{order},{'true' if prec == 32 else 'false'}>",
-                "note": "per-cell flop count not yet measured; HBM view shown"}
-    roof["kernel_ms_per_launch"] = interior_ms
-    roof["step_share"] = {"ghost": kms[0] / kms.sum(), "interior": kms[1] / kms.sum(),
-                          "sommerfeld": kms[2] / kms.sum()}
-    roof["fp64_fma_peak_tflops"] = peak64 / 1e12
-    roof["fp32_fma_peak_tflops"] = peak32 / 1e12
-
-    # end to end through the C ABI with pinned host buffers: H2D of the state,
-    # one RK4 step, D2H of the state, every step
-    nbytes = g.state_bytes
-    hin = torch.empty(nbytes // 8, dtype=torch.float64, pin_memory=True)
-    hout = torch.empty(nbytes // 8, dtype=torch.float64, pin_memory=True)
-    hin.numpy()[:] = g.z4c_get_state()
-    g.z4c_evolve_host(hin, hout, dt, 1)
-    e2e_steps = max(2, min(args.steps, 10))
-    barrier()
-    t0 = time.perf_counter()
-    for _ in range(e2e_steps):
-        g.z4c_evolve_host(hin, hout, dt, 1)
-    t1 = time.perf_counter()
-    barrier()
-    e2e = {"value": cells * e2e_steps * ws / (t1 - t0), "unit": UNIT, "h2d_bytes_per_step": nbytes,
-           "d2h_bytes_per_step": nbytes}
+    res = {}
+    if args.variant in ("fp64", "both"):
+        res[64] = measure(z4c, torch, workload, 64, args, ws, local)
+    if args.variant in ("fp32", "both"):
+        res[32] = measure(z4c, torch, workload, 32, args, ws, local)
+    prim = 64 if 64 in res else 32
+    r = res[prim]
 
     if rank != 0:
         if ws > 1:
@@ -286,21 +310,28 @@ def main():
         return
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
-        r = oracle_sample(workload, args.cpu_steps, 0)
-        cpu = {k: r[k] for k in ("value", "unit", "cores", "kind", "sample")}
-    launches = g.z4c_launches_per_step() * args.steps
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prec == 64 else "f32+f64",
+        c = oracle_sample(workload, args.cpu_steps, 0)
+        cpu = {k: c[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    order = workload["order"]
+    line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64" if prim == 64 else "f32+f64",
             "data": "synthetic",
-            "config": {"workload": workload["name"], "variant": args.variant, "cells": cells,
-                       "blocks": int(len(workload["n"])), "block": list(map(int, workload["n"][0])),
-                       "ghosts": workload["ghosts"], "fd_order": order, "dt": dt,
-                       "l2": f"inputs larger than L2 ({4 * nbytes / 2**30:.2f} GiB of registers "
-                             f"vs {L2_BYTES / 2**20:.0f} MiB L2)",
+            "config": {"workload": workload["name"], "variant": "fp64" if prim == 64 else "fp32_rhs",
+                       "cells": r["cells"], "blocks": int(len(workload["n"])),
+                       "block": list(map(int, workload["n"][0])), "ghosts": workload["ghosts"],
+                       "fd_order": order, "dt": r["dt"],
+                       "l2": f"inputs larger than L2 ({4 * r['state_bytes'] / 2**30:.2f} GiB of "
+                             f"registers vs {L2_BYTES / 2**20:.0f} MiB L2)",
                        "parallelism": f"{ws} independent instance(s)"},
-            "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
-            "clocks": clk.summary()}
+            "roofline": r["roofline"], "cpu_baseline": cpu, "e2e": r["e2e"],
+            "gpu_launches": r["gpu_launches"], "clocks": r["clocks"]}
+    if prim == 64 and 32 in res:
+        q = res[32]
+        line["fp32_rhs"] = {"value": q["value"], "unit": UNIT, "ms_per_step": q["ms_per_step"],
+                            "dtype": "f32 stencils/algebra + f64 state, RK, 1/chi, enforcement",
+                            "speedup_vs_fp64": q["value"] / r["value"], "roofline": q["roofline"],
+                            "e2e": q["e2e"], "gpu_launches": q["gpu_launches"], "clocks": q["clocks"]}
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
