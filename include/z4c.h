@@ -189,6 +189,39 @@ int z4c_profile_steps(z4c_ctx *ctx, double dt, int nsteps, double *ms);
  * cuda_stream and synchronised.  Allocates nothing. */
 int z4c_peak_fma(int fp64, void *cuda_stream, double *flops_per_s);
 
+/* Constraint norms of one MeshBlock without any device allocation.
+ *
+ * The paper has no counterpart to this call; it exists for callers that
+ * cannot allocate device memory themselves, for example a diagnostic hook
+ * inside a host code that owns the whole device memory pool, or a monitor
+ * that must not allocate while an evolution is in flight.  It computes the
+ * same six norms as z4c_constraints() for a single block, using no context
+ * and no caller scratch: its reduction records live in a fixed, file-scope
+ * device array of Z4C_STATIC_MAX_TILES records of 8 doubles (about 1 MiB),
+ * which every GPU that loads this library holds until the process exits.
+ *
+ *   u_device   the block's state in device memory, one register of a
+ *              single block: 22 fields of (n_z+2g) x (n_y+2g) x (n_x+2g)
+ *              FP64, i fastest, ghost cells already filled
+ *   n, ghosts, fd_order, lo, h, chi_floor, r_mask  as in z4c_create /
+ *              z4c_constraints
+ *   norms      host, 6 doubles (same order as z4c_constraints)
+ *   cuda_stream  stream to run on (void * cudaStream_t); the call waits for it
+ *
+ * One record is used per 16 x 8 tile of one z-plane; a block needing more
+ * than Z4C_STATIC_MAX_TILES tiles (e.g. larger than 128^3) is rejected with
+ * Z4C_ERR_UNSUPPORTED.  Calls no cudaMalloc/cudaFree and no allocating
+ * library routine.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  Every call shares the array and
+ * overwrites the records it reads; calls that overlap on the GPU (other
+ * streams or threads without ordering) race on it.  Returns Z4C_ERR_NAN if a
+ * norm is NaN. */
+#define Z4C_STATIC_MAX_TILES 16384
+int z4c_constraints_static(const void *u_device, const int32_t n[3], int ghosts, int fd_order,
+                           const double lo[3], double h, double chi_floor, double r_mask,
+                           double *norms, void *cuda_stream);
+
 /* Number of kernel launches one RK4 step enqueues. */
 int z4c_launches_per_step(const z4c_ctx *ctx);
 

@@ -24,8 +24,8 @@ REG_U0, REG_STAGE_A, REG_STAGE_B, REG_ACC = 0, 1, 2, 3
 EXPORTS = ("z4c_create", "z4c_state_bytes", "z4c_scratch_bytes", "z4c_bind",
            "z4c_set_initial_data", "z4c_fill_ghosts", "z4c_rhs", "z4c_rk4_step",
            "z4c_constraints", "z4c_get_state", "z4c_set_state", "z4c_evolve_host",
-           "z4c_sync", "z4c_profile_steps", "z4c_peak_fma", "z4c_launches_per_step",
-           "z4c_last_error", "z4c_destroy")
+           "z4c_sync", "z4c_profile_steps", "z4c_peak_fma", "z4c_constraints_static",
+           "z4c_launches_per_step", "z4c_last_error", "z4c_destroy")
 
 
 class z4c_mesh(ctypes.Structure):
@@ -75,6 +75,7 @@ def lib():
             "z4c_sync": (I, [P]),
             "z4c_profile_steps": (I, [P, D, I, P]),
             "z4c_peak_fma": (I, [I, P, P]),
+            "z4c_constraints_static": (I, [P, P, I, I, P, D, D, D, P, P]),
             "z4c_launches_per_step": (I, [P]),
             "z4c_last_error": (ctypes.c_char_p, [P]),
             "z4c_destroy": (None, [P]),
@@ -254,3 +255,16 @@ def z4c_peak_fma(fp64: bool, stream=None) -> float:
     st = stream.cuda_stream if stream is not None else None
     _check(lib().z4c_peak_fma(int(bool(fp64)), st, ctypes.byref(out)), None, "z4c_peak_fma")
     return out.value
+
+
+def z4c_constraints_static(u_device_ptr: int, n, ghosts: int, fd_order: int, lo, h: float,
+                           chi_floor: float, r_mask: float, stream=None):
+    """Constraint norms of one block in device memory, allocating nothing
+    (see include/z4c.h).  Returns (status, norms)."""
+    n_arr = (ctypes.c_int32 * 3)(*[int(v) for v in n])
+    lo_arr = (ctypes.c_double * 3)(*[float(v) for v in lo])
+    norms = np.zeros(6)
+    st = stream.cuda_stream if stream is not None else None
+    rc = lib().z4c_constraints_static(u_device_ptr, n_arr, int(ghosts), int(fd_order), lo_arr,
+                                      float(h), float(chi_floor), float(r_mask), norms.ctypes.data, st)
+    return rc, norms
