@@ -37,13 +37,14 @@ UNIT = "zone-cycles/s"
 NOMINAL_FP64 = 1.25e12     # GB300 FP64, nominal (profiling recipe)
 L2_BYTES = 129 * 2 ** 20
 
-# Executed FP64 operations per interior cell per stage of the fused interior
-# kernel, from the ncu instruction counters (dadd, dfma, dmul; exact integers
-# per cell) of an 8 x 32^3 order-6 capture of this kernel version
+# Executed FP64 operations per interior cell per stage of the dominant kernel
+# (interior_pre_kernel<6,false>: fused RHS + RK stage + enforcement, mixed
+# derivatives from the pre-pass), from the ncu instruction counters (dadd,
+# dfma, dmul; exact integers per cell) of an 8 x 32^3 order-6 capture
 # (profiles/interior_fp64_single_puncture.md): flops = dadd + dmul + 2 dfma.
-FP64_OPS_PER_CELL_STAGE = {6: dict(dadd=1927, dfma=1655, dmul=551)}
+FP64_OPS_PER_CELL_STAGE = {6: dict(dadd=951, dfma=1531, dmul=500)}
 # DRAM bytes per launch of that capture (read + write) per interior cell
-FP64_DRAM_BYTES_PER_CELL = {6: (335411584 + 1546907136) / 262144}
+FP64_DRAM_BYTES_PER_CELL = {6: (154618880 + 194336512) / 262144}
 # FP32-RHS kernel: FP32 flops and FP64 residue flops per cell per stage
 FP32_FLOPS_PER_CELL_STAGE = {6: None, 4: None}
 FP32_F64_RESIDUE_PER_CELL_STAGE = {6: None, 4: None}
@@ -225,7 +226,7 @@ def measure(z4c, torch, workload, prec, args, ws, local):
                 "frac": achieved / peak64,
                 "traffic": FP64_DRAM_BYTES_PER_CELL[order] * cells,
                 "traffic_note": "ncu dram bytes of an 8 x 32^3 capture scaled by cells",
-                "kernel": f"interior_kernel<{order},false> (fused RHS + RK stage + enforcement)",
+                "kernel": f"interior_pre_kernel<{order},false> (fused RHS + RK stage + enforcement)",
                 "peak_source": "measured DFMA throughput (z4c_peak_fma), FMA = 2 flops",
                 "peak_nominal": NOMINAL_FP64 / 1e12,
                 "fp64_issue_frac": insts / (interior_ms * 1e-3) / (peak64 / 2),
@@ -235,12 +236,12 @@ def measure(z4c, torch, workload, prec, args, ws, local):
         hbm = measured_peaks().get("hbm_gbs", 6800.0)
         achieved = bytes_launch / (interior_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                "traffic": None, "kernel": f"interior_kernel<{order},{'true' if prec == 32 else 'false'}>",
+                "traffic": None, "kernel": f"interior_pre_kernel<{order},{'true' if prec == 32 else 'false'}>",
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
                 "note": "algorithmic bytes view; the per-cell FP32/FP64 op mix is in profiles/"}
     roof["kernel_ms_per_launch"] = interior_ms
-    roof["step_share"] = {"ghost": kms[0] / kms.sum(), "interior": kms[1] / kms.sum(),
-                          "sommerfeld": kms[2] / kms.sum()}
+    roof["step_share"] = {"ghost": kms[0] / kms.sum(), "prepass": kms[3] / kms.sum(),
+                          "interior": kms[1] / kms.sum(), "sommerfeld": kms[2] / kms.sum()}
     roof["fp64_fma_peak_tflops"] = peak64 / 1e12
     roof["fp32_fma_peak_tflops"] = peak32 / 1e12
 

@@ -84,7 +84,12 @@ typedef struct z4c_block {
  *   shift         0 frozen (d_t beta = 0), 1 Gamma-driver (Gam - eta beta)
  *   rhs_precision 64: everything FP64; 32: stencils and RHS algebra in FP32,
  *                 state, RK accumulation, 1/chi, constraint enforcement and
- *                 constraint norms in FP64 */
+ *                 constraint norms in FP64
+ *   schedule      0 default, 1 one fused kernel per stage, 2 a pre-pass
+ *                 storing the y/z first derivatives of chi, gt, alpha, beta
+ *                 (in scratch) followed by the fused kernel, which then forms
+ *                 mixed second derivatives as one stencil on the stored
+ *                 values (fewer operations, fewer registers); default 2 */
 typedef struct z4c_params {
   double ko_sigma;
   double kappa1;
@@ -95,7 +100,7 @@ typedef struct z4c_params {
   int32_t lapse;
   int32_t shift;
   int32_t rhs_precision;
-  int32_t reserved;
+  int32_t schedule;
 } z4c_params;
 
 typedef struct z4c_ctx z4c_ctx;
@@ -178,9 +183,10 @@ int z4c_sync(z4c_ctx *ctx);
 
 /* Measurement aid: run nsteps RK4 steps with plain (not graph) launches,
  * each bracketed by CUDA events on the context's stream, and return the
- * average milliseconds per step spent in each kernel kind:
+ * average milliseconds per step spent in each kernel kind (4 doubles):
  * ms[0] ghost fill, ms[1] fused interior RHS + stage update, ms[2]
- * Sommerfeld cells.  Advances U0 exactly like z4c_rk4_step.  Synchronous. */
+ * Sommerfeld cells, ms[3] y/z first-derivative pre-pass (schedule 2).
+ * Advances U0 exactly like z4c_rk4_step.  Synchronous. */
 int z4c_profile_steps(z4c_ctx *ctx, double dt, int nsteps, double *ms);
 
 /* Measurement aid: FP64 (fp64 = 1) or FP32 (fp64 = 0) fused multiply-add

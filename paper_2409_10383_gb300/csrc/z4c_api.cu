@@ -26,13 +26,14 @@ struct z4c_ctx {
   std::vector<z4c_block> blocks;
   std::vector<DevBlock> dblocks;
   std::vector<Tile> tiles;
+  std::vector<Tile> wtiles;  // interior widened by order/2 in x and y (pre-pass)
   std::vector<CellRef> somm;
   std::vector<GhostCopy> gcopy;
   size_t reg_elems = 0;
   int max_S = 0;
   // scratch layout (byte offsets)
-  size_t o_blocks = 0, o_tiles = 0, o_somm = 0, o_gcopy = 0, o_part = 0, o_res = 0, o_sh0 = 0,
-         o_sh1 = 0, scratch_total = 0;
+  size_t o_blocks = 0, o_tiles = 0, o_wtiles = 0, o_somm = 0, o_gcopy = 0, o_part = 0, o_res = 0,
+         o_sh0 = 0, o_sh1 = 0, o_dstore = 0, scratch_total = 0;
   // bound buffers
   double *reg[4] = {nullptr, nullptr, nullptr, nullptr};
   char *scratch = nullptr;
@@ -45,6 +46,9 @@ struct z4c_ctx {
   std::string err;
 
   bool f32() const { return params.rhs_precision == 32; }
+  bool pre() const { return !wtiles.empty(); }
+  const Tile *d_wtiles() const { return pre() ? (const Tile *)(scratch + o_wtiles) : nullptr; }
+  void *d_dstore() const { return pre() ? (void *)(scratch + o_dstore) : nullptr; }
   const DevBlock *d_blocks() const { return (const DevBlock *)(scratch + o_blocks); }
   const Tile *d_tiles() const { return (const Tile *)(scratch + o_tiles); }
   const CellRef *d_somm() const { return (const CellRef *)(scratch + o_somm); }
@@ -94,6 +98,7 @@ int z4c_create(const z4c_mesh *mesh, const z4c_block *blocks, int nblocks, int g
   if (params->rhs_precision != 64 && params->rhs_precision != 32) return Z4C_ERR_UNSUPPORTED;
   if (params->lapse < 0 || params->lapse > 1 || params->shift < 0 || params->shift > 1) return Z4C_ERR_BAD_ARG;
   if (!(params->chi_floor > 0.0)) return Z4C_ERR_BAD_ARG;
+  if (params->schedule < 0 || params->schedule > 2) return Z4C_ERR_BAD_ARG;
   for (int d = 0; d < 3; ++d)
     if (!(mesh->hi[d] > mesh->lo[d])) return Z4C_ERR_BAD_MESH;
 
@@ -189,6 +194,16 @@ int z4c_create(const z4c_mesh *mesh, const z4c_block *blocks, int nblocks, int g
     for (int k = 0; k < n[2]; ++k)
       for (int j0 = 0; j0 < n[1]; j0 += TY)
         for (int i0 = 0; i0 < n[0]; i0 += TX) ctx->tiles.push_back(Tile{b, i0, j0, k});
+  // schedule: 0 = default (the pre-pass, faster for both precisions),
+  // 1 = single fused kernel, 2 = y/z pre-pass + fused kernel
+  const bool use_pre = params->schedule != 1;
+  if (use_pre) {
+    const int W = fd_order / 2;
+    for (int b = 0; b < nblocks; ++b)
+      for (int k = 0; k < n[2]; ++k)
+        for (int j0 = -W; j0 < n[1] + W; j0 += TY)
+          for (int i0 = -W; i0 < n[0] + W; i0 += TX) ctx->wtiles.push_back(Tile{b, i0, j0, k});
+  }
   for (int b = 0; b < nblocks; ++b)
     for (int k = 0; k < e[2]; ++k)
       for (int j = 0; j < e[1]; ++j)
@@ -228,6 +243,8 @@ int z4c_create(const z4c_mesh *mesh, const z4c_block *blocks, int nblocks, int g
   o = align256(o + sizeof(DevBlock) * ctx->dblocks.size());
   ctx->o_tiles = o;
   o = align256(o + sizeof(Tile) * ctx->tiles.size());
+  ctx->o_wtiles = o;
+  o = align256(o + sizeof(Tile) * ctx->wtiles.size());
   ctx->o_somm = o;
   o = align256(o + sizeof(CellRef) * std::max<size_t>(1, ctx->somm.size()));
   ctx->o_gcopy = o;
@@ -241,6 +258,10 @@ int z4c_create(const z4c_mesh *mesh, const z4c_block *blocks, int nblocks, int g
     o = align256(o + sizeof(float) * ctx->reg_elems);
     ctx->o_sh1 = o;
     o = align256(o + sizeof(float) * ctx->reg_elems);
+  }
+  if (use_pre) {
+    ctx->o_dstore = o;
+    o = align256(o + (ctx->f32() ? sizeof(float) : sizeof(double)) * ctx->reg_elems);
   }
   ctx->scratch_total = o;
   *out = ctx;
@@ -280,6 +301,9 @@ int z4c_bind(z4c_ctx *ctx, void *u0, void *stage_a, void *stage_b, void *acc, vo
                      sizeof(DevBlock) * ctx->dblocks.size(), cudaMemcpyHostToDevice, st));
   CK(cudaMemcpyAsync(ctx->scratch + ctx->o_tiles, ctx->tiles.data(), sizeof(Tile) * ctx->tiles.size(),
                      cudaMemcpyHostToDevice, st));
+  if (!ctx->wtiles.empty())
+    CK(cudaMemcpyAsync(ctx->scratch + ctx->o_wtiles, ctx->wtiles.data(), sizeof(Tile) * ctx->wtiles.size(),
+                       cudaMemcpyHostToDevice, st));
   if (!ctx->somm.empty())
     CK(cudaMemcpyAsync(ctx->scratch + ctx->o_somm, ctx->somm.data(), sizeof(CellRef) * ctx->somm.size(),
                        cudaMemcpyHostToDevice, st));
@@ -313,11 +337,14 @@ int fill_ghosts_f32(z4c_ctx *ctx, float *reg) {
   return Z4C_OK;
 }
 
-int launch_stage(z4c_ctx *ctx, const StageArgs &a) {
+int launch_stage(z4c_ctx *ctx, StageArgs a) {
+  a.dstore = ctx->d_dstore();
   if (ctx->f32())
-    CK(launch_interior_f32(ctx->order, a, ctx->d_tiles(), (int)ctx->tiles.size(), ctx->stream));
+    CK(launch_interior_f32(ctx->order, a, ctx->d_tiles(), (int)ctx->tiles.size(), ctx->d_wtiles(),
+                           (int)ctx->wtiles.size(), ctx->stream));
   else
-    CK(launch_interior_f64(ctx->order, a, ctx->d_tiles(), (int)ctx->tiles.size(), ctx->stream));
+    CK(launch_interior_f64(ctx->order, a, ctx->d_tiles(), (int)ctx->tiles.size(), ctx->d_wtiles(),
+                           (int)ctx->wtiles.size(), ctx->stream));
   CK(launch_sommerfeld(ctx->f32(), a, ctx->d_somm(), (int)ctx->somm.size(), ctx->stream));
   return Z4C_OK;
 }
@@ -520,7 +547,7 @@ int z4c_profile_steps(z4c_ctx *ctx, double dt, int nsteps, double *ms) {
   cudaEvent_t ev[2];
   CK(cudaEventCreate(&ev[0]));
   CK(cudaEventCreate(&ev[1]));
-  double acc[3] = {0, 0, 0};
+  double acc[4] = {0, 0, 0, 0};
   double *U0 = ctx->reg[0], *SA = ctx->reg[1], *SB = ctx->reg[2], *ACC = ctx->reg[3];
   double *X[4] = {U0, SA, SB, SA};
   double *NX[4] = {SA, SB, SA, U0};
@@ -563,9 +590,18 @@ int z4c_profile_steps(z4c_ctx *ctx, double dt, int nsteps, double *ms) {
         });
         if (r) return r;
       }
+      a.dstore = ctx->d_dstore();
+      const int nw = (int)ctx->wtiles.size();
+      if (nw) {  // pre-pass alone, then the fused kernel (which reads its output)
+        r = timed(3, [&] {
+          return ctx->f32() ? launch_prepass_f32(ctx->order, a, ctx->d_wtiles(), nw, ctx->stream)
+                            : launch_prepass_f64(ctx->order, a, ctx->d_wtiles(), nw, ctx->stream);
+        });
+        if (r) return r;
+      }
       r = timed(1, [&] {
-        return ctx->f32() ? launch_interior_f32(ctx->order, a, ctx->d_tiles(), nt, ctx->stream)
-                          : launch_interior_f64(ctx->order, a, ctx->d_tiles(), nt, ctx->stream);
+        return ctx->f32() ? launch_fused_f32(ctx->order, a, ctx->d_tiles(), nt, nw > 0, ctx->stream)
+                          : launch_fused_f64(ctx->order, a, ctx->d_tiles(), nt, nw > 0, ctx->stream);
       });
       if (r) return r;
       if (ns) {
@@ -575,7 +611,7 @@ int z4c_profile_steps(z4c_ctx *ctx, double dt, int nsteps, double *ms) {
     }
   cudaEventDestroy(ev[0]);
   cudaEventDestroy(ev[1]);
-  for (int q = 0; q < 3; ++q) ms[q] = acc[q] / nsteps;
+  for (int q = 0; q < 4; ++q) ms[q] = acc[q] / nsteps;
   return Z4C_OK;
 }
 
@@ -588,7 +624,7 @@ int z4c_peak_fma(int fp64, void *cuda_stream, double *flops_per_s) {
 
 int z4c_launches_per_step(const z4c_ctx *ctx) {
   if (!ctx) return Z4C_ERR_BAD_ARG;
-  const int per_stage = (ctx->gcopy.empty() ? 0 : 1) + 1 + (ctx->somm.empty() ? 0 : 1);
+  const int per_stage = (ctx->gcopy.empty() ? 0 : 1) + (ctx->pre() ? 2 : 1) + (ctx->somm.empty() ? 0 : 1);
   return 4 * per_stage;
 }
 

@@ -70,6 +70,7 @@ struct StageArgs {
   double *next;       // next stage state (FP64)
   float *next32;      // FP32 shadow of the next stage state (FP32 mode)
   double *rhs_out;    // MODE_RHS output
+  void *dstore;       // stored y/z first derivatives (pre-pass), FP64 or FP32 like the stencils
   double ca, cb;
   int32_t mode;
   int32_t next_full;  // FP32 mode: 1 = write every field of next in FP64, 0 = chi only
@@ -80,10 +81,19 @@ constexpr int TX = 16;
 constexpr int TY = 8;
 
 // ---- launchers (defined in the kernel translation units) ----
+// wtiles == nullptr: single fused kernel; otherwise the y/z pre-pass over
+// wtiles followed by the fused kernel reading the stored derivatives.
 cudaError_t launch_interior_f64(int order, const StageArgs &a, const Tile *tiles, int ntiles,
-                                cudaStream_t st);
+                                const Tile *wtiles, int nwtiles, cudaStream_t st);
 cudaError_t launch_interior_f32(int order, const StageArgs &a, const Tile *tiles, int ntiles,
-                                cudaStream_t st);
+                                const Tile *wtiles, int nwtiles, cudaStream_t st);
+// the two halves of launch_interior_*, launched separately (measurement)
+cudaError_t launch_prepass_f64(int order, const StageArgs &a, const Tile *wtiles, int nwtiles, cudaStream_t st);
+cudaError_t launch_prepass_f32(int order, const StageArgs &a, const Tile *wtiles, int nwtiles, cudaStream_t st);
+cudaError_t launch_fused_f64(int order, const StageArgs &a, const Tile *tiles, int ntiles, bool pre,
+                             cudaStream_t st);
+cudaError_t launch_fused_f32(int order, const StageArgs &a, const Tile *tiles, int ntiles, bool pre,
+                             cudaStream_t st);
 cudaError_t launch_sommerfeld(bool f32, const StageArgs &a, const CellRef *cells, int ncells,
                               cudaStream_t st);
 cudaError_t launch_ghosts_f64(double *reg, const DevBlock *blocks, const GhostCopy *list, int n,

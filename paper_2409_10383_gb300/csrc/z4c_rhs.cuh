@@ -175,6 +175,51 @@ struct Phys {
   int lapse, shift;
 };
 
+// Derivative providers.  Direct evaluates every stencil from the state;
+// Pre takes the y and z first derivatives of the eleven fields that also
+// need mixed second derivatives (chi, gt_ij, alpha, beta^i) from arrays
+// filled by a preceding pass, so that d_x d_y f = D_x (D_y f),
+// d_x d_z f = D_x (D_z f) and d_y d_z f = D_y (D_z f) are one first-derivative
+// stencil each (the tensor-product definition, evaluated in two passes).
+template <int ORD, class R, class SRC>
+struct Direct {
+  const SRC &s;
+  const int *st;
+  Scales<R> sc;
+  __device__ __forceinline__ R d1(int f, int d) const { return FD<ORD>::d1(s, f, st[d]) * sc.s1; }
+  __device__ __forceinline__ R d2(int f, int d) const { return FD<ORD>::d2(s, f, st[d]) * sc.s2; }
+  __device__ __forceinline__ R mix(int f, int a, int b) const {
+    return FD<ORD>::mix(s, f, st[a], st[b]) * sc.smix;
+  }
+};
+
+// slot of a field in the stored-derivative arrays (-1: not stored);
+// arrays 0..10 hold D_y f, arrays 11..21 hold D_z f
+__host__ __device__ constexpr int dslot(int f) {
+  return f == CHI ? 0 : (f >= GXX && f <= GZZ) ? f - GXX + 1 : f == ALPHA ? 7 : (f >= BETAX) ? f - BETAX + 8 : -1;
+}
+constexpr int NDS = 11;
+
+template <int ORD, class R, class SRC, class DS>
+struct Pre {
+  const SRC &s;
+  const DS &ds;  // stored derivatives at this cell (already multiplied by s1)
+  const int *st;
+  Scales<R> sc;
+  __device__ __forceinline__ R d1(int f, int d) const {
+    const int q = dslot(f);
+    if (d > 0 && q >= 0) return ds.at(q + (d - 1) * NDS, 0);
+    return FD<ORD>::d1(s, f, st[d]) * sc.s1;
+  }
+  __device__ __forceinline__ R d2(int f, int d) const { return FD<ORD>::d2(s, f, st[d]) * sc.s2; }
+  __device__ __forceinline__ R mix(int f, int a, int b) const {
+    const int q = dslot(f);
+    if (a == 0 && b == 1) return FD<ORD>::d1(ds, q, st[0]) * sc.s1;         // D_x (D_y f)
+    if (a == 0 && b == 2) return FD<ORD>::d1(ds, q + NDS, st[0]) * sc.s1;   // D_x (D_z f)
+    return FD<ORD>::d1(ds, q + NDS, st[1]) * sc.s1;                         // D_y (D_z f)
+  }
+};
+
 template <class R>
 __device__ __forceinline__ R trsym(const R gi[6], const R X[6]) {  // gt^ij X_ij
   return gi[0] * X[0] + gi[3] * X[3] + gi[5] * X[5] + R(2) * (gi[1] * X[1] + gi[2] * X[2] + gi[4] * X[4]);
@@ -227,12 +272,11 @@ __device__ __forceinline__ void christoffel(const R gi[6], const R dg[3][6], R G
 //   Rchi_ij = (DDchi_ij + gt_ij gt^lm DDchi_lm) / (2 chi)
 //             - (d_i chi d_j chi + 3 gt_ij gt^lm d_l chi d_m chi) / (4 chi^2)
 // with DDchi_ij = d_i d_j chi - Gt^k_ij d_k chi and 1/chi -> ichi.
-template <int ORD, class R, class SRC>
-__device__ __forceinline__ void ricci(const SRC &s, const int st[3], const Scales<R> &sc, R ichi,
+template <class R, class DV>
+__device__ __forceinline__ void ricci(const DV &dv, R ichi,
                                       const R g[6], const R gi[6], const R dchi[3],
                                       const R dGam[3][3], const R Gl[3][6], const R Gu[3][6],
                                       const R Gd[3], const R DDchi[6], R Ric[6]) {
-  using F = FD<ORD>;
   // U[k][m][i] = gt^lm Gt^k_li ; V[k][m][j] = gt^lm Gt_klj
   R U[3][3][3], V[3][3][3];
 #pragma unroll
@@ -254,12 +298,12 @@ __device__ __forceinline__ void ricci(const SRC &s, const int st[3], const Scale
     for (int j = i; j < 3; ++j) {
       const int q = S6(i, j);
       R dd[6];
-      dd[0] = F::d2(s, GXX + q, st[0]) * sc.s2;
-      dd[3] = F::d2(s, GXX + q, st[1]) * sc.s2;
-      dd[5] = F::d2(s, GXX + q, st[2]) * sc.s2;
-      dd[1] = F::mix(s, GXX + q, st[0], st[1]) * sc.smix;
-      dd[2] = F::mix(s, GXX + q, st[0], st[2]) * sc.smix;
-      dd[4] = F::mix(s, GXX + q, st[1], st[2]) * sc.smix;
+      dd[0] = dv.d2(GXX + q, 0);
+      dd[3] = dv.d2(GXX + q, 1);
+      dd[5] = dv.d2(GXX + q, 2);
+      dd[1] = dv.mix(GXX + q, 0, 1);
+      dd[2] = dv.mix(GXX + q, 0, 2);
+      dd[4] = dv.mix(GXX + q, 1, 2);
       R r = R(-0.5) * trsym(gi, dd);
       R t = R(0);
 #pragma unroll
@@ -285,8 +329,8 @@ __device__ __forceinline__ void ricci(const SRC &s, const int st[3], const Scale
 
 // Z4c right-hand side at one interior cell.  ichi = 1 / max(chi, chi_floor)
 // (computed by the caller in FP64).  st = element strides (1, e0, e0 e1).
-template <int ORD, class R, class SRC>
-__device__ __forceinline__ void rhs_point(const SRC &s, const int st[3], const Scales<R> &sc,
+template <int ORD, class R, class SRC, class DV>
+__device__ __forceinline__ void rhs_point(const SRC &s, const DV &dv, const int st[3], const Scales<R> &sc,
                                           const Phys<R> &p, R ichi, R k[NF]) {
   using F = FD<ORD>;
   const R chi = s.val(CHI), Khat = s.val(KHAT), Theta = s.val(THETA), al = s.val(ALPHA);
@@ -308,17 +352,17 @@ __device__ __forceinline__ void rhs_point(const SRC &s, const int st[3], const S
   R dchi[3], dal[3], dKhat[3], dTheta[3], dbeta[3][3], dGam[3][3], dg[3][6];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    dchi[d] = F::d1(s, CHI, st[d]) * sc.s1;
-    dal[d] = F::d1(s, ALPHA, st[d]) * sc.s1;
-    dKhat[d] = F::d1(s, KHAT, st[d]) * sc.s1;
-    dTheta[d] = F::d1(s, THETA, st[d]) * sc.s1;
+    dchi[d] = dv.d1(CHI, d);
+    dal[d] = dv.d1(ALPHA, d);
+    dKhat[d] = dv.d1(KHAT, d);
+    dTheta[d] = dv.d1(THETA, d);
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      dbeta[d][i] = F::d1(s, BETAX + i, st[d]) * sc.s1;
-      dGam[d][i] = F::d1(s, GAMX + i, st[d]) * sc.s1;
+      dbeta[d][i] = dv.d1(BETAX + i, d);
+      dGam[d][i] = dv.d1(GAMX + i, d);
     }
 #pragma unroll
-    for (int q = 0; q < 6; ++q) dg[d][q] = F::d1(s, GXX + q, st[d]) * sc.s1;
+    for (int q = 0; q < 6; ++q) dg[d][q] = dv.d1(GXX + q, d);
   }
 
   R Gl[3][6], Gu[3][6], Gd[3];
@@ -333,11 +377,11 @@ __device__ __forceinline__ void rhs_point(const SRC &s, const int st[3], const S
       const int q = S6(i, j);
       R ddc, dda;
       if (i == j) {
-        ddc = F::d2(s, CHI, st[i]) * sc.s2;
-        dda = F::d2(s, ALPHA, st[i]) * sc.s2;
+        ddc = dv.d2(CHI, i);
+        dda = dv.d2(ALPHA, i);
       } else {
-        ddc = F::mix(s, CHI, st[i], st[j]) * sc.smix;
-        dda = F::mix(s, ALPHA, st[i], st[j]) * sc.smix;
+        ddc = dv.mix(CHI, i, j);
+        dda = dv.mix(ALPHA, i, j);
       }
       DDchi[q] = ddc - (Gu[0][q] * dchi[0] + Gu[1][q] * dchi[1] + Gu[2][q] * dchi[2]);
       DDa0[q] = dda - (Gu[0][q] * dal[0] + Gu[1][q] * dal[1] + Gu[2][q] * dal[2]);
@@ -346,7 +390,7 @@ __device__ __forceinline__ void rhs_point(const SRC &s, const int st[3], const S
   auto quad = [&](const R *a, const R *b) { return z4c::quad(gi, a, b); };
 
   R Ric[6];
-  ricci<ORD>(s, st, sc, ichi, g, gi, dchi, dGam, Gl, Gu, Gd, DDchi, Ric);
+  ricci(dv, ichi, g, gi, dchi, dGam, Gl, Gu, Gd, DDchi, Ric);
   const R Rs = chi * trsym(Ric);
 
   // D_i D_j alpha and its trace
@@ -422,12 +466,12 @@ __device__ __forceinline__ void rhs_point(const SRC &s, const int st[3], const S
     R ddb[3][6];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      ddb[i][0] = F::d2(s, BETAX + i, st[0]) * sc.s2;
-      ddb[i][3] = F::d2(s, BETAX + i, st[1]) * sc.s2;
-      ddb[i][5] = F::d2(s, BETAX + i, st[2]) * sc.s2;
-      ddb[i][1] = F::mix(s, BETAX + i, st[0], st[1]) * sc.smix;
-      ddb[i][2] = F::mix(s, BETAX + i, st[0], st[2]) * sc.smix;
-      ddb[i][4] = F::mix(s, BETAX + i, st[1], st[2]) * sc.smix;
+      ddb[i][0] = dv.d2(BETAX + i, 0);
+      ddb[i][3] = dv.d2(BETAX + i, 1);
+      ddb[i][5] = dv.d2(BETAX + i, 2);
+      ddb[i][1] = dv.mix(BETAX + i, 0, 1);
+      ddb[i][2] = dv.mix(BETAX + i, 0, 2);
+      ddb[i][4] = dv.mix(BETAX + i, 1, 2);
     }
     R ddivb[3];
 #pragma unroll
@@ -520,7 +564,8 @@ __device__ __forceinline__ void constraints_point(const SRC &s, const int st[3],
       DDchi[q] = ddc - (Gu[0][q] * dchi[0] + Gu[1][q] * dchi[1] + Gu[2][q] * dchi[2]);
     }
   R Ric[6];
-  ricci<ORD>(s, st, sc, ichi, g, gi, dchi, dGam, Gl, Gu, Gd, DDchi, Ric);
+  const Direct<ORD, double, SRC> dv{s, st, sc};
+  ricci(dv, ichi, g, gi, dchi, dGam, Gl, Gu, Gd, DDchi, Ric);
   // At^ij and At_ij At^ij
   R M[3][3];
 #pragma unroll

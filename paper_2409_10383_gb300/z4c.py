@@ -43,7 +43,7 @@ class z4c_params(ctypes.Structure):
                 ("kappa2", ctypes.c_double), ("eta", ctypes.c_double),
                 ("chi_floor", ctypes.c_double), ("cfl", ctypes.c_double),
                 ("lapse", ctypes.c_int32), ("shift", ctypes.c_int32),
-                ("rhs_precision", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("rhs_precision", ctypes.c_int32), ("schedule", ctypes.c_int32)]
 
 
 _lib = None
@@ -110,7 +110,7 @@ class Z4c:
 
     def __init__(self, n, lo, h, ghosts, order, dom_lo, dom_hi, periodic, ko_sigma=0.0,
                  kappa1=0.0, kappa2=0.0, eta=2.0, chi_floor=1e-6, lapse=1, shift=1, precision=64,
-                 device="cuda", stream=None, **_):
+                 schedule=0, device="cuda", stream=None, **_):
         import torch
         self.torch = torch
         n = np.asarray(n).reshape(-1, 3)
@@ -130,7 +130,7 @@ class Z4c:
             B.h = float(h[b])
             self.blocks.append(B)
         self.params = z4c_params(ko_sigma, kappa1, kappa2, eta, chi_floor, 0.25, lapse, shift,
-                                 precision, 0)
+                                 precision, schedule)
         self.n, self.ghosts, self.order = n, ghosts, order
         rc, self.ctx = z4c_create(self.mesh, self.blocks, ghosts, order, self.params)
         _check(rc, None, "z4c_create")
@@ -229,7 +229,7 @@ class Z4c:
         _check(lib().z4c_sync(self.ctx), self.ctx, "z4c_sync")
 
     def z4c_profile_steps(self, dt, nsteps):
-        ms = np.zeros(3)
+        ms = np.zeros(4)
         _check(lib().z4c_profile_steps(self.ctx, float(dt), int(nsteps), ms.ctypes.data), self.ctx,
                "z4c_profile_steps")
         return ms

@@ -13,9 +13,9 @@ def oracle_mesh(oracle, w):
                        **{k: w[k] for k in PARAM_KEYS})
 
 
-def gpu_ctx(w, precision=64):
+def gpu_ctx(w, precision=64, schedule=0):
     from paper_2409_10383_gb300.z4c import Z4c
-    return Z4c.from_workload(w, precision=precision)
+    return Z4c.from_workload(w, precision=precision, schedule=schedule)
 
 
 def small_workload(kind, order, nb=(1, 1, 1), n=16, periodic=None, **over):

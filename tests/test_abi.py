@@ -49,8 +49,8 @@ def _block(n=32, lo=(-0.5, -0.5, -0.5), h=1 / 32):
     return b
 
 
-def _params(prec=64):
-    return z4c.z4c_params(0.02, 0, 0, 0, 1e-6, 0.25, 0, 0, prec, 0)
+def _params(prec=64, schedule=0):
+    return z4c.z4c_params(0.02, 0, 0, 0, 1e-6, 0.25, 0, 0, prec, schedule)
 
 
 def test_create_validates_arguments(L):
@@ -80,5 +80,10 @@ def test_sizes_and_unbound_calls(L):
     assert sc.value >= 2 * 22 * 38 ** 3 * 4  # two FP32 shadows
     assert L.z4c_rk4_step(ctx, 0.01, 1) == z4c.Z4C_ERR_NOT_BOUND
     assert b"z4c_bind" in L.z4c_last_error(ctx)
-    assert L.z4c_launches_per_step(ctx) == 8  # periodic: ghost fill + interior per stage
+    # periodic, default schedule: ghost fill + pre-pass + fused interior per stage
+    assert L.z4c_launches_per_step(ctx) == 12
     L.z4c_destroy(ctx)
+    rc, ctx = z4c.z4c_create(_mesh(), [_block()], 3, 4, _params(64, schedule=1))
+    assert rc == 0 and L.z4c_launches_per_step(ctx) == 8  # single fused kernel
+    L.z4c_destroy(ctx)
+    assert z4c.z4c_create(_mesh(), [_block()], 3, 4, _params(64, schedule=3))[0] == z4c.Z4C_ERR_BAD_ARG

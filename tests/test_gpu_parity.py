@@ -71,12 +71,15 @@ def _random_generic_state(m, w, seed):
     return u
 
 
+@pytest.mark.parametrize("schedule", [1, 2])
 @pytest.mark.parametrize("kind,order,nb,n,per", CASES)
-def test_rhs_parity_fp64(oracle, kind, order, nb, n, per):
+def test_rhs_parity_fp64(oracle, kind, order, nb, n, per, schedule):
+    """schedule 1: one fused kernel; 2: y/z first-derivative pre-pass + fused
+    kernel forming mixed derivatives from the stored values."""
     w = H.small_workload(kind, order, nb, n, per, lapse=1, shift=1, kappa1=0.05, kappa2=0.1,
                          eta=1.5, ko_sigma=0.3)
     m = H.oracle_mesh(oracle, w)
-    g = H.gpu_ctx(w)
+    g = H.gpu_ctx(w, schedule=schedule)
     u = _random_generic_state(m, w, seed=5 + order)
     g.z4c_set_state(u, reg=1)
     ref = m.rhs(u)
@@ -89,10 +92,11 @@ def test_rhs_parity_fp64(oracle, kind, order, nb, n, per):
         assert np.all(m.blocks(got)[b][:, ng] == 0)
 
 
+@pytest.mark.parametrize("schedule", [1, 2])
 @pytest.mark.parametrize("precision", [64, 32])
-def test_flat_space_is_exactly_static(oracle, precision):
+def test_flat_space_is_exactly_static(oracle, precision, schedule):
     w = H.small_workload("puncture", 6, (2, 1, 1), 12, id_kind=inputs.ID_FLAT, id_par=[])
-    g = H.gpu_ctx(w, precision)
+    g = H.gpu_ctx(w, precision, schedule)
     g.z4c_set_initial_data(inputs.ID_FLAT, [])
     g.z4c_fill_ghosts(0)
     assert np.all(g.z4c_rhs(0).cpu().numpy() == 0.0)
@@ -120,11 +124,12 @@ def test_gauge_wave_config_ten_steps(oracle):
     assert rel.max() <= STEP_TOL, (rel, absd)
 
 
+@pytest.mark.parametrize("schedule", [1, 2])
 @pytest.mark.parametrize("order,nb,n", [(6, (2, 2, 2), 16), (4, (1, 2, 1), (12, 10, 16))])
-def test_puncture_rk4_parity(oracle, order, nb, n):
+def test_puncture_rk4_parity(oracle, order, nb, n, schedule):
     w = H.small_workload("puncture", order, nb, n)
     m = H.oracle_mesh(oracle, w)
-    g = H.gpu_ctx(w)
+    g = H.gpu_ctx(w, schedule=schedule)
     g.z4c_set_initial_data(w["id_kind"], w["id_par"])
     u = m.initial_data(w["id_kind"], w["id_par"])
     dt = 0.25 * float(w["h"][0])
@@ -177,7 +182,8 @@ def _round_like_shadow(m, u):
     return v
 
 
-def test_fp32_rhs_error_budget(oracle):
+@pytest.mark.parametrize("schedule", [1, 2])
+def test_fp32_rhs_error_budget(oracle, schedule):
     """FP32 stencils and algebra (FP64 state, RK accumulation, 1/chi,
     enforcement).  Bounds, stated against what FP32 storage alone causes:
       - one RHS call: per-field error <= 8x the error of the FP64 oracle fed
@@ -186,7 +192,7 @@ def test_fp32_rhs_error_budget(oracle):
         change |u64(t) - u64(0)|, and ||H||_2 within 1e-5 (relative) of FP64."""
     w = H.small_workload("puncture", 6, (2, 2, 2), 16)
     m = H.oracle_mesh(oracle, w)
-    g = H.gpu_ctx(w, precision=32)
+    g = H.gpu_ctx(w, precision=32, schedule=schedule)
     u = m.initial_data(w["id_kind"], w["id_par"])
     m.fill_ghosts(u)
     ref = m.rhs(u)
