@@ -189,6 +189,21 @@ int z4c_sync(z4c_ctx *ctx);
  * Advances U0 exactly like z4c_rk4_step.  Synchronous. */
 int z4c_profile_steps(z4c_ctx *ctx, double dt, int nsteps, double *ms);
 
+/* Select a kernel variant explicitly: schedule 1 or 2 (see z4c_params) and
+ * occupancy, the resident CTAs per SM the fused kernel's registers are
+ * budgeted for: 1 always; 2 or 4 for the FP32-RHS schedule-2 kernel.  Other
+ * combinations return Z4C_ERR_UNSUPPORTED.  Makes no CUDA call. */
+int z4c_set_variant(z4c_ctx *ctx, int schedule, int occupancy);
+
+/* Pick the fastest kernel variant for this context on this GPU: the
+ * schedule (1 or 2, see z4c_params) and, for the FP32-RHS fused kernel, the
+ * number of resident CTAs per SM its registers are budgeted for (1, 2, 4).
+ * Each candidate runs reps + 1 times the ghost fill and stage 1 of RK4 (which
+ * reads U0 and overwrites only the accumulator and stage A, so U0 keeps its
+ * value); the fastest is kept and reported (either pointer may be NULL).
+ * Synchronous.  Call before z4c_rk4_step, or it re-captures its graph. */
+int z4c_autotune(z4c_ctx *ctx, int reps, int *schedule_out, int *occupancy_out);
+
 /* Measurement aid: FP64 (fp64 = 1) or FP32 (fp64 = 0) fused multiply-add
  * throughput of the current device in FLOP/s, from independent FMA chains
  * with no memory traffic (the ALU roofline of the RHS kernels).  Enqueued on

@@ -45,9 +45,11 @@ struct z4c_ctx {
   double graph_dt = 0.0;
   std::string err;
 
+  int sched = 2;  // 1 single fused kernel, 2 pre-pass + fused kernel
+  int occ = 1;    // resident CTAs per SM the fused kernel is compiled for (1, 2, 4)
   bool f32() const { return params.rhs_precision == 32; }
-  bool pre() const { return !wtiles.empty(); }
-  const Tile *d_wtiles() const { return pre() ? (const Tile *)(scratch + o_wtiles) : nullptr; }
+  bool pre() const { return sched == 2; }
+  const Tile *d_wtiles() const { return (const Tile *)(scratch + o_wtiles); }
   void *d_dstore() const { return pre() ? (void *)(scratch + o_dstore) : nullptr; }
   const DevBlock *d_blocks() const { return (const DevBlock *)(scratch + o_blocks); }
   const Tile *d_tiles() const { return (const Tile *)(scratch + o_tiles); }
@@ -195,9 +197,11 @@ int z4c_create(const z4c_mesh *mesh, const z4c_block *blocks, int nblocks, int g
       for (int j0 = 0; j0 < n[1]; j0 += TY)
         for (int i0 = 0; i0 < n[0]; i0 += TX) ctx->tiles.push_back(Tile{b, i0, j0, k});
   // schedule: 0 = default (the pre-pass, faster for both precisions),
-  // 1 = single fused kernel, 2 = y/z pre-pass + fused kernel
-  const bool use_pre = params->schedule != 1;
-  if (use_pre) {
+  // 1 = single fused kernel, 2 = y/z pre-pass + fused kernel.  The tables
+  // of both are built so that z4c_autotune can switch.
+  ctx->sched = params->schedule == 1 ? 1 : 2;
+  ctx->occ = params->rhs_precision == 32 ? 4 : 1;
+  {
     const int W = fd_order / 2;
     for (int b = 0; b < nblocks; ++b)
       for (int k = 0; k < n[2]; ++k)
@@ -259,7 +263,7 @@ int z4c_create(const z4c_mesh *mesh, const z4c_block *blocks, int nblocks, int g
     ctx->o_sh1 = o;
     o = align256(o + sizeof(float) * ctx->reg_elems);
   }
-  if (use_pre) {
+  {
     ctx->o_dstore = o;
     o = align256(o + (ctx->f32() ? sizeof(float) : sizeof(double)) * ctx->reg_elems);
   }
@@ -337,14 +341,34 @@ int fill_ghosts_f32(z4c_ctx *ctx, float *reg) {
   return Z4C_OK;
 }
 
+int launch_prepass(z4c_ctx *ctx, const StageArgs &a) {
+  if (!ctx->pre()) return Z4C_OK;
+  const int nw = (int)ctx->wtiles.size();
+  CK(ctx->f32() ? launch_prepass_f32(ctx->order, a, ctx->d_wtiles(), nw, ctx->stream)
+                : launch_prepass_f64(ctx->order, a, ctx->d_wtiles(), nw, ctx->stream));
+  return Z4C_OK;
+}
+
+int launch_fused(z4c_ctx *ctx, const StageArgs &a) {
+  const int nt = (int)ctx->tiles.size();
+  if (!ctx->f32()) {
+    CK(launch_fused_f64(ctx->order, a, ctx->d_tiles(), nt, ctx->pre(), ctx->stream));
+  } else if (ctx->pre() && ctx->occ == 4) {
+    CK(launch_fused_pre_f32_occ4(ctx->order, a, ctx->d_tiles(), nt, ctx->stream));
+  } else if (ctx->pre() && ctx->occ == 2) {
+    CK(launch_fused_pre_f32_occ2(ctx->order, a, ctx->d_tiles(), nt, ctx->stream));
+  } else {
+    CK(launch_fused_f32(ctx->order, a, ctx->d_tiles(), nt, ctx->pre(), ctx->stream));
+  }
+  return Z4C_OK;
+}
+
 int launch_stage(z4c_ctx *ctx, StageArgs a) {
   a.dstore = ctx->d_dstore();
-  if (ctx->f32())
-    CK(launch_interior_f32(ctx->order, a, ctx->d_tiles(), (int)ctx->tiles.size(), ctx->d_wtiles(),
-                           (int)ctx->wtiles.size(), ctx->stream));
-  else
-    CK(launch_interior_f64(ctx->order, a, ctx->d_tiles(), (int)ctx->tiles.size(), ctx->d_wtiles(),
-                           (int)ctx->wtiles.size(), ctx->stream));
+  int r = launch_prepass(ctx, a);
+  if (r) return r;
+  r = launch_fused(ctx, a);
+  if (r) return r;
   CK(launch_sommerfeld(ctx->f32(), a, ctx->d_somm(), (int)ctx->somm.size(), ctx->stream));
   return Z4C_OK;
 }
@@ -367,6 +391,8 @@ int enqueue_step(z4c_ctx *ctx, double dt) {
     a.next = NX[s];
     a.ca = ca[s];
     a.cb = cb[s];
+    a.caf = (float)ca[s];
+    a.cbf = (float)cb[s];
     a.mode = mode[s];
     if (ctx->f32()) {
       float *sh = ctx->d_sh(s % 2), *nsh = ctx->d_sh((s + 1) % 2);
@@ -574,6 +600,8 @@ int z4c_profile_steps(z4c_ctx *ctx, double dt, int nsteps, double *ms) {
       a.next = NX[s];
       a.ca = ca[s];
       a.cb = cb[s];
+      a.caf = (float)ca[s];
+      a.cbf = (float)cb[s];
       a.mode = mode[s];
       float *sh = nullptr;
       if (ctx->f32()) {
@@ -591,18 +619,11 @@ int z4c_profile_steps(z4c_ctx *ctx, double dt, int nsteps, double *ms) {
         if (r) return r;
       }
       a.dstore = ctx->d_dstore();
-      const int nw = (int)ctx->wtiles.size();
-      if (nw) {  // pre-pass alone, then the fused kernel (which reads its output)
-        r = timed(3, [&] {
-          return ctx->f32() ? launch_prepass_f32(ctx->order, a, ctx->d_wtiles(), nw, ctx->stream)
-                            : launch_prepass_f64(ctx->order, a, ctx->d_wtiles(), nw, ctx->stream);
-        });
+      if (ctx->pre()) {
+        r = timed(3, [&] { return launch_prepass(ctx, a) ? cudaErrorUnknown : cudaSuccess; });
         if (r) return r;
       }
-      r = timed(1, [&] {
-        return ctx->f32() ? launch_fused_f32(ctx->order, a, ctx->d_tiles(), nt, nw > 0, ctx->stream)
-                          : launch_fused_f64(ctx->order, a, ctx->d_tiles(), nt, nw > 0, ctx->stream);
-      });
+      r = timed(1, [&] { return launch_fused(ctx, a) ? cudaErrorUnknown : cudaSuccess; });
       if (r) return r;
       if (ns) {
         r = timed(2, [&] { return launch_sommerfeld(ctx->f32(), a, ctx->d_somm(), ns, ctx->stream); });
@@ -612,6 +633,83 @@ int z4c_profile_steps(z4c_ctx *ctx, double dt, int nsteps, double *ms) {
   cudaEventDestroy(ev[0]);
   cudaEventDestroy(ev[1]);
   for (int q = 0; q < 4; ++q) ms[q] = acc[q] / nsteps;
+  return Z4C_OK;
+}
+
+int z4c_set_variant(z4c_ctx *ctx, int schedule, int occupancy) {
+  if (!ctx) return Z4C_ERR_BAD_ARG;
+  if (schedule != 1 && schedule != 2) return fail(ctx, Z4C_ERR_BAD_ARG, "schedule must be 1 or 2");
+  const bool ok = occupancy == 1 || (ctx->f32() && schedule == 2 && (occupancy == 2 || occupancy == 4));
+  if (!ok) return fail(ctx, Z4C_ERR_UNSUPPORTED, "no kernel built for this schedule/occupancy");
+  ctx->sched = schedule;
+  ctx->occ = occupancy;
+  if (ctx->graph) {
+    cudaGraphExecDestroy(ctx->graph);
+    ctx->graph = nullptr;
+  }
+  return Z4C_OK;
+}
+
+int z4c_autotune(z4c_ctx *ctx, int reps, int *schedule_out, int *occupancy_out) {
+  int r = ensure_bound(ctx);
+  if (r) return r;
+  if (reps < 1) return fail(ctx, Z4C_ERR_BAD_ARG, "reps must be >= 1");
+  r = ensure_shadow(ctx);
+  if (r) return r;
+  // stage 1 reads U0 (and its FP32 shadow) and writes ACC and stage A only
+  StageArgs a{};
+  a.blocks = ctx->d_blocks();
+  a.x64 = ctx->reg[0];
+  a.u0 = ctx->reg[0];
+  a.acc = ctx->reg[3];
+  a.next = ctx->reg[1];
+  a.ca = a.cb = 0.0;
+  a.caf = a.cbf = 0.0f;
+  a.mode = MODE_S1;
+  if (ctx->f32()) {
+    a.x32 = ctx->d_sh(0);
+    a.next32 = ctx->d_sh(1);
+  }
+  struct Cand { int sched, occ; };
+  std::vector<Cand> cands = {{1, 1}, {2, 1}};
+  if (ctx->f32()) {
+    cands.push_back({2, 2});
+    cands.push_back({2, 4});
+  }
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  float best = 1e30f;
+  Cand pick = {ctx->sched, ctx->occ};
+  for (const Cand &c : cands) {
+    ctx->sched = c.sched;
+    ctx->occ = c.occ;
+    for (int rep = 0; rep <= reps; ++rep) {  // first pass untimed
+      if (rep == 1) CK(cudaEventRecord(e0, ctx->stream));
+      r = ctx->f32() ? fill_ghosts_f32(ctx, ctx->d_sh(0)) : fill_ghosts_f64(ctx, ctx->reg[0]);
+      if (r) return r;
+      r = launch_stage(ctx, a);
+      if (r) return r;
+    }
+    CK(cudaEventRecord(e1, ctx->stream));
+    CK(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best) {
+      best = ms;
+      pick = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  ctx->sched = pick.sched;
+  ctx->occ = pick.occ;
+  if (ctx->graph) {  // the next z4c_rk4_step captures the chosen kernels
+    cudaGraphExecDestroy(ctx->graph);
+    ctx->graph = nullptr;
+  }
+  if (schedule_out) *schedule_out = pick.sched;
+  if (occupancy_out) *occupancy_out = pick.occ;
   return Z4C_OK;
 }
 

@@ -22,8 +22,12 @@ __global__ void __launch_bounds__(TX * TY) interior_kernel(StageArgs a, const Ti
   const int st[3] = {1, e0, e0 * e1};
   const int64_t off = b.off + cidx;
   // 1/chi with the chi floor, always in FP64
-  const double chig = fmax(a.x64[off], b.chi_floor);
-  const R ichi = R(1.0 / chig);
+  // 1/max(chi, chi_floor), always from the FP64 stage state
+  R ichi;
+  if constexpr (F32)
+    ichi = inv_chi_f32(a.x64[off], b.chi_floor);
+  else
+    ichi = 1.0 / fmax(a.x64[off], b.chi_floor);
   const Phys<R> p{R(b.kappa1), R(b.kappa2), R(b.eta), b.lapse, b.shift};
   R k[NF];
   if constexpr (F32) {
@@ -86,8 +90,10 @@ __global__ void __launch_bounds__(TX * TY) dydz_kernel(StageArgs a, const Tile *
 
 // Interior stage kernel taking the y/z first derivatives and the mixed
 // second derivatives of the eleven fields from the pre-pass arrays.
-template <int ORD, bool F32>
-__global__ void __launch_bounds__(TX * TY) interior_pre_kernel(StageArgs a, const Tile *__restrict__ tiles) {
+// OCC = minimum resident CTAs per SM the register allocation must allow
+// (1: up to 255 registers per thread; 4: 128), chosen by the autotuner.
+template <int ORD, bool F32, int OCC>
+__global__ void __launch_bounds__(TX * TY, OCC) interior_pre_kernel(StageArgs a, const Tile *__restrict__ tiles) {
   using R = typename std::conditional<F32, float, double>::type;
   const Tile t = tiles[blockIdx.x];
   const DevBlock &b = a.blocks[t.block];
@@ -97,8 +103,12 @@ __global__ void __launch_bounds__(TX * TY) interior_pre_kernel(StageArgs a, cons
   const int32_t cidx = ((kk + g) * e1 + (j + g)) * e0 + (i + g);
   const int st[3] = {1, e0, e0 * e1};
   const int64_t off = b.off + cidx;
-  const double chig = fmax(a.x64[off], b.chi_floor);
-  const R ichi = R(1.0 / chig);
+  // 1/max(chi, chi_floor), always from the FP64 stage state
+  R ichi;
+  if constexpr (F32)
+    ichi = inv_chi_f32(a.x64[off], b.chi_floor);
+  else
+    ichi = 1.0 / fmax(a.x64[off], b.chi_floor);
   const Phys<R> p{R(b.kappa1), R(b.kappa2), R(b.eta), b.lapse, b.shift};
   R k[NF];
   const Src<R, false> ds{reinterpret_cast<const R *>(a.dstore) + off, b.S};

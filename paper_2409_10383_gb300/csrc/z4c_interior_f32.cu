@@ -1,36 +1,11 @@
-// FP32-RHS instantiations of the fused interior stage kernel: stencils and
-// RHS algebra in FP32 from the FP32 shadow; 1/chi, RK update and constraint
-// enforcement in FP64.
+// FP32-RHS instantiations of the interior kernels: stencils and RHS algebra in
+// FP32 from the FP32 shadow; 1/chi, RK update and enforcement in FP64.
 #include <type_traits>
 
 #include "z4c_interior.cuh"
 
 namespace z4c {
-template <bool F32>
-cudaError_t launch_interior(int order, const StageArgs &a, const Tile *tiles, int ntiles, const Tile *wtiles,
-                            int nwtiles, cudaStream_t st) {
-  if (ntiles <= 0) return cudaSuccess;
-  dim3 block(TX, TY);
-  if (wtiles) {
-    if (order == 4) {
-      dydz_kernel<4, F32><<<nwtiles, block, 0, st>>>(a, wtiles);
-      interior_pre_kernel<4, F32><<<ntiles, block, 0, st>>>(a, tiles);
-    } else {
-      dydz_kernel<6, F32><<<nwtiles, block, 0, st>>>(a, wtiles);
-      interior_pre_kernel<6, F32><<<ntiles, block, 0, st>>>(a, tiles);
-    }
-  } else if (order == 4) {
-    interior_kernel<4, F32><<<ntiles, block, 0, st>>>(a, tiles);
-  } else {
-    interior_kernel<6, F32><<<ntiles, block, 0, st>>>(a, tiles);
-  }
-  return cudaGetLastError();
-}
 
-cudaError_t launch_interior_f32(int order, const StageArgs &a, const Tile *tiles, int ntiles,
-                                const Tile *wtiles, int nwtiles, cudaStream_t st) {
-  return launch_interior<true>(order, a, tiles, ntiles, wtiles, nwtiles, st);
-}
 cudaError_t launch_prepass_f32(int order, const StageArgs &a, const Tile *wtiles, int nwtiles, cudaStream_t st) {
   if (nwtiles <= 0) return cudaSuccess;
   dim3 block(TX, TY);
@@ -40,15 +15,16 @@ cudaError_t launch_prepass_f32(int order, const StageArgs &a, const Tile *wtiles
     dydz_kernel<6, true><<<nwtiles, block, 0, st>>>(a, wtiles);
   return cudaGetLastError();
 }
+
 cudaError_t launch_fused_f32(int order, const StageArgs &a, const Tile *tiles, int ntiles, bool pre,
                              cudaStream_t st) {
   if (ntiles <= 0) return cudaSuccess;
   dim3 block(TX, TY);
   if (pre) {
     if (order == 4)
-      interior_pre_kernel<4, true><<<ntiles, block, 0, st>>>(a, tiles);
+      interior_pre_kernel<4, true, 1><<<ntiles, block, 0, st>>>(a, tiles);
     else
-      interior_pre_kernel<6, true><<<ntiles, block, 0, st>>>(a, tiles);
+      interior_pre_kernel<6, true, 1><<<ntiles, block, 0, st>>>(a, tiles);
   } else if (order == 4) {
     interior_kernel<4, true><<<ntiles, block, 0, st>>>(a, tiles);
   } else {
@@ -56,4 +32,5 @@ cudaError_t launch_fused_f32(int order, const StageArgs &a, const Tile *tiles, i
   }
   return cudaGetLastError();
 }
+
 }  // namespace z4c

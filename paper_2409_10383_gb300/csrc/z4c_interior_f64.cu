@@ -1,34 +1,10 @@
-// FP64 instantiations of the fused interior stage kernel.
+// FP64 instantiations of the interior kernels.
 #include <type_traits>
 
 #include "z4c_interior.cuh"
 
 namespace z4c {
-template <bool F32>
-cudaError_t launch_interior(int order, const StageArgs &a, const Tile *tiles, int ntiles, const Tile *wtiles,
-                            int nwtiles, cudaStream_t st) {
-  if (ntiles <= 0) return cudaSuccess;
-  dim3 block(TX, TY);
-  if (wtiles) {
-    if (order == 4) {
-      dydz_kernel<4, F32><<<nwtiles, block, 0, st>>>(a, wtiles);
-      interior_pre_kernel<4, F32><<<ntiles, block, 0, st>>>(a, tiles);
-    } else {
-      dydz_kernel<6, F32><<<nwtiles, block, 0, st>>>(a, wtiles);
-      interior_pre_kernel<6, F32><<<ntiles, block, 0, st>>>(a, tiles);
-    }
-  } else if (order == 4) {
-    interior_kernel<4, F32><<<ntiles, block, 0, st>>>(a, tiles);
-  } else {
-    interior_kernel<6, F32><<<ntiles, block, 0, st>>>(a, tiles);
-  }
-  return cudaGetLastError();
-}
 
-cudaError_t launch_interior_f64(int order, const StageArgs &a, const Tile *tiles, int ntiles,
-                                const Tile *wtiles, int nwtiles, cudaStream_t st) {
-  return launch_interior<false>(order, a, tiles, ntiles, wtiles, nwtiles, st);
-}
 cudaError_t launch_prepass_f64(int order, const StageArgs &a, const Tile *wtiles, int nwtiles, cudaStream_t st) {
   if (nwtiles <= 0) return cudaSuccess;
   dim3 block(TX, TY);
@@ -38,15 +14,16 @@ cudaError_t launch_prepass_f64(int order, const StageArgs &a, const Tile *wtiles
     dydz_kernel<6, false><<<nwtiles, block, 0, st>>>(a, wtiles);
   return cudaGetLastError();
 }
+
 cudaError_t launch_fused_f64(int order, const StageArgs &a, const Tile *tiles, int ntiles, bool pre,
                              cudaStream_t st) {
   if (ntiles <= 0) return cudaSuccess;
   dim3 block(TX, TY);
   if (pre) {
     if (order == 4)
-      interior_pre_kernel<4, false><<<ntiles, block, 0, st>>>(a, tiles);
+      interior_pre_kernel<4, false, 1><<<ntiles, block, 0, st>>>(a, tiles);
     else
-      interior_pre_kernel<6, false><<<ntiles, block, 0, st>>>(a, tiles);
+      interior_pre_kernel<6, false, 1><<<ntiles, block, 0, st>>>(a, tiles);
   } else if (order == 4) {
     interior_kernel<4, false><<<ntiles, block, 0, st>>>(a, tiles);
   } else {
@@ -54,4 +31,5 @@ cudaError_t launch_fused_f64(int order, const StageArgs &a, const Tile *tiles, i
   }
   return cudaGetLastError();
 }
+
 }  // namespace z4c

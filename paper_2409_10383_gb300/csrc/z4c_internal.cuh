@@ -72,6 +72,7 @@ struct StageArgs {
   double *rhs_out;    // MODE_RHS output
   void *dstore;       // stored y/z first derivatives (pre-pass), FP64 or FP32 like the stencils
   double ca, cb;
+  float caf, cbf;     // the same coefficients in FP32 (FP32-RHS increments)
   int32_t mode;
   int32_t next_full;  // FP32 mode: 1 = write every field of next in FP64, 0 = chi only
 };
@@ -81,13 +82,13 @@ constexpr int TX = 16;
 constexpr int TY = 8;
 
 // ---- launchers (defined in the kernel translation units) ----
-// wtiles == nullptr: single fused kernel; otherwise the y/z pre-pass over
-// wtiles followed by the fused kernel reading the stored derivatives.
-cudaError_t launch_interior_f64(int order, const StageArgs &a, const Tile *tiles, int ntiles,
-                                const Tile *wtiles, int nwtiles, cudaStream_t st);
-cudaError_t launch_interior_f32(int order, const StageArgs &a, const Tile *tiles, int ntiles,
-                                const Tile *wtiles, int nwtiles, cudaStream_t st);
-// the two halves of launch_interior_*, launched separately (measurement)
+// FP32 fused pre-pass-schedule kernel built for 2 or 4 resident CTAs per SM
+cudaError_t launch_fused_pre_f32_occ2(int order, const StageArgs &a, const Tile *tiles, int ntiles,
+                                      cudaStream_t st);
+cudaError_t launch_fused_pre_f32_occ4(int order, const StageArgs &a, const Tile *tiles, int ntiles,
+                                      cudaStream_t st);
+// y/z first-derivative pre-pass; fused RHS + stage kernel (pre: reads the
+// pre-pass output, else the single-kernel schedule)
 cudaError_t launch_prepass_f64(int order, const StageArgs &a, const Tile *wtiles, int nwtiles, cudaStream_t st);
 cudaError_t launch_prepass_f32(int order, const StageArgs &a, const Tile *wtiles, int nwtiles, cudaStream_t st);
 cudaError_t launch_fused_f64(int order, const StageArgs &a, const Tile *tiles, int ntiles, bool pre,

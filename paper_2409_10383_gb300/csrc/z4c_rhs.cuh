@@ -617,48 +617,111 @@ __device__ __forceinline__ void constraints_point(const SRC &s, const int st[3],
 
 // ---- FP64 stage epilogue: RK update and algebraic constraint enforcement ----
 
-// gt <- gt det(gt)^(-1/3); At <- At - gt tr(At)/3 with tr over the new gt^ij.
-__device__ __forceinline__ void enforce(double v[NF]) {
-  double g0 = v[GXX], g1 = v[GXY], g2 = v[GXZ], g3 = v[GYY], g4 = v[GYZ], g5 = v[GZZ];
-  double det = g0 * (g3 * g5 - g4 * g4) + g1 * (g2 * g4 - g1 * g5) + g2 * (g1 * g4 - g2 * g3);
-  double sc = rcbrt(det);
-  g0 *= sc; g1 *= sc; g2 *= sc; g3 *= sc; g4 *= sc; g5 *= sc;
-  // inverse of a unit-determinant matrix is its adjugate
-  double i0 = g3 * g5 - g4 * g4, i1 = g2 * g4 - g1 * g5, i2 = g1 * g4 - g2 * g3;
-  double i3 = g0 * g5 - g2 * g2, i4 = g1 * g2 - g0 * g4, i5 = g0 * g3 - g1 * g1;
-  double idet = 1.0 / (g0 * i0 + g1 * i1 + g2 * i2);
-  double tr = (i0 * v[AXX] + i3 * v[AYY] + i5 * v[AZZ] +
-               2.0 * (i1 * v[AXY] + i2 * v[AXZ] + i4 * v[AYZ])) * idet;
-  double t3 = tr * (1.0 / 3.0);
-  v[GXX] = g0; v[GXY] = g1; v[GXZ] = g2; v[GYY] = g3; v[GYZ] = g4; v[GZZ] = g5;
-  v[AXX] -= g0 * t3; v[AXY] -= g1 * t3; v[AXZ] -= g2 * t3;
-  v[AYY] -= g3 * t3; v[AYZ] -= g4 * t3; v[AZZ] -= g5 * t3;
+// Float <-> double conversions on the integer pipe.  On this part FP64-pipe
+// throughput is ~1/60 of FP32 and conversions otherwise issue to the FP64
+// pipe.  float -> double is exact; double -> float rounds to nearest even.
+// Both are branch-free and never fall back to a hardware conversion:
+// subnormal results/operands are flushed to a signed zero, infinities and
+// NaN are preserved (a NaN keeps the quiet bit).
+__device__ __forceinline__ double f2d_int(float x) {
+  const uint32_t b = __float_as_uint(x);
+  const uint32_t e = (b >> 23) & 0xffu;
+  const uint64_t sign = (uint64_t)(b & 0x80000000u) << 32;
+  const uint64_t de = e == 0xffu ? 0x7ffull : (uint64_t)(e + 896u);
+  const uint64_t d = sign | (de << 52) | ((uint64_t)(b & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)(e == 0u ? sign : d));
 }
 
+__device__ __forceinline__ float d2f_int(double x) {
+  const uint64_t b = (uint64_t)__double_as_longlong(x);
+  const uint32_t hi = (uint32_t)(b >> 32), lo = (uint32_t)b;
+  const uint32_t sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7ffu);
+  const int ef = e - 896;  // biased float exponent
+  const uint32_t m = ((hi & 0xfffffu) << 3) | (lo >> 29);  // top 23 mantissa bits
+  const uint32_t rest = lo & 0x1fffffffu;                    // 29 dropped bits
+  uint32_t f = sign | ((uint32_t)ef << 23) | m;
+  f += (rest > 0x10000000u || (rest == 0x10000000u && (m & 1u))) ? 1u : 0u;  // carry may reach inf
+  const uint32_t inf_nan = sign | 0x7f800000u | ((b & 0xfffffffffffffull) ? 0x400000u : 0u);
+  f = e == 0x7ff ? inf_nan : (ef >= 255 ? (sign | 0x7f800000u) : (ef <= 0 ? sign : f));
+  return __uint_as_float(f);
+}
+
+// x^(-1/3) for x > 0: FP32 seed, then Newton steps y <- y (4 - x y^3) / 3 in
+// FP64 (each step squares the relative error: 2^-23 -> 2^-45 -> rounding).
+template <int NEWTON>
+__device__ __forceinline__ double rcbrt_newton(double x) {
+  double y = f2d_int(rcbrtf(d2f_int(x)));
+#pragma unroll
+  for (int it = 0; it < NEWTON; ++it) {
+    const double y3 = y * y * y;
+    y = y * fma(-x, y3, 4.0) * (1.0 / 3.0);
+  }
+  return y;
+}
+
+// gt <- s gt with s = det(gt)^(-1/3); At <- At - gt tr(At)/3, the trace over
+// the new inverse metric adj(s gt)/det(s gt) = s^2 adj(gt) (no division).
+template <int NEWTON>
+__device__ __forceinline__ void enforce(double v[NF]) {
+  const double g0 = v[GXX], g1 = v[GXY], g2 = v[GXZ], g3 = v[GYY], g4 = v[GYZ], g5 = v[GZZ];
+  const double a0 = g3 * g5 - g4 * g4, a1 = g2 * g4 - g1 * g5, a2 = g1 * g4 - g2 * g3;
+  const double a3 = g0 * g5 - g2 * g2, a4 = g1 * g2 - g0 * g4, a5 = g0 * g3 - g1 * g1;
+  const double det = g0 * a0 + g1 * a1 + g2 * a2;
+  const double s = rcbrt_newton<NEWTON>(det);
+  const double tr = s * s * (a0 * v[AXX] + a3 * v[AYY] + a5 * v[AZZ] +
+                             2.0 * (a1 * v[AXY] + a2 * v[AXZ] + a4 * v[AYZ]));
+  const double t3 = s * tr * (1.0 / 3.0);  // (s gt_ij) tr / 3 = gt_ij t3
+  v[AXX] -= g0 * t3; v[AXY] -= g1 * t3; v[AXZ] -= g2 * t3;
+  v[AYY] -= g3 * t3; v[AYZ] -= g4 * t3; v[AZZ] -= g5 * t3;
+  v[GXX] = g0 * s; v[GXY] = g1 * s; v[GXZ] = g2 * s;
+  v[GYY] = g3 * s; v[GYZ] = g4 * s; v[GZZ] = g5 * s;
+}
+
+// RK4 stage update of one cell and enforcement, then the stores.  FP64 mode:
+// FP64 fused multiply-adds of the FP64 RHS.  FP32 mode: the increment c k of
+// the FP32 RHS is formed in FP32 and added to the FP64 state / accumulator
+// in FP64; the next stage also goes to the FP32 shadow (gt diagonal minus 1).
 template <class R>
 __device__ __forceinline__ void stage_epilogue(const StageArgs &a, int64_t off, int32_t S, const R k[NF]) {
+  constexpr bool F32 = sizeof(R) == 4;
   if (a.mode == MODE_RHS) {
 #pragma unroll
-    for (int f = 0; f < NF; ++f) a.rhs_out[off + (int64_t)f * S] = double(k[f]);
+    for (int f = 0; f < NF; ++f) a.rhs_out[off + (int64_t)f * S] = F32 ? f2d_int(float(k[f])) : double(k[f]);
     return;
   }
   double v[NF];
 #pragma unroll
   for (int f = 0; f < NF; ++f) {
     const int64_t o = off + (int64_t)f * S;
-    const double kd = double(k[f]);
-    if (a.mode == MODE_S1) {
-      const double u = a.u0[o];
-      a.acc[o] = fma(a.cb, kd, u);
-      v[f] = fma(a.ca, kd, u);
-    } else if (a.mode == MODE_S23) {
-      a.acc[o] = fma(a.cb, kd, a.acc[o]);
-      v[f] = fma(a.ca, kd, a.u0[o]);
+    if constexpr (F32) {
+      const double dn = f2d_int(a.caf * float(k[f]));
+      const double da = f2d_int(a.cbf * float(k[f]));
+      if (a.mode == MODE_S1) {
+        const double u = a.u0[o];
+        a.acc[o] = u + da;
+        v[f] = u + dn;
+      } else if (a.mode == MODE_S23) {
+        a.acc[o] = a.acc[o] + da;
+        v[f] = a.u0[o] + dn;
+      } else {
+        v[f] = a.acc[o] + da;
+      }
     } else {
-      v[f] = fma(a.cb, kd, a.acc[o]);
+      const double kd = double(k[f]);
+      if (a.mode == MODE_S1) {
+        const double u = a.u0[o];
+        a.acc[o] = fma(a.cb, kd, u);
+        v[f] = fma(a.ca, kd, u);
+      } else if (a.mode == MODE_S23) {
+        a.acc[o] = fma(a.cb, kd, a.acc[o]);
+        v[f] = fma(a.ca, kd, a.u0[o]);
+      } else {
+        v[f] = fma(a.cb, kd, a.acc[o]);
+      }
     }
   }
-  enforce(v);
+  enforce<F32 ? 1 : 2>(v);
   if (a.next32 == nullptr) {
 #pragma unroll
     for (int f = 0; f < NF; ++f) a.next[off + (int64_t)f * S] = v[f];
@@ -672,9 +735,19 @@ __device__ __forceinline__ void stage_epilogue(const StageArgs &a, int64_t off, 
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
       const double w = (f == GXX || f == GYY || f == GZZ) ? v[f] - 1.0 : v[f];
-      a.next32[off + (int64_t)f * S] = __double2float_rn(w);
+      a.next32[off + (int64_t)f * S] = d2f_int(w);
     }
   }
+}
+
+// 1/max(chi, floor) in FP64 for the FP32 algebra: integer compare (both
+// operands positive or chi negative, so the bit patterns order like the
+// values), FP32 reciprocal seed, one FP64 Newton step, rounded to FP32.
+__device__ __forceinline__ float inv_chi_f32(double chi, double floor_) {
+  const double c = __double_as_longlong(chi) > __double_as_longlong(floor_) ? chi : floor_;
+  const double r0 = f2d_int(__frcp_rn(d2f_int(c)));
+  const double e = fma(-c, r0, 1.0);
+  return d2f_int(fma(r0, e, r0));
 }
 
 }  // namespace z4c

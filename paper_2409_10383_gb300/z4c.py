@@ -24,7 +24,7 @@ REG_U0, REG_STAGE_A, REG_STAGE_B, REG_ACC = 0, 1, 2, 3
 EXPORTS = ("z4c_create", "z4c_state_bytes", "z4c_scratch_bytes", "z4c_bind",
            "z4c_set_initial_data", "z4c_fill_ghosts", "z4c_rhs", "z4c_rk4_step",
            "z4c_constraints", "z4c_get_state", "z4c_set_state", "z4c_evolve_host",
-           "z4c_sync", "z4c_profile_steps", "z4c_peak_fma", "z4c_constraints_static",
+           "z4c_sync", "z4c_profile_steps", "z4c_set_variant", "z4c_autotune", "z4c_peak_fma", "z4c_constraints_static",
            "z4c_launches_per_step", "z4c_last_error", "z4c_destroy")
 
 
@@ -74,6 +74,8 @@ def lib():
             "z4c_evolve_host": (I, [P, P, P, S, D, I]),
             "z4c_sync": (I, [P]),
             "z4c_profile_steps": (I, [P, D, I, P]),
+            "z4c_set_variant": (I, [P, I, I]),
+            "z4c_autotune": (I, [P, I, P, P]),
             "z4c_peak_fma": (I, [I, P, P]),
             "z4c_constraints_static": (I, [P, P, I, I, P, D, D, D, P, P]),
             "z4c_launches_per_step": (I, [P]),
@@ -233,6 +235,16 @@ class Z4c:
         _check(lib().z4c_profile_steps(self.ctx, float(dt), int(nsteps), ms.ctypes.data), self.ctx,
                "z4c_profile_steps")
         return ms
+
+    def z4c_set_variant(self, schedule, occupancy=1):
+        _check(lib().z4c_set_variant(self.ctx, int(schedule), int(occupancy)), self.ctx, "z4c_set_variant")
+
+    def z4c_autotune(self, reps=3):
+        sch, occ = ctypes.c_int(), ctypes.c_int()
+        self._enter()
+        _check(lib().z4c_autotune(self.ctx, int(reps), ctypes.byref(sch), ctypes.byref(occ)), self.ctx,
+               "z4c_autotune")
+        return sch.value, occ.value
 
     def z4c_launches_per_step(self) -> int:
         return int(lib().z4c_launches_per_step(self.ctx))

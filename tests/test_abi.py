@@ -87,3 +87,10 @@ def test_sizes_and_unbound_calls(L):
     assert rc == 0 and L.z4c_launches_per_step(ctx) == 8  # single fused kernel
     L.z4c_destroy(ctx)
     assert z4c.z4c_create(_mesh(), [_block()], 3, 4, _params(64, schedule=3))[0] == z4c.Z4C_ERR_BAD_ARG
+    rc, ctx = z4c.z4c_create(_mesh(), [_block()], 3, 4, _params(64))
+    assert L.z4c_set_variant(ctx, 2, 4) == z4c.Z4C_ERR_UNSUPPORTED  # FP64 has one occupancy
+    assert L.z4c_set_variant(ctx, 1, 1) == 0 and L.z4c_launches_per_step(ctx) == 8
+    L.z4c_destroy(ctx)
+    rc, ctx = z4c.z4c_create(_mesh(), [_block()], 3, 4, _params(32))
+    assert L.z4c_set_variant(ctx, 2, 2) == 0 and L.z4c_set_variant(ctx, 1, 4) == z4c.Z4C_ERR_UNSUPPORTED
+    L.z4c_destroy(ctx)

@@ -182,8 +182,8 @@ def _round_like_shadow(m, u):
     return v
 
 
-@pytest.mark.parametrize("schedule", [1, 2])
-def test_fp32_rhs_error_budget(oracle, schedule):
+@pytest.mark.parametrize("schedule,occupancy", [(1, 1), (2, 1), (2, 2), (2, 4)])
+def test_fp32_rhs_error_budget(oracle, schedule, occupancy):
     """FP32 stencils and algebra (FP64 state, RK accumulation, 1/chi,
     enforcement).  Bounds, stated against what FP32 storage alone causes:
       - one RHS call: per-field error <= 8x the error of the FP64 oracle fed
@@ -193,6 +193,7 @@ def test_fp32_rhs_error_budget(oracle, schedule):
     w = H.small_workload("puncture", 6, (2, 2, 2), 16)
     m = H.oracle_mesh(oracle, w)
     g = H.gpu_ctx(w, precision=32, schedule=schedule)
+    g.z4c_set_variant(schedule, occupancy)
     u = m.initial_data(w["id_kind"], w["id_par"])
     m.fill_ghosts(u)
     ref = m.rhs(u)
@@ -217,3 +218,27 @@ def test_fp32_rhs_error_budget(oracle, schedule):
     n64, _ = m.constraints(u)
     n32, _ = m.constraints(v)
     assert abs(n32[0] / n64[0] - 1) <= 1e-5, (n32[0], n64[0])
+
+
+def test_autotune_keeps_state_and_picks_a_built_variant(oracle):
+    """The autotuner runs only stage 1 (U0 unchanged) and leaves a valid
+    variant; evolution after tuning still matches the oracle."""
+    w = H.small_workload("puncture", 6, (2, 2, 2), 16)
+    m = H.oracle_mesh(oracle, w)
+    for prec in (64, 32):
+        g = H.gpu_ctx(w, precision=prec)
+        g.z4c_set_initial_data(w["id_kind"], w["id_par"])
+        before = g.z4c_get_state()
+        sch, occ = g.z4c_autotune(2)
+        assert sch in (1, 2) and occ in ((1,) if prec == 64 else (1, 2, 4))
+        after = g.z4c_get_state()
+        for b in range(m.nblocks):
+            ev = m.evolved_mask(b)
+            assert np.array_equal(m.blocks(before)[b][:, ev], m.blocks(after)[b][:, ev])
+        if prec == 64:
+            u = m.initial_data(w["id_kind"], w["id_par"])
+            dt = 0.25 * float(w["h"][0])
+            g.z4c_rk4_step(dt, 2)
+            m.rk4(u, dt, 2)
+            rel, _ = H.field_errors(m, u, g.z4c_get_state())
+            assert rel.max() <= STEP_TOL
