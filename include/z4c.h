@@ -63,8 +63,9 @@ typedef struct z4c_mesh {
 } z4c_mesh;
 
 /* One MeshBlock (Sec. 3): n interior cells per direction, lower corner lo of
- * the active region, cubic cell spacing h.  level and instance are reserved
- * for refinement levels and independent problems (must be 0 here). */
+ * the active region, cubic cell spacing h.  instance: the independent
+ * problem the block belongs to (z4c_create_batch; 0 for z4c_create).  level
+ * is reserved for mesh refinement and must be 0. */
 typedef struct z4c_block {
   int32_t level;
   int32_t n[3];
@@ -126,6 +127,25 @@ typedef struct z4c_ctx z4c_ctx;
 int z4c_create(const z4c_mesh *mesh, const z4c_block *blocks, int nblocks, int ghosts,
                int fd_order, const z4c_params *params, z4c_ctx **out);
 
+/* One independent problem of a batch: its Mesh, parameters, ghost width and
+ * differencing order (the arguments of z4c_create). */
+typedef struct z4c_instance {
+  z4c_mesh mesh;
+  z4c_params params;
+  int32_t ghosts;
+  int32_t fd_order;
+} z4c_instance;
+
+/* A pack of independent problems evolved together (the paper's
+ * MeshBlockPack, Sec. 3, across problems): instances may differ in mesh,
+ * block size, order, precision and parameters.  blocks: the blocks of every
+ * instance, grouped by instance in increasing order (block.instance), each
+ * instance's blocks tiling its mesh as in z4c_create.  One RK4 step of the
+ * whole batch is one CUDA graph (z4c_rk4_step_batch), each instance with its
+ * own dt.  Registers hold the blocks in the order given.  Makes no CUDA call. */
+int z4c_create_batch(const z4c_instance *instances, int ninstances, const z4c_block *blocks, int nblocks,
+                     z4c_ctx **out);
+
 /* Bytes of one FP64 register (see conventions). */
 int z4c_state_bytes(const z4c_ctx *ctx, size_t *bytes_per_register);
 
@@ -144,6 +164,9 @@ int z4c_bind(z4c_ctx *ctx, void *u0, void *stage_a, void *stage_b, void *acc, vo
 /* Analytic initial data of the given kind into every storage cell of U0. */
 int z4c_set_initial_data(z4c_ctx *ctx, int kind, const double *params, int nparams);
 
+/* The same for the blocks of one instance only (instance = -1: all). */
+int z4c_set_initial_data_instance(z4c_ctx *ctx, int instance, int kind, const double *params, int nparams);
+
 /* Fill the ghost cells of register reg from neighbouring blocks' active
  * cells (same level) or by periodic wrap (Sec. 3).  Sommerfeld cells are
  * evolved, never overwritten. */
@@ -160,6 +183,11 @@ int z4c_rhs(z4c_ctx *ctx, int reg, void *rhs_out);
  * step is captured once into a CUDA graph and replayed. */
 int z4c_rk4_step(z4c_ctx *ctx, double dt, int nsteps);
 
+/* nsteps RK4 steps of every instance of a batch, instance i with time step
+ * dt_per_instance[i] (host array of ninstances doubles).  The steps read dt
+ * from a device table, so one captured graph serves every choice of dt. */
+int z4c_rk4_step_batch(z4c_ctx *ctx, const double *dt_per_instance, int nsteps);
+
 /* Hamiltonian and momentum constraints of U0 (ghosts are filled first).
  * norms (host, 6 doubles): ||H||_2, ||M||_2, max|H|, ||H||_2 and ||M||_2
  * over cells with r > r_mask, max|M|; ||X||_2 = sqrt(sum X^2 h^3 / sum h^3)
@@ -167,6 +195,10 @@ int z4c_rk4_step(z4c_ctx *ctx, double dt, int nsteps);
  * storage cell (H, M^x, M^y, M^z) laid out like a 4-field register.
  * Synchronises the stream.  Returns Z4C_ERR_NAN if a norm is NaN. */
 int z4c_constraints(z4c_ctx *ctx, double r_mask, double *norms, void *per_cell_out);
+
+/* The constraint norms over the blocks of one instance (instance = -1: all);
+ * per_cell_out as in z4c_constraints (cells of other instances are 0). */
+int z4c_constraints_instance(z4c_ctx *ctx, int instance, double r_mask, double *norms, void *per_cell_out);
 
 /* Copy register reg to / from host memory (bytes = z4c_state_bytes()).
  * Synchronous.  Pinned host memory makes the copy faster. */
@@ -200,7 +232,9 @@ int z4c_set_variant(z4c_ctx *ctx, int schedule, int occupancy);
  * number of resident CTAs per SM its registers are budgeted for (1, 2, 4).
  * Each candidate runs reps + 1 times the ghost fill and stage 1 of RK4 (which
  * reads U0 and overwrites only the accumulator and stage A, so U0 keeps its
- * value); the fastest is kept and reported (either pointer may be NULL).
+ * value); the fastest is kept, FP64 and FP32-RHS kernels tuned separately.
+ * Reported (either pointer may be NULL): the FP32-RHS choice if the context
+ * has FP32-RHS blocks, else the FP64 one.
  * Synchronous.  Call before z4c_rk4_step, or it re-captures its graph. */
 int z4c_autotune(z4c_ctx *ctx, int reps, int *schedule_out, int *occupancy_out);
 

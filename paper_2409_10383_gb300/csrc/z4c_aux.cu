@@ -28,12 +28,12 @@ cudaError_t launch_sommerfeld(bool f32, const StageArgs &a, const CellRef *cells
   return cudaGetLastError();
 }
 
-cudaError_t launch_initial_data(double *u0, const DevBlock *blocks, int nblocks, int max_S, int kind,
-                                const double *par, int npar, cudaStream_t st) {
+cudaError_t launch_initial_data(double *u0, const DevBlock *blocks, int nblocks, int max_S, int instance,
+                                int kind, const double *par, int npar, cudaStream_t st) {
   IdPar P{};
   for (int q = 0; q < npar && q < 64; ++q) P.v[q] = par[q];
   dim3 grid((max_S + 255) / 256, nblocks);
-  initial_data_kernel<<<grid, 256, 0, st>>>(u0, blocks, kind, P);
+  initial_data_kernel<<<grid, 256, 0, st>>>(u0, blocks, instance, kind, P);
   return cudaGetLastError();
 }
 
@@ -44,17 +44,20 @@ cudaError_t launch_to_shadow(const double *src, float *dst, const DevBlock *bloc
   return cudaGetLastError();
 }
 
-cudaError_t launch_constraints(int order, const double *u0, const DevBlock *blocks, const Tile *tiles,
-                               int ntiles, double r_mask, double *per_cell, double *partials,
-                               double *result, cudaStream_t st) {
+cudaError_t launch_constraint_partials(int order, const double *u0, const DevBlock *blocks, const Tile *tiles,
+                                       int ntiles, int instance, double r_mask, double *per_cell,
+                                       double *partials, cudaStream_t st) {
+  if (ntiles <= 0) return cudaSuccess;
   dim3 block(TX, TY);
   if (order == 4)
-    constraints_kernel<4><<<ntiles, block, 0, st>>>(u0, blocks, tiles, r_mask, per_cell, partials);
+    constraints_kernel<4><<<ntiles, block, 0, st>>>(u0, blocks, tiles, instance, r_mask, per_cell, partials);
   else
-    constraints_kernel<6><<<ntiles, block, 0, st>>>(u0, blocks, tiles, r_mask, per_cell, partials);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  constraints_finalize<<<1, 1024, 0, st>>>(partials, ntiles, result);
+    constraints_kernel<6><<<ntiles, block, 0, st>>>(u0, blocks, tiles, instance, r_mask, per_cell, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_constraint_finalize(const double *partials, int n, double *result, cudaStream_t st) {
+  constraints_finalize<<<1, 1024, 0, st>>>(partials, n, result);
   return cudaGetLastError();
 }
 

@@ -93,7 +93,7 @@ __global__ void sommerfeld_kernel(StageArgs a, const CellRef *__restrict__ cells
     }
     k[f] = -(xdu + um) * ir;
   }
-  stage_epilogue<R>(a, off, b.S, k);
+  stage_epilogue<R>(a, c.block, off, b.S, k);
 }
 
 
@@ -167,9 +167,10 @@ __device__ void id_cell(int kind, const IdPar &P, double x, double y, double z, 
   }
 }
 
-__global__ void initial_data_kernel(double *__restrict__ u0, const DevBlock *__restrict__ blocks, int kind,
-                                    IdPar P) {
+__global__ void initial_data_kernel(double *__restrict__ u0, const DevBlock *__restrict__ blocks, int instance,
+                                    int kind, IdPar P) {
   const DevBlock &b = blocks[blockIdx.y];
+  if (instance >= 0 && b.instance != instance) return;
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < b.S; c += gridDim.x * blockDim.x) {
     const int e0 = b.e[0], e1 = b.e[1];
     const int i = c % e0, j = (c / e0) % e1, k = c / (e0 * e1);
@@ -188,6 +189,7 @@ __global__ void initial_data_kernel(double *__restrict__ u0, const DevBlock *__r
 __global__ void to_shadow_kernel(const double *__restrict__ src, float *__restrict__ dst,
                                  const DevBlock *__restrict__ blocks) {
   const DevBlock &b = blocks[blockIdx.y];
+  if (!b.f32) return;
   for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < b.S; c += gridDim.x * blockDim.x) {
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
@@ -221,18 +223,19 @@ template <int ORD>
 __global__ void __launch_bounds__(TX * TY) constraints_kernel(const double *__restrict__ u0,
                                                               const DevBlock *__restrict__ blocks,
                                                               const Tile *__restrict__ tiles,
-                                                              double r_mask, double *per_cell,
-                                                              double *partials) {
+                                                              int instance, double r_mask,
+                                                              double *per_cell, double *partials) {
   const Tile t = tiles[blockIdx.x];
   const DevBlock &b = blocks[t.block];
   const int i = t.i0 + threadIdx.x, j = t.j0 + threadIdx.y, kk = t.k0;
   double acc[NPART] = {0, 0, 0, 0, 0, 0, 0, 0};
-  if (i < b.n[0] && j < b.n[1]) {
+  const bool mine = b.order == ORD && (instance < 0 || b.instance == instance);
+  if (mine && i < b.n[0] && j < b.n[1]) {
     const int g = b.g, e0 = b.e[0], e1 = b.e[1];
     const int32_t cidx = ((kk + g) * e1 + (j + g)) * e0 + (i + g);
     const int st[3] = {1, e0, e0 * e1};
     const int64_t off = b.off + cidx;
-    const Src<double, false> s{u0 + off, b.S};
+    const Src<double, false> s{u0 + b.off, cidx, b.S};
     const double ichi = 1.0 / fmax(u0[off], b.chi_floor);
     double out[4];
     constraints_point<ORD>(s, st, scales_of(b, 0.0), ichi, out);

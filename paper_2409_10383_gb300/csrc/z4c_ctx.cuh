@@ -1,0 +1,107 @@
+// Host-side context of the C ABI: descriptors, work lists and the scratch
+// layout.  Shared by z4c_build.cu (creation, binding) and z4c_api.cu (the
+// calls that enqueue GPU work).  Not part of the C ABI.
+#pragma once
+
+#include <cstdarg>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "z4c.h"
+#include "z4c_internal.cuh"
+
+namespace z4c {
+
+// One independent problem: a Mesh of equal MeshBlocks on one level.
+struct Instance {
+  z4c_mesh mesh;
+  z4c_params params;
+  int ghosts = 0, order = 0;
+  int first = 0, count = 0;  // its blocks are [first, first + count)
+};
+
+// Kernels are templated on (order, precision): one work list per group.
+// Group index = 2 * (order == 6) + f32.
+struct Group {
+  int order = 4;
+  bool f32 = false;
+  std::vector<Tile> tiles;   // interior tiles of the group's blocks
+  std::vector<Tile> wtiles;  // interior widened by order/2 in x and y (pre-pass)
+  size_t o_tiles = 0, o_wtiles = 0;
+  bool empty() const { return tiles.empty(); }
+};
+
+}  // namespace z4c
+
+struct z4c_ctx {
+  std::vector<z4c::Instance> inst;
+  std::vector<z4c_block> blocks;
+  std::vector<z4c::DevBlock> dblocks;
+  z4c::Group grp[4];
+  std::vector<z4c::CellRef> somm[2];    // Sommerfeld cells, per precision (0 FP64, 1 FP32)
+  std::vector<z4c::GhostCopy> gcopy[2];  // same-level ghost copies, per precision
+  std::vector<z4c::Tile> ctiles;         // every interior tile (constraints)
+  std::vector<double> dt_host;           // time step per block
+  size_t reg_elems = 0;
+  int max_S = 0;
+  bool has[2] = {false, false};          // precisions present
+  // scratch layout (byte offsets)
+  size_t o_blocks = 0, o_somm[2] = {0, 0}, o_gcopy[2] = {0, 0}, o_ctiles = 0, o_part = 0, o_res = 0,
+         o_dt = 0, o_sh0 = 0, o_sh1 = 0, o_ds64 = 0, o_ds32 = 0, scratch_total = 0;
+  // bound buffers
+  double *reg[4] = {nullptr, nullptr, nullptr, nullptr};
+  char *scratch = nullptr;
+  cudaStream_t stream = nullptr;
+  bool bound = false;
+  bool shadow_valid = false;
+  bool dt_dirty = true;
+  // kernel variant per precision: schedule (1 one kernel, 2 pre-pass + fused)
+  // and occupancy (resident CTAs per SM the fused kernel is built for)
+  int sched[2] = {2, 2}, occ[2] = {1, 4};
+  // graph of one RK4 step
+  cudaGraphExec_t graph = nullptr;
+  std::string err;
+
+  const z4c::DevBlock *d_blocks() const { return (const z4c::DevBlock *)(scratch + o_blocks); }
+  const z4c::Tile *d_tiles(int g) const { return (const z4c::Tile *)(scratch + grp[g].o_tiles); }
+  const z4c::Tile *d_wtiles(int g) const { return (const z4c::Tile *)(scratch + grp[g].o_wtiles); }
+  const z4c::CellRef *d_somm(int p) const { return (const z4c::CellRef *)(scratch + o_somm[p]); }
+  const z4c::GhostCopy *d_gcopy(int p) const { return (const z4c::GhostCopy *)(scratch + o_gcopy[p]); }
+  const z4c::Tile *d_ctiles() const { return (const z4c::Tile *)(scratch + o_ctiles); }
+  double *d_part() const { return (double *)(scratch + o_part); }
+  double *d_res() const { return (double *)(scratch + o_res); }
+  double *d_dt() const { return (double *)(scratch + o_dt); }
+  float *d_sh(int q) const { return (float *)(scratch + (q == 0 ? o_sh0 : o_sh1)); }
+  void *d_dstore(bool f32) const { return scratch + (f32 ? o_ds32 : o_ds64); }
+  void drop_graph() {
+    if (graph) {
+      cudaGraphExecDestroy(graph);
+      graph = nullptr;
+    }
+  }
+};
+
+namespace z4c {
+
+inline int fail(z4c_ctx *c, int code, const char *fmt, ...) {
+  if (c) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    c->err = buf;
+  }
+  return code;
+}
+
+}  // namespace z4c
+
+#define CK(call)                                                                             \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess)                                                                   \
+      return z4c::fail(ctx, Z4C_ERR_CUDA, "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                       __FILE__, __LINE__);                                                  \
+  } while (0)

@@ -31,17 +31,17 @@ __global__ void __launch_bounds__(TX * TY) interior_kernel(StageArgs a, const Ti
   const Phys<R> p{R(b.kappa1), R(b.kappa2), R(b.eta), b.lapse, b.shift};
   R k[NF];
   if constexpr (F32) {
-    const Src<float, true> s{a.x32 + off, b.S};
+    const Src<float, true> s{a.x32 + b.off, cidx, b.S};
     const Scales<float> sc = scales_of(b, 0.0f);
     const Direct<ORD, float, Src<float, true>> dv{s, st, sc};
     rhs_point<ORD, float>(s, dv, st, sc, p, ichi, k);
   } else {
-    const Src<double, false> s{a.x64 + off, b.S};
+    const Src<double, false> s{a.x64 + b.off, cidx, b.S};
     const Scales<double> sc = scales_of(b, 0.0);
     const Direct<ORD, double, Src<double, false>> dv{s, st, sc};
     rhs_point<ORD, double>(s, dv, st, sc, p, ichi, k);
   }
-  stage_epilogue<R>(a, off, b.S, k);
+  stage_epilogue<R>(a, t.block, off, b.S, k);
 }
 
 
@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(TX * TY) dydz_kernel(StageArgs a, const Tile *
   const R s1 = F32 ? R(b.s1f) : R(b.s1);
   const int sy = e0, sz = e0 * e1;
   if constexpr (F32) {
-    const Src<float, true> s{a.x32 + off, b.S};
+    const Src<float, true> s{a.x32 + b.off, cidx, b.S};
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
       if (dslot(f) < 0) continue;
@@ -78,7 +78,7 @@ __global__ void __launch_bounds__(TX * TY) dydz_kernel(StageArgs a, const Tile *
       out[(int64_t)(dslot(f) + NDS) * b.S] = FD<ORD>::d1(s, f, sz) * s1;
     }
   } else {
-    const Src<double, false> s{a.x64 + off, b.S};
+    const Src<double, false> s{a.x64 + b.off, cidx, b.S};
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
       if (dslot(f) < 0) continue;
@@ -111,19 +111,19 @@ __global__ void __launch_bounds__(TX * TY, OCC) interior_pre_kernel(StageArgs a,
     ichi = 1.0 / fmax(a.x64[off], b.chi_floor);
   const Phys<R> p{R(b.kappa1), R(b.kappa2), R(b.eta), b.lapse, b.shift};
   R k[NF];
-  const Src<R, false> ds{reinterpret_cast<const R *>(a.dstore) + off, b.S};
+  const Src<R, false> ds{reinterpret_cast<const R *>(a.dstore) + b.off, cidx, b.S};
   if constexpr (F32) {
-    const Src<float, true> s{a.x32 + off, b.S};
+    const Src<float, true> s{a.x32 + b.off, cidx, b.S};
     const Scales<float> sc = scales_of(b, 0.0f);
     const Pre<ORD, float, Src<float, true>, Src<float, false>> dv{s, ds, st, sc};
     rhs_point<ORD, float>(s, dv, st, sc, p, ichi, k);
   } else {
-    const Src<double, false> s{a.x64 + off, b.S};
+    const Src<double, false> s{a.x64 + b.off, cidx, b.S};
     const Scales<double> sc = scales_of(b, 0.0);
     const Pre<ORD, double, Src<double, false>, Src<double, false>> dv{s, ds, st, sc};
     rhs_point<ORD, double>(s, dv, st, sc, p, ichi, k);
   }
-  stage_epilogue<R>(a, off, b.S, k);
+  stage_epilogue<R>(a, t.block, off, b.S, k);
 }
 
 }  // namespace z4c

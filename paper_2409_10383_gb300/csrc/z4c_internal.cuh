@@ -37,6 +37,8 @@ struct DevBlock {
   // physics parameters of the block's problem instance (Sec. 2, Sec. 4.3)
   double kappa1, kappa2, eta, chi_floor;
   int32_t lapse, shift;  // 0 harmonic / 1 one-plus-log; 0 frozen / 1 Gamma-driver
+  int32_t instance;      // independent problem this block belongs to
+  int32_t f32;           // 1: FP32-RHS block (FP32 shadow holds its stage states)
 };
 
 // One interior tile: TX x TY cells of one z-plane of one block.
@@ -71,8 +73,8 @@ struct StageArgs {
   float *next32;      // FP32 shadow of the next stage state (FP32 mode)
   double *rhs_out;    // MODE_RHS output
   void *dstore;       // stored y/z first derivatives (pre-pass), FP64 or FP32 like the stencils
-  double ca, cb;
-  float caf, cbf;     // the same coefficients in FP32 (FP32-RHS increments)
+  const double *dts;  // time step of each block (its instance's dt)
+  double fa, fb;      // next = base + fa dt k, acc = acc + fb dt k (classic RK4 weights)
   int32_t mode;
   int32_t next_full;  // FP32 mode: 1 = write every field of next in FP64, 0 = chi only
 };
@@ -101,13 +103,18 @@ cudaError_t launch_ghosts_f64(double *reg, const DevBlock *blocks, const GhostCo
                               cudaStream_t st);
 cudaError_t launch_ghosts_f32(float *reg, const DevBlock *blocks, const GhostCopy *list, int n,
                               cudaStream_t st);
-cudaError_t launch_initial_data(double *u0, const DevBlock *blocks, int nblocks, int max_S, int kind,
-                                const double *par, int npar, cudaStream_t st);
+// instance < 0: every block; otherwise only the blocks of that instance
+cudaError_t launch_initial_data(double *u0, const DevBlock *blocks, int nblocks, int max_S, int instance,
+                                int kind, const double *par, int npar, cudaStream_t st);
+// FP32-RHS blocks only
 cudaError_t launch_to_shadow(const double *src, float *dst, const DevBlock *blocks, int nblocks,
                              int max_S, cudaStream_t st);
-cudaError_t launch_constraints(int order, const double *u0, const DevBlock *blocks,
-                               const Tile *tiles, int ntiles, double r_mask, double *per_cell,
-                               double *partials, double *result, cudaStream_t st);
+// per-CTA partial records of the tiles' blocks of this order (and instance,
+// if >= 0); records of other blocks are zero
+cudaError_t launch_constraint_partials(int order, const double *u0, const DevBlock *blocks,
+                                       const Tile *tiles, int ntiles, int instance, double r_mask,
+                                       double *per_cell, double *partials, cudaStream_t st);
+cudaError_t launch_constraint_finalize(const double *partials, int n, double *result, cudaStream_t st);
 
 cudaError_t peak_fma(bool f64, cudaStream_t st, double *flops_per_s);
 

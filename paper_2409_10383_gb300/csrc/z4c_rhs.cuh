@@ -27,9 +27,10 @@ __device__ __forceinline__ R ldg_(const R *p) {
 // one, so centre values add it back.
 template <class R, bool SHIFTED_DIAG>
 struct Src {
-  const R *__restrict__ base;
-  int32_t S;
-  __device__ __forceinline__ R at(int f, int off) const { return ldg_(base + f * S + off); }
+  const R *__restrict__ base;  // field 0 of the block (the same for the whole CTA)
+  int32_t c;                   // storage index of the centre cell
+  int32_t S;                   // cells per field
+  __device__ __forceinline__ R at(int f, int off) const { return ldg_(base + (c + (f * S + off))); }
   __device__ __forceinline__ R val(int f) const {
     R v = at(f, 0);
     if (SHIFTED_DIAG && (f == GXX || f == GYY || f == GZZ)) v += R(1);
@@ -42,8 +43,7 @@ struct FD;
 
 // 4th order: d1 = (8 (f1 - f-1) - (f2 - f-2)) / 12h
 //            d2 = (16 (f1 + f-1) - (f2 + f-2) - 30 f0) / 12h^2
-//            lopsided (beta > 0), offsets -1..3: (-3, -10, 18, -6, 1) / 12h
-//            KO: N = 3, (+1) sigma / (64 h) * (1 -6 15 -20 15 -6 1)
+//            (lopsided advection and KO dissipation: KoAdv<4> below)
 template <>
 struct FD<4> {
   static constexpr int W = 2;
@@ -71,33 +71,11 @@ struct FD<4> {
     using R = decltype(q11);
     return fma(q11, R(64), fma(q12 + q21, R(-8), q22));
   }
-  // upwind-signed stride: sst = +st for beta >= 0, -st otherwise; result
-  // times sign(beta) is the lopsided derivative
-  template <class S_>
-  __device__ static auto lop(const S_ &s, int f, int sst) {
-    auto fm1 = s.at(f, -sst), f0 = s.at(f, 0), f1 = s.at(f, sst), f2 = s.at(f, 2 * sst),
-         f3 = s.at(f, 3 * sst);
-    using R = decltype(f0);
-    return fma(fm1, R(-3), fma(f0, R(-10), fma(f1, R(18), fma(f2, R(-6), f3))));
-  }
-  // sum over the three directions of the 6th undivided difference
-  template <class S_>
-  __device__ static auto ko3(const S_ &s, int f, int sx, int sy, int sz) {
-    auto c = s.at(f, 0);
-    using R = decltype(c);
-    R p1 = (s.at(f, sx) + s.at(f, -sx)) + (s.at(f, sy) + s.at(f, -sy)) + (s.at(f, sz) + s.at(f, -sz));
-    R p2 = (s.at(f, 2 * sx) + s.at(f, -2 * sx)) + (s.at(f, 2 * sy) + s.at(f, -2 * sy)) +
-           (s.at(f, 2 * sz) + s.at(f, -2 * sz));
-    R p3 = (s.at(f, 3 * sx) + s.at(f, -3 * sx)) + (s.at(f, 3 * sy) + s.at(f, -3 * sy)) +
-           (s.at(f, 3 * sz) + s.at(f, -3 * sz));
-    return fma(c, R(-60), fma(p1, R(15), fma(p2, R(-6), p3)));
-  }
 };
 
 // 6th order: d1 = (45 (f1 - f-1) - 9 (f2 - f-2) + (f3 - f-3)) / 60h
 //            d2 = (270 (f1 + f-1) - 27 (f2 + f-2) + 2 (f3 + f-3) - 490 f0) / 180h^2
-//            lopsided (beta > 0), offsets -2..4: (2, -24, -35, 80, -30, 8, -1) / 60h
-//            KO: N = 4, (-1) sigma / (256 h) * (1 -8 28 -56 70 -56 28 -8 1)
+//            (lopsided advection and KO dissipation: KoAdv<6> below)
 template <>
 struct FD<6> {
   static constexpr int W = 3;
@@ -136,26 +114,74 @@ struct FD<6> {
     r = fma(q23 + q32, R(-9), r);
     return r + q33;
   }
-  template <class S_>
-  __device__ static auto lop(const S_ &s, int f, int sst) {
-    auto fm2 = s.at(f, -2 * sst), fm1 = s.at(f, -sst), f0 = s.at(f, 0), f1 = s.at(f, sst),
-         f2 = s.at(f, 2 * sst), f3 = s.at(f, 3 * sst), f4 = s.at(f, 4 * sst);
-    using R = decltype(f0);
-    return fma(fm2, R(2), fma(fm1, R(-24), fma(f0, R(-35), fma(f1, R(80),
-               fma(f2, R(-30), fma(f3, R(8), -f4))))));
+};
+
+// Kreiss-Oliger dissipation (all three directions) plus lopsided advection
+// beta^k d_k f of one field from one load of its 3 x (2KW+1)-point cross:
+// the lopsided stencil takes its points from the same loads, mirrored when
+// beta^k < 0 (the mirror image of the beta > 0 stencil).  Returns the
+// unscaled KO sum (times sko by the caller) and adds |beta^k| slop D_lop to adv.
+template <int ORD>
+struct KoAdv;
+template <>
+struct KoAdv<4> {
+  // lopsided (beta > 0) offsets -1..3: (-3, -10, 18, -6, 1) / 12h;
+  // KO: N = 3, (+1) sigma / (64 h) * (1 -6 15 -20 15 -6 1) per direction
+  static constexpr int KW = 3;                       // KO half width (N = 3)
+  static constexpr int LOFF = -1, LN = 5;            // lopsided offsets -1..3
+  template <class R>
+  __device__ static R lop(const R *v) {              // v[m - LOFF] = f(m) upwind-oriented
+    return fma(v[0], R(-3), fma(v[1], R(-10), fma(v[2], R(18), fma(v[3], R(-6), v[4]))));
   }
-  template <class S_>
-  __device__ static auto ko3(const S_ &s, int f, int sx, int sy, int sz) {
-    auto c = s.at(f, 0);
-    using R = decltype(c);
-    R p[4];
-#pragma unroll
-    for (int m = 1; m <= 4; ++m)
-      p[m - 1] = (s.at(f, m * sx) + s.at(f, -m * sx)) + (s.at(f, m * sy) + s.at(f, -m * sy)) +
-                 (s.at(f, m * sz) + s.at(f, -m * sz));
+  template <class R>
+  __device__ static R ko(R c, const R *p) {          // p[m-1] = sum over directions of f(+m) + f(-m)
+    return fma(c, R(-60), fma(p[0], R(15), fma(p[1], R(-6), p[2])));
+  }
+};
+template <>
+struct KoAdv<6> {
+  // lopsided (beta > 0) offsets -2..4: (2, -24, -35, 80, -30, 8, -1) / 60h;
+  // KO: N = 4, (-1) sigma / (256 h) * (1 -8 28 -56 70 -56 28 -8 1) per direction
+  static constexpr int KW = 4;
+  static constexpr int LOFF = -2, LN = 7;            // lopsided offsets -2..4
+  template <class R>
+  __device__ static R lop(const R *v) {
+    return fma(v[0], R(2), fma(v[1], R(-24), fma(v[2], R(-35), fma(v[3], R(80),
+               fma(v[4], R(-30), fma(v[5], R(8), -v[6]))))));
+  }
+  template <class R>
+  __device__ static R ko(R c, const R *p) {
     return fma(c, R(210), fma(p[0], R(-56), fma(p[1], R(28), fma(p[2], R(-8), p[3]))));
   }
 };
+
+template <int ORD, class R, class S_>
+__device__ __forceinline__ R ko_adv(const S_ &s, int f, const int st[3], const bool up[3], const R ab[3],
+                                    R sko) {
+  using K = KoAdv<ORD>;
+  constexpr int W = K::KW;
+  const R c = s.at(f, 0);
+  R pairs[W];
+#pragma unroll
+  for (int m = 0; m < W; ++m) pairs[m] = R(0);
+  R adv = R(0);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    R x[2 * W + 1];
+#pragma unroll
+    for (int m = -W; m <= W; ++m) x[m + W] = m == 0 ? c : s.at(f, m * st[d]);
+#pragma unroll
+    for (int m = 1; m <= W; ++m) pairs[m - 1] += x[W + m] + x[W - m];
+    R v[K::LN];
+#pragma unroll
+    for (int q = 0; q < K::LN; ++q) {
+      const int m = q + K::LOFF;
+      v[q] = up[d] ? x[W + m] : x[W - m];
+    }
+    adv = fma(ab[d], K::lop(v), adv);
+  }
+  return fma(K::ko(c, pairs), sko, adv);
+}
 
 // Scale factors of one block in precision R.
 template <class R>
@@ -502,21 +528,17 @@ __device__ __forceinline__ void rhs_point(const SRC &s, const DV &dv, const int 
   for (int i = 0; i < 3; ++i) k[BETAX + i] = p.shift ? Gam[i] - p.eta * beta[i] : R(0);
 
   // lopsided advection along the shift and Kreiss-Oliger dissipation
-  int sst[3];
+  bool up[3];
   R ab[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    sst[d] = beta[d] >= R(0) ? st[d] : -st[d];
+    up[d] = beta[d] >= R(0);
     ab[d] = fabs(beta[d]) * sc.slop;
   }
 #pragma unroll 1
   for (int f = 0; f < NF; ++f) {
     if (!p.shift && f >= BETAX) continue;
-    R adv = ab[0] * F::lop(s, f, sst[0]);
-    adv = fma(ab[1], F::lop(s, f, sst[1]), adv);
-    adv = fma(ab[2], F::lop(s, f, sst[2]), adv);
-    R ko = F::ko3(s, f, st[0], st[1], st[2]);
-    k[f] += fma(ko, sc.sko, adv);
+    k[f] += ko_adv<ORD>(s, f, st, up, ab, sc.sko);
   }
 }
 
@@ -683,8 +705,12 @@ __device__ __forceinline__ void enforce(double v[NF]) {
 // the FP32 RHS is formed in FP32 and added to the FP64 state / accumulator
 // in FP64; the next stage also goes to the FP32 shadow (gt diagonal minus 1).
 template <class R>
-__device__ __forceinline__ void stage_epilogue(const StageArgs &a, int64_t off, int32_t S, const R k[NF]) {
+__device__ __forceinline__ void stage_epilogue(const StageArgs &a, int32_t block, int64_t off, int32_t S,
+                                               const R k[NF]) {
   constexpr bool F32 = sizeof(R) == 4;
+  const double dt = a.mode == MODE_RHS ? 0.0 : a.dts[block];
+  const double ca = a.fa * dt, cb = a.fb * dt;
+  const float caf = (float)ca, cbf = (float)cb;
   if (a.mode == MODE_RHS) {
 #pragma unroll
     for (int f = 0; f < NF; ++f) a.rhs_out[off + (int64_t)f * S] = F32 ? f2d_int(float(k[f])) : double(k[f]);
@@ -695,8 +721,8 @@ __device__ __forceinline__ void stage_epilogue(const StageArgs &a, int64_t off, 
   for (int f = 0; f < NF; ++f) {
     const int64_t o = off + (int64_t)f * S;
     if constexpr (F32) {
-      const double dn = f2d_int(a.caf * float(k[f]));
-      const double da = f2d_int(a.cbf * float(k[f]));
+      const double dn = f2d_int(caf * float(k[f]));
+      const double da = f2d_int(cbf * float(k[f]));
       if (a.mode == MODE_S1) {
         const double u = a.u0[o];
         a.acc[o] = u + da;
@@ -711,13 +737,13 @@ __device__ __forceinline__ void stage_epilogue(const StageArgs &a, int64_t off, 
       const double kd = double(k[f]);
       if (a.mode == MODE_S1) {
         const double u = a.u0[o];
-        a.acc[o] = fma(a.cb, kd, u);
-        v[f] = fma(a.ca, kd, u);
+        a.acc[o] = fma(cb, kd, u);
+        v[f] = fma(ca, kd, u);
       } else if (a.mode == MODE_S23) {
-        a.acc[o] = fma(a.cb, kd, a.acc[o]);
-        v[f] = fma(a.ca, kd, a.u0[o]);
+        a.acc[o] = fma(cb, kd, a.acc[o]);
+        v[f] = fma(ca, kd, a.u0[o]);
       } else {
-        v[f] = fma(a.cb, kd, a.acc[o]);
+        v[f] = fma(cb, kd, a.acc[o]);
       }
     }
   }

@@ -49,7 +49,7 @@ __global__ void __launch_bounds__(TX * TY) constraints_static_kernel(const doubl
     const int g = b.g, e0 = b.e[0], e1 = b.e[1];
     const int32_t cidx = ((kk + g) * e1 + (j + g)) * e0 + (i + g);
     const int st[3] = {1, e0, e0 * e1};
-    const Src<double, false> s{u + cidx, b.S};
+    const Src<double, false> s{u, cidx, b.S};
     const double ichi = 1.0 / fmax(u[cidx], b.chi_floor);
     double out[4];
     constraints_point<ORD>(s, st, scales_of(b, 0.0), ichi, out);

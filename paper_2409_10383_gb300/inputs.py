@@ -82,21 +82,42 @@ def perturbation(shape_per_block, seed: int, amp: float) -> list:
     return [rng.uniform(-amp, amp, (NF,) + tuple(s)) for s in shape_per_block]
 
 
-def uneven_batch(seed: int = SEED):
-    """64 single-puncture instances with seeded masses in [0.5, 2] and sizes
-    from {24, 48, 64, 96}^3, plus 16 gauge-wave instances with amplitudes in
-    [0.001, 0.1]; order and precision alternate with the instance index."""
+def _instance(kind, n, order, precision, value):
+    """One single-block problem: a puncture of mass `value` on [-16,16]^3 with
+    the Sommerfeld boundary, or a gauge wave of amplitude `value` on the
+    periodic [-1/2,1/2]^3; 4 or 6th order, FP64 or FP32-RHS."""
+    if kind == "puncture":
+        L, per, ko = 16.0, False, 0.5
+        idk, idp = ID_SCHWARZSCHILD, [value, 0.0]
+        lapse, shift, eta, k1 = 1, 1, 2.0, 0.02
+    else:
+        L, per, ko = 0.5, True, 0.02
+        idk, idp = ID_GAUGE_WAVE, [value, 1.0, 0.0]
+        lapse, shift, eta, k1 = 0, 0, 0.0, 0.0
+    nn, lo, h = uniform_blocks((1, 1, 1), n, (-L,) * 3, (L,) * 3)
+    return dict(name=f"{kind}_{n}", n=nn, lo=lo, h=h, ghosts=order // 2 + 1, order=order, periodic=per,
+                dom_lo=(-L,) * 3, dom_hi=(L,) * 3, lapse=lapse, shift=shift, ko_sigma=ko, kappa1=k1,
+                kappa2=0.0, eta=eta, chi_floor=1e-6, cfl=0.25, id_kind=idk, id_par=idp,
+                precision=precision)
+
+
+def uneven_batch(seed: int = SEED, sizes=(24, 48, 64, 96), n_puncture=64, n_wave=16):
+    """The uneven batch: 64 single-puncture instances with seeded masses in
+    [0.5, 2] and seeded sizes from {24, 48, 64, 96}^3, plus 16 gauge-wave
+    instances with seeded amplitudes in [0.001, 0.1]; the instance index
+    alternates the order (even: 6, odd: 4) and, in pairs, the precision
+    (FP64, FP64, FP32, FP32, ...).  Draws in the order instance -> size ->
+    mass/amplitude.  Returns a list of single-instance workloads."""
     rng = np.random.default_rng(seed)
-    sizes = (24, 48, 64, 96)
     out = []
-    for i in range(80):
-        n = int(sizes[rng.integers(0, 4)])
-        if i < 64:
-            mass = float(rng.uniform(0.5, 2.0))
-            out.append(dict(kind="puncture", n=n, mass=mass, order=6 if i % 2 == 0 else 4,
-                            precision=64 if (i // 2) % 2 == 0 else 32))
-        else:
-            amp = float(rng.uniform(0.001, 0.1))
-            out.append(dict(kind="gauge_wave", n=n, amp=amp, order=6 if i % 2 == 0 else 4,
-                            precision=64 if (i // 2) % 2 == 0 else 32))
+    for i in range(n_puncture + n_wave):
+        n = int(sizes[rng.integers(0, len(sizes))])
+        kind = "puncture" if i < n_puncture else "gauge_wave"
+        value = float(rng.uniform(0.5, 2.0)) if kind == "puncture" else float(rng.uniform(0.001, 0.1))
+        out.append(_instance(kind, n, 6 if i % 2 == 0 else 4, 64 if (i // 2) % 2 == 0 else 32, value))
     return out
+
+
+def uneven_batch_small(seed: int = SEED):
+    """The same mix at test size: 6 punctures and 2 gauge waves of 8..20^3."""
+    return uneven_batch(seed, sizes=(8, 12, 16, 20), n_puncture=6, n_wave=2)

@@ -21,7 +21,8 @@ Z4C_ERR_CUDA, Z4C_ERR_TIMEOUT, Z4C_ERR_NAN, Z4C_ERR_NOT_BOUND = -4, -5, -6, -7
 REG_U0, REG_STAGE_A, REG_STAGE_B, REG_ACC = 0, 1, 2, 3
 
 # every entry point declared in include/z4c.h
-EXPORTS = ("z4c_create", "z4c_state_bytes", "z4c_scratch_bytes", "z4c_bind",
+EXPORTS = ("z4c_create", "z4c_create_batch", "z4c_set_initial_data_instance", "z4c_rk4_step_batch",
+           "z4c_constraints_instance", "z4c_state_bytes", "z4c_scratch_bytes", "z4c_bind",
            "z4c_set_initial_data", "z4c_fill_ghosts", "z4c_rhs", "z4c_rk4_step",
            "z4c_constraints", "z4c_get_state", "z4c_set_state", "z4c_evolve_host",
            "z4c_sync", "z4c_profile_steps", "z4c_set_variant", "z4c_autotune", "z4c_peak_fma", "z4c_constraints_static",
@@ -46,6 +47,11 @@ class z4c_params(ctypes.Structure):
                 ("rhs_precision", ctypes.c_int32), ("schedule", ctypes.c_int32)]
 
 
+class z4c_instance(ctypes.Structure):
+    _fields_ = [("mesh", z4c_mesh), ("params", z4c_params), ("ghosts", ctypes.c_int32),
+                ("fd_order", ctypes.c_int32)]
+
+
 _lib = None
 
 
@@ -61,6 +67,11 @@ def lib():
         sig = {
             "z4c_create": (I, [ctypes.POINTER(z4c_mesh), ctypes.POINTER(z4c_block), I, I, I,
                                ctypes.POINTER(z4c_params), ctypes.POINTER(P)]),
+            "z4c_create_batch": (I, [ctypes.POINTER(z4c_instance), I, ctypes.POINTER(z4c_block), I,
+                                     ctypes.POINTER(P)]),
+            "z4c_set_initial_data_instance": (I, [P, I, I, P, I]),
+            "z4c_rk4_step_batch": (I, [P, P, I]),
+            "z4c_constraints_instance": (I, [P, I, D, P, P]),
             "z4c_state_bytes": (I, [P, ctypes.POINTER(S)]),
             "z4c_scratch_bytes": (I, [P, ctypes.POINTER(S)]),
             "z4c_bind": (I, [P, P, P, P, P, P, P]),
@@ -108,34 +119,56 @@ def z4c_create(mesh: z4c_mesh, blocks, ghosts: int, fd_order: int, params: z4c_p
 
 
 class Z4c:
-    """One context plus its caller-owned device buffers (torch tensors)."""
+    """One context plus its caller-owned device buffers (torch tensors).
 
-    def __init__(self, n, lo, h, ghosts, order, dom_lo, dom_hi, periodic, ko_sigma=0.0,
-                 kappa1=0.0, kappa2=0.0, eta=2.0, chi_floor=1e-6, lapse=1, shift=1, precision=64,
-                 schedule=0, device="cuda", stream=None, **_):
+    ``Z4c(**workload)`` makes a single-problem context; ``Z4c.batch([w0, w1,
+    ...])`` a batch of independent problems (z4c_create_batch).  A workload
+    is a dict with n, lo, h (per block), ghosts, order, dom_lo, dom_hi,
+    periodic and the physics parameters."""
+
+    def __init__(self, n=None, lo=None, h=None, ghosts=None, order=None, dom_lo=None, dom_hi=None,
+                 periodic=None, ko_sigma=0.0, kappa1=0.0, kappa2=0.0, eta=2.0, chi_floor=1e-6, lapse=1,
+                 shift=1, precision=64, schedule=0, device="cuda", stream=None, instances=None, **_):
         import torch
         self.torch = torch
-        n = np.asarray(n).reshape(-1, 3)
-        lo = np.asarray(lo, float).reshape(-1, 3)
-        h = np.broadcast_to(np.asarray(h, float), (len(n),))
-        self.mesh = z4c_mesh()
-        self.mesh.lo[:] = [float(v) for v in dom_lo]
-        self.mesh.hi[:] = [float(v) for v in dom_hi]
-        self.mesh.periodic = int(bool(periodic))
-        self.mesh.outer_bc = 0 if periodic else 1
+        if instances is None:
+            instances = [dict(n=n, lo=lo, h=h, ghosts=ghosts, order=order, dom_lo=dom_lo, dom_hi=dom_hi,
+                              periodic=periodic, ko_sigma=ko_sigma, kappa1=kappa1, kappa2=kappa2, eta=eta,
+                              chi_floor=chi_floor, lapse=lapse, shift=shift, precision=precision,
+                              schedule=schedule)]
+        self.instances = instances
+        insts = (z4c_instance * len(instances))()
         self.blocks = []
-        for b in range(len(n)):
-            B = z4c_block()
-            B.level, B.instance = 0, 0
-            B.n[:] = [int(v) for v in n[b]]
-            B.lo[:] = [float(v) for v in lo[b]]
-            B.h = float(h[b])
-            self.blocks.append(B)
-        self.params = z4c_params(ko_sigma, kappa1, kappa2, eta, chi_floor, 0.25, lapse, shift,
-                                 precision, schedule)
-        self.n, self.ghosts, self.order = n, ghosts, order
-        rc, self.ctx = z4c_create(self.mesh, self.blocks, ghosts, order, self.params)
-        _check(rc, None, "z4c_create")
+        self.block_elems = []
+        for i, w in enumerate(instances):
+            I = insts[i]
+            I.mesh.lo[:] = [float(v) for v in w["dom_lo"]]
+            I.mesh.hi[:] = [float(v) for v in w["dom_hi"]]
+            I.mesh.periodic = int(bool(w["periodic"]))
+            I.mesh.outer_bc = 0 if w["periodic"] else 1
+            I.params = z4c_params(w.get("ko_sigma", 0.0), w.get("kappa1", 0.0), w.get("kappa2", 0.0),
+                                  w.get("eta", 2.0), w.get("chi_floor", 1e-6), 0.25, w.get("lapse", 1),
+                                  w.get("shift", 1), w.get("precision", 64), w.get("schedule", 0))
+            I.ghosts, I.fd_order = int(w["ghosts"]), int(w["order"])
+            nn = np.asarray(w["n"]).reshape(-1, 3)
+            ll = np.asarray(w["lo"], float).reshape(-1, 3)
+            hh = np.broadcast_to(np.asarray(w["h"], float), (len(nn),))
+            for b in range(len(nn)):
+                B = z4c_block()
+                B.level, B.instance = 0, i
+                B.n[:] = [int(v) for v in nn[b]]
+                B.lo[:] = [float(v) for v in ll[b]]
+                B.h = float(hh[b])
+                self.blocks.append(B)
+                self.block_elems.append(NF * int(np.prod(nn[b] + 2 * int(w["ghosts"]))))
+        w0 = instances[0]
+        self.n, self.ghosts, self.order = np.asarray(w0["n"]).reshape(-1, 3), w0["ghosts"], w0["order"]
+        self.params = insts[0].params
+        arr = (z4c_block * len(self.blocks))(*self.blocks)
+        out = ctypes.c_void_p()
+        rc = lib().z4c_create_batch(insts, len(instances), arr, len(self.blocks), ctypes.byref(out))
+        _check(rc, None, "z4c_create_batch")
+        self.ctx = out
         sb, sc = ctypes.c_size_t(), ctypes.c_size_t()
         _check(lib().z4c_state_bytes(self.ctx, ctypes.byref(sb)), self.ctx, "z4c_state_bytes")
         _check(lib().z4c_scratch_bytes(self.ctx, ctypes.byref(sc)), self.ctx, "z4c_scratch_bytes")
@@ -154,6 +187,17 @@ class Z4c:
         args.update(kw)
         args.setdefault("precision", 64)
         return cls(**args)
+
+    @classmethod
+    def batch(cls, workloads, device="cuda", stream=None):
+        return cls(instances=list(workloads), device=device, stream=stream)
+
+    def instance_slice(self, i: int) -> slice:
+        """Elements of instance i's blocks in a register."""
+        first = sum(1 for B in self.blocks if B.instance < i)
+        last = first + sum(1 for B in self.blocks if B.instance == i)
+        start = sum(self.block_elems[:first])
+        return slice(start, start + sum(self.block_elems[first:last]))
 
     # --- stream ordering between torch's current stream and the context's ---
     def _enter(self):
@@ -176,6 +220,27 @@ class Z4c:
         p = np.ascontiguousarray(np.asarray(par, dtype=np.float64).reshape(-1))
         _check(lib().z4c_set_initial_data(self.ctx, int(kind), p.ctypes.data if p.size else None,
                                           int(p.size)), self.ctx, "z4c_set_initial_data")
+
+    def z4c_set_initial_data_instance(self, instance, kind, par):
+        p = np.ascontiguousarray(np.asarray(par, dtype=np.float64).reshape(-1))
+        _check(lib().z4c_set_initial_data_instance(self.ctx, int(instance), int(kind),
+                                                   p.ctypes.data if p.size else None, int(p.size)),
+               self.ctx, "z4c_set_initial_data_instance")
+
+    def z4c_rk4_step_batch(self, dts, nsteps=1):
+        d = np.ascontiguousarray(np.asarray(dts, dtype=np.float64).reshape(-1))
+        assert d.size == len(self.instances)
+        _check(lib().z4c_rk4_step_batch(self.ctx, d.ctypes.data, int(nsteps)), self.ctx, "z4c_rk4_step_batch")
+        self._leave()
+
+    def z4c_constraints_instance(self, instance, r_mask=0.0):
+        norms = np.zeros(6)
+        self._enter()
+        rc = lib().z4c_constraints_instance(self.ctx, int(instance), float(r_mask), norms.ctypes.data, None)
+        self._leave()
+        if rc not in (Z4C_OK, Z4C_ERR_NAN):
+            _check(rc, self.ctx, "z4c_constraints_instance")
+        return norms, rc
 
     def z4c_fill_ghosts(self, reg=REG_U0):
         self._enter()
