@@ -47,7 +47,8 @@ class _Mesh(ctypes.Structure):
                 ("kappa2", ctypes.c_double), ("eta", ctypes.c_double),
                 ("chi_floor", ctypes.c_double),
                 ("n", ctypes.POINTER(ctypes.c_int32)), ("lo", ctypes.POINTER(ctypes.c_double)),
-                ("h", ctypes.POINTER(ctypes.c_double))]
+                ("h", ctypes.POINTER(ctypes.c_double)),
+                ("level", ctypes.POINTER(ctypes.c_int32))]
 
 
 _lib = None
@@ -64,7 +65,7 @@ def lib():
             "orc_fd": (D, [I, I, P, I, I, I, I, I, I, I, I, D, D]),
             "orc_rhs": (None, [mp, P, P]),
             "orc_rhs_cells": (None, [mp, P, P, L, P]),
-            "orc_fill_ghosts": (None, [mp, P]),
+            "orc_fill_ghosts": (I, [mp, P]),
             "orc_enforce": (None, [mp, P]),
             "orc_rk4_step": (I, [mp, P, D, I]),
             "orc_constraints": (None, [mp, P, D, P, P]),
@@ -105,6 +106,7 @@ class Mesh:
     kappa2: float = 0.0
     eta: float = 2.0
     chi_floor: float = 1e-6
+    level: np.ndarray = None  # (nb,) refinement level per block, or None (all 0)
     _c: _Mesh = field(default=None, repr=False)
 
     def __post_init__(self):
@@ -122,6 +124,9 @@ class Mesh:
         c.n = self.n.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
         c.lo = self.lo.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
         c.h = self.h.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        if self.level is not None:
+            self.level = np.ascontiguousarray(self.level, dtype=np.int32).reshape(-1)
+            c.level = self.level.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
         self._c = c
 
     @property
@@ -184,7 +189,8 @@ class Mesh:
         return u
 
     def fill_ghosts(self, u: np.ndarray) -> np.ndarray:
-        lib().orc_fill_ghosts(ctypes.byref(self._c), _ptr(u))
+        if lib().orc_fill_ghosts(ctypes.byref(self._c), _ptr(u)) != 0:
+            raise ValueError("ghost fill needs data two refinement levels apart")
         return u
 
     def rhs(self, u: np.ndarray) -> np.ndarray:
@@ -204,6 +210,8 @@ class Mesh:
 
     def rk4(self, u: np.ndarray, dt: float, nsteps: int) -> np.ndarray:
         rc = lib().orc_rk4_step(ctypes.byref(self._c), _ptr(u), float(dt), int(nsteps))
+        if rc == -2:
+            raise ValueError("ghost fill needs data two refinement levels apart")
         if rc != 0:
             raise MemoryError("oracle rk4 allocation failed")
         return u

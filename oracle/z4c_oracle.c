@@ -91,6 +91,7 @@ typedef struct {
   const int32_t *n;  /* [nblocks][3] interior cells per direction */
   const double *lo;  /* [nblocks][3] lower corner of each active region */
   const double *h;   /* [nblocks] grid spacing */
+  const int32_t *level; /* [nblocks] refinement level (h = h0 / 2^level), or NULL: all 0 */
 } orc_mesh;
 
 /* ------------------------------------------------------------------ */
@@ -627,7 +628,9 @@ void orc_rhs_cells(const orc_mesh *m, const double *u, const int32_t *cells, lon
 /* ghost fill: same-level copies and periodic wrap (Sec. 3)            */
 /* ------------------------------------------------------------------ */
 
-/* owning block and storage index of the cell whose centre is x, or -1 */
+/* owning block and storage index of the cell whose centre is x, or -1.
+ * Blocks never overlap, so the block containing x is unique (whatever its
+ * level). */
 static int find_owner(const orc_mesh *m, const double x[3], int idx[3]) {
   for (int b = 0; b < m->nblocks; ++b) {
     int inside = 1;
@@ -649,36 +652,184 @@ static int find_owner(const orc_mesh *m, const double x[3], int idx[3]) {
   return -1;
 }
 
-void orc_fill_ghosts(const orc_mesh *m, double *u) {
+static int level_of(const orc_mesh *m, int b) { return m->level ? m->level[b] : 0; }
+
+static void wrap(const orc_mesh *m, double x[3]) {
+  for (int d = 0; d < 3; ++d) {
+    double L = m->dom_hi[d] - m->dom_lo[d];
+    while (x[d] < m->dom_lo[d]) x[d] += L;
+    while (x[d] >= m->dom_hi[d]) x[d] -= L;
+  }
+}
+
+/* Lagrange basis polynomial l_i(x) over the points xs[0..n-1] (Sec. 3.1.1) */
+static double lagrange(const double *xs, int n, int i, double x) {
+  double w = 1.0;
+  for (int q = 0; q < n; ++q)
+    if (q != i) w *= (x - xs[q]) / (xs[i] - xs[q]);
+  return w;
+}
+
+/* Restriction (Sec. 3.1.1): value of field f at the centre xc of a coarse
+ * cell (spacing 2h) covered by fine block F, by 5-point Lagrange
+ * interpolation per axis (3D tensor product) over fine cells that always lie
+ * inside F's active region: the stencil starts at 2c-1 for coarse cells in
+ * the lower half of F and at 2c-2 in the upper half, clamped to [0, n-5]. */
+static double restrict_at(const orc_mesh *m, const double *u, int F, int f, const double xc[3]) {
+  const double h = m->h[F];
+  int s[3];
+  double w[3][5];
+  for (int d = 0; d < 3; ++d) {
+    int n = m->n[3 * F + d], nc = n / 2;
+    int c = (int)floor((xc[d] - m->lo[3 * F + d]) / (2.0 * h));
+    int st = c < nc / 2 ? 2 * c - 1 : 2 * c - 2;
+    if (st < 0) st = 0;
+    if (st > n - 5) st = n - 5;
+    double xs[5];
+    for (int q = 0; q < 5; ++q) xs[q] = m->lo[3 * F + d] + (st + q + 0.5) * h;
+    for (int q = 0; q < 5; ++q) w[d][q] = lagrange(xs, 5, q, xc[d]);
+    s[d] = st + m->ghosts;
+  }
+  long e0 = ext(m, F, 0), e1 = ext(m, F, 1), e2 = ext(m, F, 2);
+  const double *base = u + blk_offset(m, F) + (long)f * e0 * e1 * e2;
+  double v = 0.0;
+  for (int c = 0; c < 5; ++c)
+    for (int b = 0; b < 5; ++b)
+      for (int a = 0; a < 5; ++a)
+        v += w[2][c] * w[1][b] * w[0][a] * base[((long)(s[2] + c) * e1 + (s[1] + b)) * e0 + (s[0] + a)];
+  return v;
+}
+
+/* Coarse value (all fields) at the centre xq of a level-lc cell: the active
+ * value of the level-lc block that owns it, or the restriction of the
+ * level-(lc+1) block that owns it (Sec. 3.1: coarse buffers hold the
+ * restriction of the block's own / same-level neighbours' data and the
+ * coarser neighbours' active data).  Returns 0, or 1 if no such value
+ * exists (outside a non-periodic domain, or levels two apart). */
+static int coarse_value(const orc_mesh *m, const double *u, const double xq_in[3], int lc, double v[NF]) {
+  double xq[3] = {xq_in[0], xq_in[1], xq_in[2]};
+  if (m->periodic)
+    wrap(m, xq);
+  else if (is_outside(m, xq))
+    return 1;
+  int idx[3];
+  int N = find_owner(m, xq, idx);
+  if (N < 0) return 1;
+  if (level_of(m, N) == lc) {
+    long e0 = ext(m, N, 0), e1 = ext(m, N, 1), e2 = ext(m, N, 2);
+    for (int f = 0; f < NF; ++f)
+      v[f] = u[blk_offset(m, N) + (long)f * e0 * e1 * e2 + ((long)idx[2] * e1 + idx[1]) * e0 + idx[0]];
+    return 0;
+  }
+  if (level_of(m, N) == lc + 1) {
+    for (int f = 0; f < NF; ++f) v[f] = restrict_at(m, u, N, f, xq);
+    return 0;
+  }
+  return 1;
+}
+
+/* Ghost fill (Sec. 3, Sec. 3.1): every ghost cell of every block whose centre
+ * lies inside the domain (or anywhere, periodic) gets, from the block that
+ * owns that point,
+ *   - same level: a copy of the active value;
+ *   - one level finer: the restriction of the finer block's active data;
+ *   - one level coarser: the prolongation, 5-point Lagrange per axis over the
+ *     coarse cells parent-2..parent+2, evaluated at the fine centre (offset
+ *     +-1/4 coarse spacing), from the block's coarse buffer: the coarse
+ *     values (coarse_value) over its extent widened by W = g/2 + 2 coarse
+ *     cells (ghost depth plus stencil reach) on every side.
+ * Ghost cells outside a non-periodic domain are Sommerfeld cells, untouched.
+ * Returns 0, or -1 if a stencil needs data that is missing or two levels
+ * apart. */
+int orc_fill_ghosts(const orc_mesh *m, double *u) {
+  int err = 0;
   for (int b = 0; b < m->nblocks; ++b) {
     long e0 = ext(m, b, 0), e1 = ext(m, b, 1), e2 = ext(m, b, 2);
     long S = e0 * e1 * e2;
     double *base = u + blk_offset(m, b);
+    const int L = level_of(m, b);
+    const double hc = 2.0 * m->h[b];
+    const int W = m->ghosts / 2 + 2;
+    double *cb = NULL;   /* coarse buffer [cell][field], cells (nc+2W)^3 */
+    char *cbad = NULL;
+    long cbn[3] = {0, 0, 0}, cb0[3] = {0, 0, 0};
     for (long k = 0; k < e2; ++k)
       for (long j = 0; j < e1; ++j)
         for (long i = 0; i < e0; ++i) {
           if (is_interior(m, b, (int)i, (int)j, (int)k)) continue;
-          double x[3];
+          double x[3], xw[3];
           cell_centre(m, b, (int)i, (int)j, (int)k, x);
-          if (m->periodic) {
-            for (int d = 0; d < 3; ++d) {
-              double L = m->dom_hi[d] - m->dom_lo[d];
-              while (x[d] < m->dom_lo[d]) x[d] += L;
-              while (x[d] >= m->dom_hi[d]) x[d] -= L;
-            }
-          } else if (is_outside(m, x)) {
-            continue; /* Sommerfeld cell: evolved, never copied into */
-          }
+          for (int d = 0; d < 3; ++d) xw[d] = x[d];
+          if (m->periodic)
+            wrap(m, xw);
+          else if (is_outside(m, xw))
+            continue; /* Sommerfeld cell: evolved, never filled */
           int q[3];
-          int ob = find_owner(m, x, q);
+          int ob = find_owner(m, xw, q);
           if (ob < 0) continue;
-          long f0 = ext(m, ob, 0), f1 = ext(m, ob, 1), f2 = ext(m, ob, 2);
-          long So = f0 * f1 * f2;
-          const double *src = u + blk_offset(m, ob) + ((long)q[2] * f1 + q[1]) * f0 + q[0];
           long cidx = (k * e1 + j) * e0 + i;
-          for (int f = 0; f < NF; ++f) base[f * S + cidx] = src[f * So];
+          int lo_ = level_of(m, ob);
+          if (lo_ == L) {
+            long f0 = ext(m, ob, 0), f1 = ext(m, ob, 1), f2 = ext(m, ob, 2);
+            long So = f0 * f1 * f2;
+            const double *src = u + blk_offset(m, ob) + ((long)q[2] * f1 + q[1]) * f0 + q[0];
+            for (int f = 0; f < NF; ++f) base[f * S + cidx] = src[f * So];
+          } else if (lo_ == L + 1) {
+            for (int f = 0; f < NF; ++f) base[f * S + cidx] = restrict_at(m, u, ob, f, xw);
+          } else if (lo_ == L - 1) {
+            if (!cb) { /* build this block's coarse buffer on first use */
+              long tot = 1;
+              for (int d = 0; d < 3; ++d) {
+                cb0[d] = (long)llround((m->lo[3 * b + d] - m->dom_lo[d]) / hc) - W;
+                cbn[d] = m->n[3 * b + d] / 2 + 2 * W;
+                tot *= cbn[d];
+              }
+              cb = malloc(sizeof(double) * NF * tot);
+              cbad = malloc(tot);
+              if (!cb || !cbad) return -3;
+              for (long c2 = 0; c2 < cbn[2]; ++c2)
+                for (long c1 = 0; c1 < cbn[1]; ++c1)
+                  for (long c0 = 0; c0 < cbn[0]; ++c0) {
+                    long ci = (c2 * cbn[1] + c1) * cbn[0] + c0;
+                    double xq[3] = {m->dom_lo[0] + (cb0[0] + c0 + 0.5) * hc,
+                                    m->dom_lo[1] + (cb0[1] + c1 + 0.5) * hc,
+                                    m->dom_lo[2] + (cb0[2] + c2 + 0.5) * hc};
+                    cbad[ci] = (char)coarse_value(m, u, xq, L - 1, cb + NF * ci);
+                  }
+            }
+            long p[3];
+            double w[3][5];
+            for (int d = 0; d < 3; ++d) {
+              p[d] = (long)floor((x[d] - m->dom_lo[d]) / hc) - cb0[d]; /* parent, buffer index */
+              double pc = m->dom_lo[d] + (p[d] + cb0[d] + 0.5) * hc;
+              double xs[5];
+              for (int a = 0; a < 5; ++a) xs[a] = pc + (a - 2) * hc;
+              for (int a = 0; a < 5; ++a) w[d][a] = lagrange(xs, 5, a, x[d]);
+            }
+            double v[NF];
+            for (int f = 0; f < NF; ++f) v[f] = 0.0;
+            for (int c = 0; c < 5; ++c)
+              for (int bb = 0; bb < 5; ++bb)
+                for (int a = 0; a < 5; ++a) {
+                  long c0 = p[0] + a - 2, c1 = p[1] + bb - 2, c2 = p[2] + c - 2;
+                  if (c0 < 0 || c1 < 0 || c2 < 0 || c0 >= cbn[0] || c1 >= cbn[1] || c2 >= cbn[2]) {
+                    err = 1;
+                    continue;
+                  }
+                  long ci = (c2 * cbn[1] + c1) * cbn[0] + c0;
+                  if (cbad[ci]) err = 1;
+                  double wt = w[2][c] * w[1][bb] * w[0][a];
+                  for (int f = 0; f < NF; ++f) v[f] += wt * cb[NF * ci + f];
+                }
+            for (int f = 0; f < NF; ++f) base[f * S + cidx] = v[f];
+          } else {
+            err = 1;
+          }
         }
+    free(cb);
+    free(cbad);
   }
+  return err ? -1 : 0;
 }
 
 /* ------------------------------------------------------------------ */
@@ -757,7 +908,7 @@ int orc_rk4_step(const orc_mesh *m, double *u, double dt, int nsteps) {
         axpy_evolved(m, us, u, c[s] * dt, k[s - 1]);
         orc_enforce(m, us);
       }
-      orc_fill_ghosts(m, us);
+      if (orc_fill_ghosts(m, us)) return -2;
       orc_rhs(m, us, k[s]);
     }
     /* u+ = u0 + dt/6 (k1 + 2 k2 + 2 k3 + k4) */

@@ -121,3 +121,101 @@ def uneven_batch(seed: int = SEED, sizes=(24, 48, 64, 96), n_puncture=64, n_wave
 def uneven_batch_small(seed: int = SEED):
     """The same mix at test size: 6 punctures and 2 gauge waves of 8..20^3."""
     return uneven_batch(seed, sizes=(8, 12, 16, 20), n_puncture=6, n_wave=2)
+
+
+# ---------------------------------------------------------------------------
+# static mesh refinement: oct-tree of equal MeshBlocks (paper Sec. 3, 2:1)
+# ---------------------------------------------------------------------------
+def _touch(a_lo, a_hi, b_lo, b_hi, tol):
+    """Boxes touch or overlap (faces, edges, corners count)."""
+    return all(a_lo[d] <= b_hi[d] + tol and b_lo[d] <= a_hi[d] + tol for d in range(3))
+
+
+def octree_mesh(root_nb, n, dom_lo, dom_hi, centres, radii, max_level, reach=None):
+    """Leaves of an oct-tree of n^3-cell blocks over the box.  A leaf at level
+    L < max_level is refined while its box lies within radii[L] of one of the
+    centres; then 2:1 balance is enforced (a leaf touching a leaf two levels
+    finer, across a face, edge or corner, is refined), and every coarse leaf
+    that the prolongation stencil of a finer neighbour would need two levels
+    apart (within `reach` coarse cells of the fine block, default n/4 + 2) is
+    refined too.  Returns (n, lo, h, level) arrays for the leaves, sorted by
+    level then position."""
+    dom_lo = np.asarray(dom_lo, float)
+    dom_hi = np.asarray(dom_hi, float)
+    h0 = (dom_hi[0] - dom_lo[0]) / (root_nb[0] * n)
+    reach = n // 4 + 2 if reach is None else reach
+    leaves = set()
+    for k in range(root_nb[2]):
+        for j in range(root_nb[1]):
+            for i in range(root_nb[0]):
+                leaves.add((0, i, j, k))
+
+    def box(leaf):
+        L, i, j, k = leaf
+        w = n * h0 / 2 ** L
+        lo = dom_lo + np.array([i, j, k]) * w
+        return lo, lo + w
+
+    def dist(leaf, c):
+        lo, hi = box(leaf)
+        d = np.maximum(0.0, np.maximum(lo - c, c - hi))
+        return float(np.sqrt((d * d).sum()))
+
+    def refine(leaf):
+        L, i, j, k = leaf
+        leaves.discard(leaf)
+        for dk in (0, 1):
+            for dj in (0, 1):
+                for di in (0, 1):
+                    leaves.add((L + 1, 2 * i + di, 2 * j + dj, 2 * k + dk))
+
+    for L in range(max_level):
+        for leaf in [f for f in leaves if f[0] == L]:
+            if any(dist(leaf, np.asarray(c, float)) < radii[L] for c in centres):
+                refine(leaf)
+    changed = True
+    while changed:
+        changed = False
+        ls = sorted(leaves)
+        boxes = {f: box(f) for f in ls}
+        for a in ls:
+            if a not in leaves:
+                continue
+            alo, ahi = boxes[a]
+            for b in ls:
+                if b not in leaves or b[0] <= a[0]:
+                    continue
+                blo, bhi = boxes[b]
+                wb = n * h0 / 2 ** b[0]
+                if b[0] >= a[0] + 2 and _touch(alo, ahi, blo, bhi, 1e-9 * wb):
+                    refine(a)
+                    changed = True
+                    break
+                if b[0] == a[0] + 1:
+                    # b's prolongation reads a's cells within `reach` coarse cells;
+                    # those must not be two levels finer than a: any leaf of
+                    # level >= b+1 there forces a refinement of a
+                    hc = 2 * wb / n
+                    grow = reach * hc
+                    if _touch(alo, ahi, blo - grow, bhi + grow, 1e-9 * wb):
+                        for c in ls:
+                            if c in leaves and c[0] >= b[0] + 1:
+                                clo, chi = boxes[c]
+                                if _touch(clo, chi, blo - grow, bhi + grow, 1e-9 * wb) and \
+                                        _touch(clo, chi, alo, ahi, 1e-9 * wb):
+                                    refine(a)
+                                    changed = True
+                                    break
+                        if changed:
+                            break
+            if changed:
+                break
+    ls = sorted(leaves)
+    ns, los, hs, lev = [], [], [], []
+    for f in ls:
+        lo, _ = box(f)
+        ns.append([n, n, n])
+        los.append(lo)
+        hs.append(h0 / 2 ** f[0])
+        lev.append(f[0])
+    return (np.array(ns, np.int64), np.array(los, float), np.array(hs, float), np.array(lev, np.int64))
