@@ -189,7 +189,10 @@ class Mesh:
         return u
 
     def fill_ghosts(self, u: np.ndarray) -> np.ndarray:
-        if lib().orc_fill_ghosts(ctypes.byref(self._c), _ptr(u)) != 0:
+        rc = lib().orc_fill_ghosts(ctypes.byref(self._c), _ptr(u))
+        if rc == -3:
+            raise MemoryError("oracle coarse-buffer allocation failed")
+        if rc != 0:
             raise ValueError("ghost fill needs data two refinement levels apart")
         return u
 

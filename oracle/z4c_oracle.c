@@ -45,6 +45,15 @@
  *      cell.
  *   R8 shift == 0 freezes beta (d_t beta = 0); lapse == 0 is harmonic
  *      slicing (mu_L = 1), lapse == 1 is 1+log (mu_L = 2/alpha).
+ *   R12 mesh refinement (Sec. 3.1) on one address space: a coarse value is the
+ *      active value of the coarser block that owns the point, or else the
+ *      restriction of the same-level block that owns it; restriction takes
+ *      5 fine cells per axis starting at 2c-1 (coarse cell c in the lower
+ *      half of the block) or 2c-2 (upper half), clamped into the active
+ *      region; prolongation takes the 5 coarse cells parent-2..parent+2.
+ *   R13 along a non-periodic axis the 5 coarse cells of a prolongation
+ *      stencil are shifted (by at most 2) to lie inside the domain, as the
+ *      restriction stencil is kept inside the active region.
  *
  * Field order (fixed): chi, gt_xx gt_xy gt_xz gt_yy gt_yz gt_zz, Khat,
  * At_xx .. At_zz, Gam^x Gam^y Gam^z, Theta, alpha, beta^x beta^y beta^z.
@@ -735,21 +744,26 @@ static int coarse_value(const orc_mesh *m, const double *u, const double xq_in[3
  *   - one level finer: the restriction of the finer block's active data;
  *   - one level coarser: the prolongation, 5-point Lagrange per axis over the
  *     coarse cells parent-2..parent+2, evaluated at the fine centre (offset
- *     +-1/4 coarse spacing), from the block's coarse buffer: the coarse
- *     values (coarse_value) over its extent widened by W = g/2 + 2 coarse
- *     cells (ghost depth plus stencil reach) on every side.
+ *     +-1/4 coarse spacing); along a non-periodic axis the 5 cells are
+ *     shifted to lie inside the domain (reading R13); taken from the
+ *     block's coarse buffer: the coarse
+ *     values (coarse_value) over its extent widened by W = ceil(g/2) + 2
+ *     coarse cells (ghost depth plus stencil reach) on every side.
  * Ghost cells outside a non-periodic domain are Sommerfeld cells, untouched.
  * Returns 0, or -1 if a stencil needs data that is missing or two levels
  * apart. */
 int orc_fill_ghosts(const orc_mesh *m, double *u) {
-  int err = 0;
+  int err = 0, oom = 0;
+  /* blocks in parallel: each writes only its own ghost cells and reads only
+   * active cells */
+#pragma omp parallel for schedule(dynamic) reduction(| : err, oom)
   for (int b = 0; b < m->nblocks; ++b) {
     long e0 = ext(m, b, 0), e1 = ext(m, b, 1), e2 = ext(m, b, 2);
     long S = e0 * e1 * e2;
     double *base = u + blk_offset(m, b);
     const int L = level_of(m, b);
     const double hc = 2.0 * m->h[b];
-    const int W = m->ghosts / 2 + 2;
+    const int W = (m->ghosts + 1) / 2 + 2;
     double *cb = NULL;   /* coarse buffer [cell][field], cells (nc+2W)^3 */
     char *cbad = NULL;
     long cbn[3] = {0, 0, 0}, cb0[3] = {0, 0, 0};
@@ -786,7 +800,10 @@ int orc_fill_ghosts(const orc_mesh *m, double *u) {
               }
               cb = malloc(sizeof(double) * NF * tot);
               cbad = malloc(tot);
-              if (!cb || !cbad) return -3;
+              if (!cb || !cbad) {
+                oom = 1;
+                goto next_block;
+              }
               for (long c2 = 0; c2 < cbn[2]; ++c2)
                 for (long c1 = 0; c1 < cbn[1]; ++c1)
                   for (long c0 = 0; c0 < cbn[0]; ++c0) {
@@ -800,10 +817,17 @@ int orc_fill_ghosts(const orc_mesh *m, double *u) {
             long p[3];
             double w[3][5];
             for (int d = 0; d < 3; ++d) {
-              p[d] = (long)floor((x[d] - m->dom_lo[d]) / hc) - cb0[d]; /* parent, buffer index */
-              double pc = m->dom_lo[d] + (p[d] + cb0[d] + 0.5) * hc;
+              /* stencil start (global level-(L-1) index): parent - 2, shifted
+               * into a non-periodic domain (reading R13) */
+              long st = (long)floor((x[d] - m->dom_lo[d]) / hc) - 2;
+              if (!m->periodic) {
+                long nd = (long)llround((m->dom_hi[d] - m->dom_lo[d]) / hc);
+                if (st > nd - 5) st = nd - 5;
+                if (st < 0) st = 0;
+              }
+              p[d] = st + 2 - cb0[d]; /* stencil centre, buffer index */
               double xs[5];
-              for (int a = 0; a < 5; ++a) xs[a] = pc + (a - 2) * hc;
+              for (int a = 0; a < 5; ++a) xs[a] = m->dom_lo[d] + (st + a + 0.5) * hc;
               for (int a = 0; a < 5; ++a) w[d][a] = lagrange(xs, 5, a, x[d]);
             }
             double v[NF];
@@ -826,9 +850,11 @@ int orc_fill_ghosts(const orc_mesh *m, double *u) {
             err = 1;
           }
         }
+  next_block:
     free(cb);
     free(cbad);
   }
+  if (oom) return -3;
   return err ? -1 : 0;
 }
 

@@ -13,6 +13,11 @@ Workloads (shapes and values follow the paper's test problems, Secs. 4-5):
                     Gamma-driver eta = 2, kappa1 = 0.02, Schwarzschild M = 1
                     with pre-collapsed lapse
   uneven_batch      seeded instances of mixed sizes (see uneven_batch())
+  bl_binary_smr     two Brill-Lindquist punctures (m = 1/2 at x = +-3) on an
+                    oct-tree of 16^3 blocks, 2x2x2 roots at h = 2 over
+                    [-32,32]^3, 6 refinement levels down to h = 1/32, 4
+                    ghosts, order 6, puncture gauge, Sommerfeld boundary,
+                    dt = 1/128 for every block (680 blocks; see octree_mesh)
 """
 from __future__ import annotations
 
@@ -66,7 +71,39 @@ def workload(name: str) -> dict:
                     dom_lo=(-16.0,) * 3, dom_hi=(16.0,) * 3, lapse=1, shift=1, ko_sigma=0.5,
                     kappa1=0.02, kappa2=0.0, eta=2.0, chi_floor=1e-6, cfl=0.25, steps=100,
                     id_kind=ID_SCHWARZSCHILD, id_par=[1.0, 0.0])
+    if name.startswith("bl_binary_smr"):
+        # bl_binary_smr[_<max_level>]: levels 0..max_level (default 6)
+        parts = name.split("_")
+        max_level = int(parts[3]) if len(parts) > 3 else 6
+        n, lo, h, level = octree_mesh((2, 2, 2), 16, (-32.0,) * 3, (32.0,) * 3, BL_BINARY_CENTRES,
+                                      BL_BINARY_RADII, max_level)
+        return dict(name=name, n=n, lo=lo, h=h, level=level, ghosts=4, order=6, periodic=False,
+                    dom_lo=(-32.0,) * 3, dom_hi=(32.0,) * 3, lapse=1, shift=1, ko_sigma=0.5,
+                    kappa1=0.02, kappa2=0.0, eta=2.0, chi_floor=1e-6, cfl=0.25, steps=50,
+                    dt=0.25 * float(h.min()), id_kind=ID_BRILL_LINDQUIST,
+                    id_par=[2.0, 0.5, 3.0, 0.0, 0.0, 0.5, -3.0, 0.0, 0.0])
     raise KeyError(name)
+
+
+def mirror_blocks(n, lo, h):
+    """For each block, the index of the block that is its image under
+    x -> -x (KeyError if the mesh is not symmetric)."""
+    key = {(round(lo[b, 0] / h[b]), round(lo[b, 1] / h[b]), round(lo[b, 2] / h[b]), round(np.log2(h[b]))): b
+           for b in range(len(h))}
+    out = []
+    for b in range(len(h)):
+        xm = -(lo[b, 0] + n[b, 0] * h[b])
+        out.append(key[(round(xm / h[b]), round(lo[b, 1] / h[b]), round(lo[b, 2] / h[b]), round(np.log2(h[b])))])
+    return np.array(out)
+
+
+# Two punctures at x = +-3; a level-L block is refined when it comes within
+# half its own width (16 / 2^L) of one.  Both punctures lie on block faces at
+# every level, so any radius below the block width gives the same 680-block
+# tree: the smallest 2:1-balanced tree that keeps each puncture inside the
+# finest level on all sides.
+BL_BINARY_CENTRES = [(3.0, 0.0, 0.0), (-3.0, 0.0, 0.0)]
+BL_BINARY_RADII = [16.0 / 2 ** L for L in range(6)]
 
 
 def noise(size: int, seed: int, amp: float = 1.0) -> np.ndarray:
@@ -126,40 +163,27 @@ def uneven_batch_small(seed: int = SEED):
 # ---------------------------------------------------------------------------
 # static mesh refinement: oct-tree of equal MeshBlocks (paper Sec. 3, 2:1)
 # ---------------------------------------------------------------------------
-def _touch(a_lo, a_hi, b_lo, b_hi, tol):
-    """Boxes touch or overlap (faces, edges, corners count)."""
-    return all(a_lo[d] <= b_hi[d] + tol and b_lo[d] <= a_hi[d] + tol for d in range(3))
+def octree_mesh(root_nb, n, dom_lo, dom_hi, centres, radii, max_level):
+    """Leaves of an oct-tree of n^3-cell blocks over the box (Sec. 3.1).
 
-
-def octree_mesh(root_nb, n, dom_lo, dom_hi, centres, radii, max_level, reach=None):
-    """Leaves of an oct-tree of n^3-cell blocks over the box.  A leaf at level
-    L < max_level is refined while its box lies within radii[L] of one of the
-    centres; then 2:1 balance is enforced (a leaf touching a leaf two levels
-    finer, across a face, edge or corner, is refined), and every coarse leaf
-    that the prolongation stencil of a finer neighbour would need two levels
-    apart (within `reach` coarse cells of the fine block, default n/4 + 2) is
-    refined too.  Returns (n, lo, h, level) arrays for the leaves, sorted by
-    level then position."""
+    A leaf at level L < max_level is refined while its box comes within
+    radii[L] of one of the centres; then, until nothing changes, a leaf is
+    refined if it touches (face, edge or corner) a leaf two levels finer
+    (2:1 balance).  For n >= 8 and ghost depth <= 4 this balance also keeps
+    every prolongation stencil (ghost depth / 2 + 2 coarse cells beyond a
+    fine block) inside leaves at most one level finer than the coarse
+    neighbour, so no extra rule is needed.  Returns (n, lo, h, level) arrays
+    for the leaves, sorted by level then position."""
     dom_lo = np.asarray(dom_lo, float)
     dom_hi = np.asarray(dom_hi, float)
     h0 = (dom_hi[0] - dom_lo[0]) / (root_nb[0] * n)
-    reach = n // 4 + 2 if reach is None else reach
-    leaves = set()
-    for k in range(root_nb[2]):
-        for j in range(root_nb[1]):
-            for i in range(root_nb[0]):
-                leaves.add((0, i, j, k))
+    leaves = {(0, i, j, k) for k in range(root_nb[2]) for j in range(root_nb[1]) for i in range(root_nb[0])}
 
-    def box(leaf):
-        L, i, j, k = leaf
-        w = n * h0 / 2 ** L
-        lo = dom_lo + np.array([i, j, k]) * w
-        return lo, lo + w
-
-    def dist(leaf, c):
-        lo, hi = box(leaf)
-        d = np.maximum(0.0, np.maximum(lo - c, c - hi))
-        return float(np.sqrt((d * d).sum()))
+    def boxes(ls):
+        a = np.array(ls, dtype=np.int64).reshape(-1, 4)
+        w = n * h0 / 2.0 ** a[:, 0]
+        lo = dom_lo + a[:, [1, 2, 3]] * w[:, None]
+        return a[:, 0], lo, lo + w[:, None], w
 
     def refine(leaf):
         L, i, j, k = leaf
@@ -169,53 +193,28 @@ def octree_mesh(root_nb, n, dom_lo, dom_hi, centres, radii, max_level, reach=Non
                 for di in (0, 1):
                     leaves.add((L + 1, 2 * i + di, 2 * j + dj, 2 * k + dk))
 
+    cs = np.asarray(centres, float).reshape(-1, 3)
     for L in range(max_level):
-        for leaf in [f for f in leaves if f[0] == L]:
-            if any(dist(leaf, np.asarray(c, float)) < radii[L] for c in centres):
-                refine(leaf)
-    changed = True
-    while changed:
-        changed = False
+        ls = [f for f in leaves if f[0] == L]
+        if not ls:
+            continue
+        _, lo, hi, _ = boxes(ls)
+        d = np.maximum(0.0, np.maximum(lo[:, None, :] - cs[None], cs[None] - hi[:, None, :]))
+        near = (np.sqrt((d * d).sum(-1)) < radii[L]).any(axis=1)
+        for f, r in zip(ls, near):
+            if r:
+                refine(f)
+    while True:
         ls = sorted(leaves)
-        boxes = {f: box(f) for f in ls}
-        for a in ls:
-            if a not in leaves:
-                continue
-            alo, ahi = boxes[a]
-            for b in ls:
-                if b not in leaves or b[0] <= a[0]:
-                    continue
-                blo, bhi = boxes[b]
-                wb = n * h0 / 2 ** b[0]
-                if b[0] >= a[0] + 2 and _touch(alo, ahi, blo, bhi, 1e-9 * wb):
-                    refine(a)
-                    changed = True
-                    break
-                if b[0] == a[0] + 1:
-                    # b's prolongation reads a's cells within `reach` coarse cells;
-                    # those must not be two levels finer than a: any leaf of
-                    # level >= b+1 there forces a refinement of a
-                    hc = 2 * wb / n
-                    grow = reach * hc
-                    if _touch(alo, ahi, blo - grow, bhi + grow, 1e-9 * wb):
-                        for c in ls:
-                            if c in leaves and c[0] >= b[0] + 1:
-                                clo, chi = boxes[c]
-                                if _touch(clo, chi, blo - grow, bhi + grow, 1e-9 * wb) and \
-                                        _touch(clo, chi, alo, ahi, 1e-9 * wb):
-                                    refine(a)
-                                    changed = True
-                                    break
-                        if changed:
-                            break
-            if changed:
-                break
+        lev, lo, hi, w = boxes(ls)
+        tol = 1e-9 * w.min()
+        touch = np.all((lo[:, None, :] <= hi[None, :, :] + tol) & (lo[None, :, :] <= hi[:, None, :] + tol), axis=-1)
+        bad = (touch & (lev[None, :] >= lev[:, None] + 2)).any(axis=1)
+        if not bad.any():
+            break
+        for ia in np.where(bad)[0]:
+            refine(ls[ia])
     ls = sorted(leaves)
-    ns, los, hs, lev = [], [], [], []
-    for f in ls:
-        lo, _ = box(f)
-        ns.append([n, n, n])
-        los.append(lo)
-        hs.append(h0 / 2 ** f[0])
-        lev.append(f[0])
-    return (np.array(ns, np.int64), np.array(los, float), np.array(hs, float), np.array(lev, np.int64))
+    lev, lo, _, _ = boxes(ls)
+    h = h0 / 2.0 ** lev
+    return (np.tile(np.array([n, n, n], np.int64), (len(ls), 1)), lo, h, lev.astype(np.int64))

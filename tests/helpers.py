@@ -10,7 +10,7 @@ PARAM_KEYS = ("lapse", "shift", "ko_sigma", "kappa1", "kappa2", "eta", "chi_floo
 def oracle_mesh(oracle, w):
     return oracle.Mesh(n=w["n"], lo=w["lo"], h=w["h"], ghosts=w["ghosts"], order=w["order"],
                        dom_lo=w["dom_lo"], dom_hi=w["dom_hi"], periodic=w["periodic"],
-                       **{k: w[k] for k in PARAM_KEYS})
+                       level=w.get("level"), **{k: w[k] for k in PARAM_KEYS})
 
 
 def gpu_ctx(w, precision=64, schedule=0):

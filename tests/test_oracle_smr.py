@@ -24,9 +24,8 @@ def two_level(oracle, n=8, nb=4, half=8.0, order=6, periodic=False, centre=(0.1,
 def fill_with(m, fn):
     u = m.zeros()
     for b, blk in enumerate(m.blocks(u)):
-        X, Y, Z = m.centres(b)
-        for f in range(22):
-            blk[f] = fn(X, Y, Z) * (1 + 0.1 * f)
+        v = fn(*m.centres(b))
+        blk[:] = v[None] * (1 + 0.1 * np.arange(22))[:, None, None, None]
     return u
 
 
@@ -57,6 +56,58 @@ def test_transfer_exact_on_degree4_polynomials(oracle, deg):
         err = max(err, np.abs(got - want).max())
         scale = max(scale, np.abs(want).max())
     assert err <= 1e-11 * scale, (err, scale)
+
+
+def boundary_two_level(oracle, n=8):
+    """Refined blocks on the x = +8 face next to coarse blocks on the same
+    face: prolongation stencils there need the shift into the domain."""
+    return two_level(oracle, n=n, centre=(7.9, 0.1, 0.2), radius=0.5)
+
+
+def test_boundary_mesh_needs_shifted_stencils(oracle):
+    m = boundary_two_level(oracle)
+    fine = np.where(m.level == 1)[0]
+    assert len(fine) > 0 and np.all(np.isclose(m.lo[fine, 0] + m.n[fine, 0] * m.h[fine], 8.0) |
+                                    (m.lo[fine, 0] + m.n[fine, 0] * m.h[fine] < 8.0))
+    assert np.any(np.isclose(m.lo[fine, 0] + m.n[fine, 0] * m.h[fine], 8.0))
+    assert np.any((m.level == 0) & np.isclose(m.lo[:, 0] + m.n[:, 0] * m.h, 8.0))
+
+
+@pytest.mark.parametrize("deg", [(4, 4, 4), (4, 0, 2)])
+def test_transfer_exact_near_outer_boundary(oracle, deg):
+    """Reading R13: near a non-periodic face the 5 coarse cells of a
+    prolongation stencil are shifted into the domain; Lagrange interpolation
+    on any 5 nodes stays exact for degree <= 4."""
+    m = boundary_two_level(oracle)
+    p = lambda X, Y, Z: (0.3 + X) ** deg[0] * (0.2 - Y) ** deg[1] * (0.1 + Z) ** deg[2]
+    u = fill_with(m, p)
+    ref = u.copy()
+    for b, blk in enumerate(m.blocks(u)):
+        blk[:, ghost_masks(m)[b]] = np.nan
+    m.fill_ghosts(u)
+    err, scale = 0.0, 0.0
+    for b in range(m.nblocks):
+        g = ghost_masks(m)[b]
+        got, want = m.blocks(u)[b][:, g], m.blocks(ref)[b][:, g]
+        assert np.all(np.isfinite(got))
+        err = max(err, np.abs(got - want).max())
+        scale = max(scale, np.abs(want).max())
+    assert err <= 1e-11 * scale, (err, scale)
+
+
+def test_boundary_transfer_converges_at_fifth_order(oracle):
+    """The shifted stencils keep the 5th-order interpolation error."""
+    errs = []
+    for n in (8, 16):
+        m = two_level(oracle, n=n, centre=(7.9, 0.1, 0.2), radius=0.5 * 8 / n)
+        fn = lambda X, Y, Z: np.sin(0.6 * X + 0.3) * np.cos(0.5 * Y - 0.2) * np.sin(0.4 * Z + 0.7)
+        u = fill_with(m, fn)
+        ref = u.copy()
+        m.fill_ghosts(u)
+        errs.append(max(np.abs(m.blocks(u)[b] - m.blocks(ref)[b])[:, ghost_masks(m)[b]].max()
+                        for b in range(m.nblocks) if m.level[b] == 1))
+    rate = np.log2(errs[0] / errs[1])
+    assert rate > 4.5, (errs, rate)
 
 
 def test_transfer_not_exact_on_degree5(oracle):
@@ -113,3 +164,27 @@ def test_linear_wave_with_refined_region(oracle):
     e12, _ = run(12)
     assert nref == 8
     assert np.log(e8 / e12) / np.log(1.5) > 3.5, (e8, e12)
+
+
+def test_bl_binary_mesh_fills_exactly_on_quartics(oracle):
+    """The refined two-puncture mesh (2x2x2 roots of 16^3 at h = 2 over
+    [-32,32]^3, levels 0..6): 680 blocks, symmetric under x -> -x, 2:1
+    balanced; the oracle fills every ghost cell of it (no stencil reaches two
+    levels apart or leaves the domain, reading R13 at the outer faces) and
+    the fill is exact on a tensor quartic."""
+    w = inputs.workload("bl_binary_smr")
+    assert len(w["h"]) == 680 and w["level"].max() == 6
+    assert np.isclose(w["h"].min(), 1.0 / 32) and np.isclose(w["h"].max(), 1.0)
+    pairs = inputs.mirror_blocks(w["n"], w["lo"], w["h"])
+    assert np.all(pairs[pairs] == np.arange(len(pairs)))
+    m = oracle.Mesh(n=w["n"], lo=w["lo"], h=w["h"], level=w["level"], ghosts=4, order=6, dom_lo=w["dom_lo"],
+                    dom_hi=w["dom_hi"], periodic=False)
+    p = lambda X, Y, Z: 1.0 + 1e-6 * (X + 1.0) ** 4 * (2.0 - Y) ** 3 * (Z + 0.5) ** 2
+    u = fill_with(m, p)
+    ref = u.copy()
+    masks = ghost_masks(m)
+    for b, blk in enumerate(m.blocks(u)):
+        blk[:, masks[b]] = np.nan
+    m.fill_ghosts(u)
+    assert np.all(np.isfinite(u))
+    assert np.abs(u - ref).max() <= 1e-11 * np.abs(ref).max()
