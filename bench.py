@@ -45,10 +45,14 @@ L2_BYTES = 129 * 2 ** 20
 FP64_OPS_PER_CELL_STAGE = {6: dict(dadd=951, dfma=1531, dmul=500)}
 # DRAM bytes per launch of that capture (read + write) per interior cell
 FP64_DRAM_BYTES_PER_CELL = {6: (154618880 + 194336512) / 262144}
-# FP32-RHS kernel: FP32 flops and FP64 residue flops per cell per stage
-FP32_FLOPS_PER_CELL_STAGE = {6: None, 4: None}
-FP32_F64_RESIDUE_PER_CELL_STAGE = {6: None, 4: None}
-# algorithmic HBM bytes per zone-cycle (fused 3-register RK4, 22 FP64 fields)
+# FP32-RHS kernel (interior_pre_kernel<6,true,OCC>): executed FP32 and FP64
+# operations per interior cell per stage, from the ncu instruction counters
+# of an 8 x 32^3 order-6 capture (profiles/interior_fp32_single_puncture.md);
+# the arithmetic is the same in every occupancy build.
+FP32_OPS_PER_CELL_STAGE = {6: dict(fadd=955, ffma=1447, fmul=524)}
+FP32_F64_RESIDUE_PER_CELL_STAGE = {6: dict(dadd=47, dfma=22, dmul=23)}
+# algorithmic HBM bytes per zone-cycle (fused 3-register RK4, 22 FP64 fields;
+# the same for the FP32-RHS path, whose state stays FP64)
 ALG_BYTES_PER_ZONE_CYCLE = 352 * 8
 
 
@@ -233,6 +237,28 @@ def measure(z4c, torch, workload, prec, args, ws, local):
                 "peak_nominal": NOMINAL_FP64 / 1e12,
                 "fp64_issue_frac": insts / (interior_ms * 1e-3) / (peak64 / 2),
                 "flops_per_cell_stage": flops / cells}
+    elif prec == 32 and order in FP32_OPS_PER_CELL_STAGE:
+        # the slower of: FP32 flops at the FP32 peak, FP64-residue flops at
+        # the FP64 peak, algorithmic bytes at the HBM bandwidth
+        o32, o64 = FP32_OPS_PER_CELL_STAGE[order], FP32_F64_RESIDUE_PER_CELL_STAGE[order]
+        f32 = (o32["fadd"] + o32["fmul"] + 2 * o32["ffma"]) * cells
+        f64 = (o64["dadd"] + o64["dmul"] + 2 * o64["dfma"]) * cells
+        byt = ALG_BYTES_PER_ZONE_CYCLE / 4 * cells
+        hbm = measured_peaks().get("hbm_gbs", 6800.0) * 1e9
+        t = {"fp32_alu": f32 / peak32, "fp64_residue": f64 / peak64, "hbm": byt / hbm}
+        kind = max(t, key=t.get)
+        sec = interior_ms * 1e-3
+        if kind == "hbm":
+            roof = {"bound": "hbm", "achieved": byt / sec / 1e9, "peak": hbm / 1e9, "unit": "GB/s",
+                    "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
+        else:
+            w, pk = (f32, peak32) if kind == "fp32_alu" else (f64, peak64)
+            roof = {"bound": "alu", "achieved": w / sec / 1e12, "peak": pk / 1e12, "unit": "TFLOP/s",
+                    "peak_source": "measured FMA throughput (z4c_peak_fma), FMA = 2 flops"}
+        roof.update({"frac": t[kind] / sec, "limiter": kind, "traffic": None,
+                     "kernel": f"interior_pre_kernel<{order},true,OCC> (FP32 RHS, FP64 state/RK/enforcement)",
+                     "bound_ms_per_launch": {k: v * 1e3 for k, v in t.items()},
+                     "fracs": {k: v / sec for k, v in t.items()}})
     else:
         bytes_launch = ALG_BYTES_PER_ZONE_CYCLE / 4 * cells
         hbm = measured_peaks().get("hbm_gbs", 6800.0)
@@ -240,7 +266,7 @@ def measure(z4c, torch, workload, prec, args, ws, local):
         roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                 "traffic": None, "kernel": f"interior_pre_kernel<{order},{'true' if prec == 32 else 'false'}>",
                 "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)",
-                "note": "algorithmic bytes view; the per-cell FP32/FP64 op mix is in profiles/"}
+                "note": "algorithmic bytes view (no instruction counts taken for this order)"}
     roof["kernel_ms_per_launch"] = interior_ms
     roof["step_share"] = {"ghost": kms[0] / kms.sum(), "prepass": kms[3] / kms.sum(),
                           "interior": kms[1] / kms.sum(), "sommerfeld": kms[2] / kms.sum()}
@@ -310,6 +336,45 @@ def measure_batch(z4c, torch, steps, warmup):
     return out
 
 
+def measure_smr(z4c, torch, steps, warmup):
+    """The refined two-puncture mesh (680 blocks of 16^3 on levels 0..6,
+    h = 2 .. 1/32, Brill-Lindquist m = 1/2 at x = +-3): whole RK4 steps with
+    restriction / prolongation ghost transfer, one CUDA-graph launch per
+    step, dt = 1/128 for every block; plus the per-kind time split of one
+    step (ghost fill including the refinement transfer, pre-pass, fused
+    RHS + update, Sommerfeld)."""
+    w = inputs.workload("bl_binary_smr")
+    g = z4c.Z4c.from_workload(w)
+    g.z4c_set_initial_data(w["id_kind"], w["id_par"])
+    dt = w["dt"]
+    cells = int(np.prod(w["n"], axis=1).sum())
+    g.z4c_rk4_step(dt, max(1, warmup))
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(g.stream)
+    g.z4c_rk4_step(dt, steps)
+    e1.record(g.stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    split = g.z4c_profile_steps(dt, 1)
+    h_norm = float(g.z4c_constraints()[0][0])
+    out = {"value": cells * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
+           "blocks": int(len(w["h"])), "levels": np.bincount(w["level"]).tolist(), "cells": cells,
+           "storage_per_register_bytes": int(g.nelem * 8),
+           "split_ms_per_step": {"ghost_fill_incl_refinement": split[0], "prepass": split[3],
+                                 "fused_rhs_update": split[1], "sommerfeld": split[2]},
+           "ghost_share": float(split[0] / split.sum()),
+           "hamiltonian_l2_after": h_norm,
+           "gpu_launches": g.z4c_launches_per_step() * steps, "graph_launches_per_step": 1,
+           "workload": "Brill-Lindquist binary m=0.5 at x=+-3, 680 blocks of 16^3, levels 0..6 "
+                       "(h=2..1/32), [-32,32]^3, order 6, 4 ghosts, dt=1/128"}
+    g.close()
+    del g
+    torch.cuda.empty_cache()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -322,6 +387,8 @@ def main():
     ap.add_argument("--cpu-steps", type=int, default=2)
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--batch-steps", type=int, default=5)
+    ap.add_argument("--no-smr", action="store_true")
+    ap.add_argument("--smr-steps", type=int, default=50)
     args = ap.parse_args()
     workload = inputs.workload(args.workload)
 
@@ -354,6 +421,14 @@ def main():
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             batched["value"] = batched["cells"] * ws / (float(t.item()) * 1e-3)
 
+    smr = None
+    if not args.no_smr and args.variant == "both":
+        smr = measure_smr(z4c, torch, args.smr_steps, 2)
+        if ws > 1:
+            t = torch.tensor([smr["ms_per_step"]], device="cuda")
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            smr["value"] = smr["cells"] * ws / (float(t.item()) * 1e-3)
+
     if rank != 0:
         if ws > 1:
             torch.distributed.destroy_process_group()
@@ -384,6 +459,8 @@ def main():
                             "e2e": q["e2e"], "gpu_launches": q["gpu_launches"], "clocks": q["clocks"]}
     if batched is not None:
         line["batched"] = batched
+    if smr is not None:
+        line["smr"] = smr
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()

@@ -64,8 +64,14 @@ typedef struct z4c_mesh {
 
 /* One MeshBlock (Sec. 3): n interior cells per direction, lower corner lo of
  * the active region, cubic cell spacing h.  instance: the independent
- * problem the block belongs to (z4c_create_batch; 0 for z4c_create).  level
- * is reserved for mesh refinement and must be 0. */
+ * problem the block belongs to (z4c_create_batch; 0 for z4c_create).  level:
+ * refinement level, h = h0 / 2^level with one h0 per instance (static mesh
+ * refinement, Sec. 3.1).  The blocks of an instance are the leaves of an
+ * oct-tree: equal n, aligned to their level's block lattice, tiling the mesh;
+ * with more than one level, n is even and >= 8, neighbours (faces, edges,
+ * corners) differ by at most one level, every prolongation stencil finds its
+ * coarse values one level coarser or on its own level (else
+ * Z4C_ERR_BAD_MESH), and the instance is FP64 (rhs_precision 64). */
 typedef struct z4c_block {
   int32_t level;
   int32_t n[3];
@@ -168,8 +174,12 @@ int z4c_set_initial_data(z4c_ctx *ctx, int kind, const double *params, int npara
 int z4c_set_initial_data_instance(z4c_ctx *ctx, int instance, int kind, const double *params, int nparams);
 
 /* Fill the ghost cells of register reg from neighbouring blocks' active
- * cells (same level) or by periodic wrap (Sec. 3).  Sommerfeld cells are
- * evolved, never overwritten. */
+ * cells (same level) or by periodic wrap (Sec. 3); at refinement boundaries
+ * (Sec. 3.1) a ghost cell facing a finer block gets the restriction of its
+ * active data (5-point Lagrange per axis inside the fine active region) and
+ * a ghost cell facing a coarser block the 5^3-point Lagrange prolongation
+ * of coarse values (coarser active cells, or restrictions of same-level
+ * data).  Sommerfeld cells are evolved, never overwritten. */
 int z4c_fill_ghosts(z4c_ctx *ctx, int reg);
 
 /* Raw right-hand side of register reg (ghosts must be filled) into rhs_out

@@ -1,12 +1,17 @@
-// Context creation and binding (C ABI, include/z4c.h): validates each
-// instance's Mesh of MeshBlocks (paper Sec. 3), builds the per-block
+// Context creation and binding (C ABI, include/z4c.h).  Validates each
+// instance's Mesh of MeshBlocks (paper Sec. 3: an oct-tree of equal blocks,
+// neighbours at most one refinement level apart), builds the per-block
 // descriptors, the interior tile lists of every (order, precision) group, the
-// same-level ghost-copy lists and the Sommerfeld cell lists, and lays them out
-// in the caller's scratch buffer.  No CUDA call happens before z4c_bind.
+// Sommerfeld cell lists and the ghost-fill lists: same-level copies and, at
+// refinement boundaries (Sec. 3.1), restrictions, coarse-buffer copies and
+// prolongations.  Everything is laid out in the caller's scratch buffer.  No
+// CUDA call happens before z4c_bind.
 #include <algorithm>
 #include <array>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <unordered_map>
 
 #include "z4c_ctx.cuh"
 
@@ -16,6 +21,15 @@ namespace {
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 long long iround(double v) { return (long long)std::llround(v); }
+long long ifloor(double v) { return (long long)std::floor(v); }
+
+// Lagrange basis polynomial l_i(x) over the points xs[0..4] (Sec. 3.1.1)
+double lagrange5(const double xs[5], int i, double x) {
+  double w = 1.0;
+  for (int q = 0; q < 5; ++q)
+    if (q != i) w *= (x - xs[q]) / (xs[i] - xs[q]);
+  return w;
+}
 
 int check_instance(const z4c_instance &I) {
   const z4c_params &p = I.params;
@@ -30,45 +44,260 @@ int check_instance(const z4c_instance &I) {
   return Z4C_OK;
 }
 
-// Blocks of one instance: one spacing and one size, tiling the mesh on a
-// lattice.  Fills the global integer origin of each block and the lattice
-// (block index per lattice cell, relative to the instance).
-int check_blocks(const z4c_instance &I, const z4c_block *blocks, int count, std::vector<int> &lattice,
-                 std::vector<std::array<long long, 3>> &go, long long N[3], long long nb[3]) {
-  const double h = blocks[0].h;
-  const int *n = blocks[0].n;
-  if (!(h > 0.0)) return Z4C_ERR_BAD_MESH;
-  for (int d = 0; d < 3; ++d)
-    if (n[d] < I.ghosts) return Z4C_ERR_UNSUPPORTED;  // a ghost region must come from one neighbour
-  for (int d = 0; d < 3; ++d) {
-    const double v = (I.mesh.hi[d] - I.mesh.lo[d]) / h;
-    N[d] = iround(v);
-    if (std::fabs(v - N[d]) > 1e-8 * std::max(1.0, v) || N[d] % n[d] != 0) return Z4C_ERR_BAD_MESH;
-    nb[d] = N[d] / n[d];
-  }
-  if (nb[0] * nb[1] * nb[2] != count) return Z4C_ERR_BAD_MESH;
-  lattice.assign(count, -1);
-  go.resize(count);
+// The blocks of one instance: equal n, spacing h0 / 2^level, aligned to their
+// level's block lattice, tiling the mesh without overlap.  The owner map
+// records the block covering each cell of the finest block lattice.
+struct Layout {
+  int n[3] = {0, 0, 0};
+  double h0 = 0.0;
+  int lmax = 0;
+  double unit[3] = {0, 0, 0};     // finest block width per axis
+  long long M[3] = {0, 0, 0};     // finest lattice cells per axis
+  std::vector<int> owner;         // local block index per finest lattice cell
+  std::vector<std::array<long long, 3>> go;  // first interior cell, global index at the block's level
+};
+
+int make_layout(const z4c_instance &I, const z4c_block *blocks, int count, Layout &Lo) {
+  for (int d = 0; d < 3; ++d) Lo.n[d] = blocks[0].n[d];
+  Lo.h0 = blocks[0].h * std::ldexp(1.0, blocks[0].level);
+  if (!(Lo.h0 > 0.0)) return Z4C_ERR_BAD_MESH;
   for (int b = 0; b < count; ++b) {
     const z4c_block &B = blocks[b];
-    if (B.level != 0) return Z4C_ERR_UNSUPPORTED;
-    if (std::fabs(B.h - h) > 1e-12 * h) return Z4C_ERR_BAD_MESH;
-    long long L[3];
-    for (int d = 0; d < 3; ++d) {
-      if (B.n[d] != n[d]) return Z4C_ERR_BAD_MESH;
-      const double v = (B.lo[d] - I.mesh.lo[d]) / h;
-      go[b][d] = iround(v);
-      if (std::fabs(v - go[b][d]) > 1e-8 * std::max(1.0, std::fabs(v))) return Z4C_ERR_BAD_MESH;
-      if (go[b][d] < 0 || go[b][d] % n[d] != 0) return Z4C_ERR_BAD_MESH;
-      L[d] = go[b][d] / n[d];
-      if (L[d] >= nb[d]) return Z4C_ERR_BAD_MESH;
-    }
-    const long long li = (L[2] * nb[1] + L[1]) * nb[0] + L[0];
-    if (lattice[li] != -1) return Z4C_ERR_BAD_MESH;  // overlap
-    lattice[li] = b;
+    if (B.level < 0 || B.level > 20) return Z4C_ERR_BAD_MESH;
+    for (int d = 0; d < 3; ++d)
+      if (B.n[d] != Lo.n[d]) return Z4C_ERR_BAD_MESH;
+    if (std::fabs(B.h * std::ldexp(1.0, B.level) - Lo.h0) > 1e-12 * Lo.h0) return Z4C_ERR_BAD_MESH;
+    Lo.lmax = std::max(Lo.lmax, B.level);
   }
+  for (int d = 0; d < 3; ++d)
+    if (Lo.n[d] < I.ghosts) return Z4C_ERR_UNSUPPORTED;  // a ghost region must come from one neighbour
+  if (Lo.lmax > 0)  // restriction stencils: 5 fine cells inside an even block
+    for (int d = 0; d < 3; ++d)
+      if (Lo.n[d] < 8 || Lo.n[d] % 2) return Z4C_ERR_UNSUPPORTED;
+  long long total = 1;
+  for (int d = 0; d < 3; ++d) {
+    Lo.unit[d] = Lo.n[d] * Lo.h0 / std::ldexp(1.0, Lo.lmax);
+    const double v = (I.mesh.hi[d] - I.mesh.lo[d]) / Lo.unit[d];
+    Lo.M[d] = iround(v);
+    if (Lo.M[d] < 1 || std::fabs(v - Lo.M[d]) > 1e-8 * std::max(1.0, v)) return Z4C_ERR_BAD_MESH;
+    total *= Lo.M[d];
+  }
+  if (total > (1LL << 28)) return Z4C_ERR_UNSUPPORTED;
+  Lo.owner.assign((size_t)total, -1);
+  Lo.go.resize(count);
+  for (int b = 0; b < count; ++b) {
+    const z4c_block &B = blocks[b];
+    const long long span = 1LL << (Lo.lmax - B.level);  // finest cells per block
+    long long o[3];
+    for (int d = 0; d < 3; ++d) {
+      const double v = (B.lo[d] - I.mesh.lo[d]) / Lo.unit[d];
+      o[d] = iround(v);
+      if (std::fabs(v - o[d]) > 1e-8 * std::max(1.0, std::fabs(v))) return Z4C_ERR_BAD_MESH;
+      if (o[d] < 0 || o[d] % span != 0 || o[d] + span > Lo.M[d]) return Z4C_ERR_BAD_MESH;
+      Lo.go[b][d] = o[d] / span * Lo.n[d];
+    }
+    for (long long k = o[2]; k < o[2] + span; ++k)
+      for (long long j = o[1]; j < o[1] + span; ++j)
+        for (long long i = o[0]; i < o[0] + span; ++i) {
+          int &c = Lo.owner[(size_t)((k * Lo.M[1] + j) * Lo.M[0] + i)];
+          if (c != -1) return Z4C_ERR_BAD_MESH;  // overlap
+          c = b;
+        }
+  }
+  for (int c : Lo.owner)
+    if (c == -1) return Z4C_ERR_BAD_MESH;  // gap
   return Z4C_OK;
 }
+
+// Builder of one instance's ghost-fill lists.
+struct GhostBuilder {
+  z4c_ctx *ctx;
+  const Instance &I;
+  const Layout &Lo;
+  int p;  // precision slot
+  std::map<int, int> wpat;  // restriction pattern key -> row of ctx->wtab
+  std::map<std::array<long long, 4>, int> slot;  // (level, wrapped coarse cell) -> coarse-buffer slot
+
+  const z4c_block &blk(int lb) const { return ctx->blocks[I.first + lb]; }
+  double hb(int lb) const { return blk(lb).h; }
+
+  // wrap into a periodic domain; false if outside a non-periodic one
+  bool inside(double x[3]) const {
+    for (int d = 0; d < 3; ++d) {
+      if (I.mesh.periodic) {
+        const double L = I.mesh.hi[d] - I.mesh.lo[d];
+        while (x[d] < I.mesh.lo[d]) x[d] += L;
+        while (x[d] >= I.mesh.hi[d]) x[d] -= L;
+      } else if (x[d] < I.mesh.lo[d] || x[d] > I.mesh.hi[d]) {
+        return false;
+      }
+    }
+    return true;
+  }
+
+  int owner_of(const double x[3]) const {
+    long long u[3];
+    for (int d = 0; d < 3; ++d) {
+      u[d] = ifloor((x[d] - I.mesh.lo[d]) / Lo.unit[d]);
+      u[d] = std::min(std::max(u[d], 0LL), Lo.M[d] - 1);
+    }
+    return Lo.owner[(size_t)((u[2] * Lo.M[1] + u[1]) * Lo.M[0] + u[0])];
+  }
+
+  int storage_index(int lb, const long long q[3]) const {
+    const int g = I.ghosts;
+    const long long e0 = Lo.n[0] + 2 * g, e1 = Lo.n[1] + 2 * g;
+    return (int)((q[2] * e1 + q[1]) * e0 + q[0]);
+  }
+
+  // storage index in block lb of the cell whose centre is x
+  int cell_in(int lb, const double x[3]) const {
+    long long q[3];
+    for (int d = 0; d < 3; ++d) q[d] = ifloor((x[d] - blk(lb).lo[d]) / hb(lb)) + I.ghosts;
+    return storage_index(lb, q);
+  }
+
+  int pattern(int key) {
+    auto it = wpat.find(key);
+    if (it != wpat.end()) return it->second;
+    // fine points at offsets key + q - 1/2 (fine units) from the coarse centre
+    double xs[5];
+    for (int q = 0; q < 5; ++q) xs[q] = key + q - 0.5;
+    const int row = (int)(ctx->wtab.size() / 5);
+    for (int q = 0; q < 5; ++q) ctx->wtab.push_back(lagrange5(xs, q, 0.0));
+    wpat[key] = row;
+    return row;
+  }
+
+  // restriction of fine block nb at the coarse cell centred at x (Sec. 3.1.1):
+  // 5 fine cells per axis, start 2c-1 (lower half of the block) or 2c-2
+  // (upper half), clamped into the active region
+  RestrictRef restriction(int nb, const double x[3]) {
+    RestrictRef r{};
+    long long st[3];
+    for (int d = 0; d < 3; ++d) {
+      const int n = Lo.n[d], nc = n / 2;
+      const long long c = ifloor((x[d] - blk(nb).lo[d]) / (2.0 * hb(nb)));
+      long long s = c < nc / 2 ? 2 * c - 1 : 2 * c - 2;
+      s = std::min<long long>(std::max<long long>(s, 0), n - 5);
+      r.wp[d] = pattern((int)(s - 2 * c));
+      st[d] = s + I.ghosts;
+    }
+    r.src = I.first + nb;
+    r.s = storage_index(nb, st);
+    return r;
+  }
+
+  // coarse-buffer slot of the level-lc cell with global index q (unwrapped)
+  int coarse_slot(int lc, const long long q[3], int &err) {
+    double x[3];
+    const double hc = Lo.h0 / std::ldexp(1.0, lc);
+    for (int d = 0; d < 3; ++d) x[d] = I.mesh.lo[d] + (q[d] + 0.5) * hc;
+    if (!inside(x)) {
+      err = 1;
+      return 0;
+    }
+    long long w[3];
+    for (int d = 0; d < 3; ++d) w[d] = ifloor((x[d] - I.mesh.lo[d]) / hc);
+    const std::array<long long, 4> key = {lc, w[0], w[1], w[2]};
+    auto it = slot.find(key);
+    if (it != slot.end()) return it->second;
+    const int nb = owner_of(x);
+    const int s = ctx->ncb++;
+    if (blk(nb).level == lc) {
+      ctx->cbcopy.push_back(CbCopy{s, I.first + nb, cell_in(nb, x), 0});
+    } else if (blk(nb).level == lc + 1) {
+      RestrictRef r = restriction(nb, x);
+      r.dst = -1;
+      r.didx = s;
+      ctx->rbuf.push_back(r);
+    } else {
+      err = 1;  // two levels apart
+    }
+    slot[key] = s;
+    return s;
+  }
+
+  int build() {
+    const int g = I.ghosts;
+    const int e[3] = {Lo.n[0] + 2 * g, Lo.n[1] + 2 * g, Lo.n[2] + 2 * g};
+    int err = 0;
+    for (int lb = 0; lb < I.count; ++lb) {
+      const int b = I.first + lb, L = blk(lb).level;
+      const double h = hb(lb);
+      std::map<std::array<long long, 3>, int> parents;  // prolongation parents already listed
+      for (int k = 0; k < e[2]; ++k)
+        for (int j = 0; j < e[1]; ++j)
+          for (int i = 0; i < e[0]; ++i) {
+            const int idx[3] = {i, j, k};
+            bool interior = true;
+            for (int d = 0; d < 3; ++d) interior &= idx[d] >= g && idx[d] < Lo.n[d] + g;
+            if (interior) continue;
+            double x[3], xw[3];
+            for (int d = 0; d < 3; ++d) xw[d] = x[d] = blk(lb).lo[d] + (idx[d] - g + 0.5) * h;
+            const int cidx = (k * e[1] + j) * e[0] + i;
+            if (!inside(xw)) {
+              ctx->somm[p].push_back(CellRef{b, cidx});
+              continue;
+            }
+            const int nb = owner_of(xw);
+            const int ln = blk(nb).level;
+            if (ln == L) {
+              ctx->gcopy[p].push_back(GhostCopy{b, cidx, I.first + nb, cell_in(nb, xw)});
+            } else if (ln == L + 1) {
+              RestrictRef r = restriction(nb, xw);
+              r.dst = b;
+              r.didx = cidx;
+              ctx->rghost.push_back(r);
+            } else if (ln == L - 1) {
+              // parent coarse cell (global index at level L-1, unwrapped)
+              std::array<long long, 3> pc;
+              const double hc = 2.0 * h;
+              for (int d = 0; d < 3; ++d) pc[d] = ifloor((x[d] - I.mesh.lo[d]) / hc);
+              if (parents.count(pc)) continue;
+              parents[pc] = 1;
+              long long child[3];
+              int ok[3][2];
+              for (int d = 0; d < 3; ++d) {
+                child[d] = 2 * pc[d] - Lo.go[lb][d] + g;  // storage index of the lower child
+                ok[d][0] = child[d] >= 0 && child[d] < e[d];
+                ok[d][1] = child[d] + 1 >= 0 && child[d] + 1 < e[d];
+              }
+              int mask = 0;
+              for (int q = 0; q < 8; ++q)
+                if (ok[0][q & 1] && ok[1][(q >> 1) & 1] && ok[2][(q >> 2) & 1]) mask |= 1 << q;
+              // stencil shift into a non-periodic domain: cells pc-2+sh .. pc+2+sh
+              // must lie in [0, nd) with nd the level-(L-1) cells across the domain
+              long long sh[3] = {0, 0, 0};
+              if (!I.mesh.periodic)
+                for (int d = 0; d < 3; ++d) {
+                  const long long nd = iround((I.mesh.hi[d] - I.mesh.lo[d]) / hc);
+                  const long long s0 = std::max<long long>(std::min<long long>(pc[d] - 2, nd - 5), 0);
+                  sh[d] = s0 - (pc[d] - 2);
+                }
+              for (int d = 0; d < 3; ++d) {
+                if (sh[d] < -2 || sh[d] > 2) err = 1;  // domain narrower than 5 coarse cells
+                else mask |= (int)(sh[d] + 2) << (PROLONG_SHIFT_BIT + 3 * d);
+              }
+              // the lower child may lie before the storage (odd ghost width): address
+              // children relative to an index that can be negative; the kernel only
+              // touches the masked ones
+              ProlongRef pr{b, (int)((child[2] * e[1] + child[1]) * e[0] + child[0]), (int)ctx->pidx.size(), mask};
+              for (int c = 0; c < 5; ++c)
+                for (int bb = 0; bb < 5; ++bb)
+                  for (int a = 0; a < 5; ++a) {
+                    const long long q[3] = {pc[0] + sh[0] + a - 2, pc[1] + sh[1] + bb - 2, pc[2] + sh[2] + c - 2};
+                    ctx->pidx.push_back(coarse_slot(L - 1, q, err));
+                  }
+              ctx->prol.push_back(pr);
+            } else {
+              err = 1;  // neighbours more than one level apart
+            }
+          }
+    }
+    return err ? Z4C_ERR_BAD_MESH : Z4C_OK;
+  }
+};
 
 }  // namespace
 
@@ -95,19 +324,31 @@ int z4c_create_batch(const z4c_instance *instances, int ninstances, const z4c_bl
   }
 
   z4c_ctx *ctx = new z4c_ctx();
+  auto bail = [&](int code) {
+    delete ctx;
+    return code;
+  };
   ctx->blocks.assign(blocks, blocks + nblocks);
   int64_t off = 0;
   bool sched_set[2] = {false, false};
+  // prolongation weights: coarse points at shift-2..shift+2 (coarse
+  // spacing) from the parent centre, evaluated at the children's offsets
+  // -1/4 and +1/4, for shift = -2..2
+  for (int sh = -2; sh <= 2; ++sh) {
+    double xs[5];
+    for (int q = 0; q < 5; ++q) xs[q] = sh + q - 2;
+    for (int q = 0; q < 5; ++q) {
+      ctx->pw[10 * (sh + 2) + q] = lagrange5(xs, q, -0.25);
+      ctx->pw[10 * (sh + 2) + 5 + q] = lagrange5(xs, q, 0.25);
+    }
+  }
   for (int i = 0; i < ninstances; ++i) {
     const z4c_instance &I = instances[i];
-    std::vector<int> lattice;
-    std::vector<std::array<long long, 3>> go;
-    long long N[3], nb[3];
-    const int r = check_blocks(I, blocks + first[i], count[i], lattice, go, N, nb);
-    if (r) {
-      delete ctx;
-      return r;
-    }
+    Layout Lo;
+    int r = make_layout(I, blocks + first[i], count[i], Lo);
+    if (r) return bail(r);
+    const bool f32 = I.params.rhs_precision == 32;
+    if (f32 && Lo.lmax > 0) return bail(Z4C_ERR_UNSUPPORTED);  // refinement transfer is FP64 only
     Instance in;
     in.mesh = I.mesh;
     in.params = I.params;
@@ -116,7 +357,6 @@ int z4c_create_batch(const z4c_instance *instances, int ninstances, const z4c_bl
     in.first = first[i];
     in.count = count[i];
     ctx->inst.push_back(in);
-    const bool f32 = I.params.rhs_precision == 32;
     const int p = f32 ? 1 : 0;
     ctx->has[p] = true;
     if (!sched_set[p]) {
@@ -124,22 +364,20 @@ int z4c_create_batch(const z4c_instance *instances, int ninstances, const z4c_bl
       sched_set[p] = true;
     }
     const int g = I.ghosts, ord = I.fd_order;
-    const int *n = blocks[first[i]].n;
-    const double h = blocks[first[i]].h;
+    const int *n = Lo.n;
     const int e[3] = {n[0] + 2 * g, n[1] + 2 * g, n[2] + 2 * g};
     const long long S = (long long)e[0] * e[1] * e[2];
-    if (S * NF >= (1LL << 31)) {
-      delete ctx;
-      return Z4C_ERR_UNSUPPORTED;
-    }
+    if (S * NF >= (1LL << 31)) return bail(Z4C_ERR_UNSUPPORTED);
     ctx->max_S = std::max(ctx->max_S, (int)S);
     const double den1 = ord == 4 ? 12.0 : 60.0, den2 = ord == 4 ? 12.0 : 180.0;
     const double kosg = ord == 4 ? 1.0 / 64.0 : -1.0 / 256.0;  // (-1)^(N+1) / 2^(2N)
     Group &G = ctx->grp[2 * (ord == 6) + (f32 ? 1 : 0)];
     G.order = ord;
     G.f32 = f32;
+    const int W = ord / 2;
     for (int lb = 0; lb < count[i]; ++lb) {
       const int b = first[i] + lb;
+      const double h = blocks[b].h;
       DevBlock D{};
       for (int d = 0; d < 3; ++d) {
         D.n[d] = n[d];
@@ -173,8 +411,6 @@ int z4c_create_batch(const z4c_instance *instances, int ninstances, const z4c_bl
       D.f32 = f32 ? 1 : 0;
       ctx->dblocks.push_back(D);
       ctx->dt_host.push_back(0.0);
-      // interior tiles (fused kernel, constraints) and widened tiles (pre-pass)
-      const int W = ord / 2;
       for (int k = 0; k < n[2]; ++k) {
         for (int j0 = 0; j0 < n[1]; j0 += TY)
           for (int i0 = 0; i0 < n[0]; i0 += TX) {
@@ -184,38 +420,10 @@ int z4c_create_batch(const z4c_instance *instances, int ninstances, const z4c_bl
         for (int j0 = -W; j0 < n[1] + W; j0 += TY)
           for (int i0 = -W; i0 < n[0] + W; i0 += TX) G.wtiles.push_back(Tile{b, i0, j0, k});
       }
-      // ghost cells: copies from the lattice neighbour, or Sommerfeld cells
-      for (int k = 0; k < e[2]; ++k)
-        for (int j = 0; j < e[1]; ++j)
-          for (int ii = 0; ii < e[0]; ++ii) {
-            const int idx[3] = {ii, j, k};
-            bool interior = true;
-            for (int d = 0; d < 3; ++d) interior &= idx[d] >= g && idx[d] < n[d] + g;
-            if (interior) continue;
-            long long Gc[3];
-            bool outside = false;
-            for (int d = 0; d < 3; ++d) {
-              Gc[d] = go[lb][d] + idx[d] - g;
-              if (I.mesh.periodic)
-                Gc[d] = ((Gc[d] % N[d]) + N[d]) % N[d];
-              else if (Gc[d] < 0 || Gc[d] >= N[d])
-                outside = true;
-            }
-            const int cidx = (k * e[1] + j) * e[0] + ii;
-            if (outside) {
-              ctx->somm[p].push_back(CellRef{b, cidx});
-              continue;
-            }
-            long long L[3], q[3];
-            for (int d = 0; d < 3; ++d) {
-              L[d] = Gc[d] / n[d];
-              q[d] = Gc[d] - L[d] * n[d] + g;
-            }
-            const int src = first[i] + lattice[(L[2] * nb[1] + L[1]) * nb[0] + L[0]];
-            const int scidx = (int)((q[2] * e[1] + q[1]) * e[0] + q[0]);
-            ctx->gcopy[p].push_back(GhostCopy{b, cidx, src, scidx});
-          }
     }
+    GhostBuilder gb{ctx, ctx->inst.back(), Lo, p, {}, {}};
+    r = gb.build();
+    if (r) return bail(r);
   }
   ctx->reg_elems = (size_t)off;
 
@@ -235,6 +443,14 @@ int z4c_create_batch(const z4c_instance *instances, int ninstances, const z4c_bl
     ctx->o_somm[p] = take(sizeof(CellRef) * ctx->somm[p].size());
     ctx->o_gcopy[p] = take(sizeof(GhostCopy) * ctx->gcopy[p].size());
   }
+  ctx->o_rghost = take(sizeof(RestrictRef) * ctx->rghost.size());
+  ctx->o_rbuf = take(sizeof(RestrictRef) * ctx->rbuf.size());
+  ctx->o_cbcopy = take(sizeof(CbCopy) * ctx->cbcopy.size());
+  ctx->o_prol = take(sizeof(ProlongRef) * ctx->prol.size());
+  ctx->o_pidx = take(sizeof(int32_t) * ctx->pidx.size());
+  ctx->o_wtab = take(sizeof(double) * ctx->wtab.size());
+  ctx->o_pw = take(sizeof(double) * 50);
+  ctx->o_cb = take(sizeof(double) * NF * (size_t)ctx->ncb);
   ctx->o_ctiles = take(sizeof(Tile) * ctx->ctiles.size());
   ctx->o_part = take(sizeof(double) * 8 * 2 * ctx->ctiles.size());  // order-4 and order-6 records
   ctx->o_res = take(sizeof(double) * 8);
@@ -303,6 +519,13 @@ int z4c_bind(z4c_ctx *ctx, void *u0, void *stage_a, void *stage_b, void *acc, vo
     CK(up(ctx->o_somm[p], ctx->somm[p].data(), sizeof(CellRef) * ctx->somm[p].size()));
     CK(up(ctx->o_gcopy[p], ctx->gcopy[p].data(), sizeof(GhostCopy) * ctx->gcopy[p].size()));
   }
+  CK(up(ctx->o_rghost, ctx->rghost.data(), sizeof(RestrictRef) * ctx->rghost.size()));
+  CK(up(ctx->o_rbuf, ctx->rbuf.data(), sizeof(RestrictRef) * ctx->rbuf.size()));
+  CK(up(ctx->o_cbcopy, ctx->cbcopy.data(), sizeof(CbCopy) * ctx->cbcopy.size()));
+  CK(up(ctx->o_prol, ctx->prol.data(), sizeof(ProlongRef) * ctx->prol.size()));
+  CK(up(ctx->o_pidx, ctx->pidx.data(), sizeof(int32_t) * ctx->pidx.size()));
+  CK(up(ctx->o_wtab, ctx->wtab.data(), sizeof(double) * ctx->wtab.size()));
+  CK(up(ctx->o_pw, ctx->pw, sizeof(double) * 50));
   CK(up(ctx->o_ctiles, ctx->ctiles.data(), sizeof(Tile) * ctx->ctiles.size()));
   // the tables live in host vectors owned by ctx; wait so the copies are done
   CK(cudaStreamSynchronize(st));

@@ -42,13 +42,23 @@ struct z4c_ctx {
   std::vector<z4c::CellRef> somm[2];    // Sommerfeld cells, per precision (0 FP64, 1 FP32)
   std::vector<z4c::GhostCopy> gcopy[2];  // same-level ghost copies, per precision
   std::vector<z4c::Tile> ctiles;         // every interior tile (constraints)
+  // mesh refinement transfer (FP64 instances with more than one level)
+  std::vector<z4c::RestrictRef> rghost;  // coarse ghost cells <- restriction of a finer block
+  std::vector<z4c::RestrictRef> rbuf;    // coarse-buffer slots <- restriction of a same-level block
+  std::vector<z4c::CbCopy> cbcopy;       // coarse-buffer slots <- a coarser block's active cell
+  std::vector<z4c::ProlongRef> prol;     // fine ghost cells <- prolongation from the buffer
+  std::vector<int32_t> pidx;             // 125 buffer slots per prolongation entry
+  std::vector<double> wtab;              // restriction weight patterns (5 each)
+  double pw[50] = {0};                   // prolongation weights [shift + 2][child][5]
+  int ncb = 0;                           // coarse-buffer slots
   std::vector<double> dt_host;           // time step per block
   size_t reg_elems = 0;
   int max_S = 0;
   bool has[2] = {false, false};          // precisions present
   // scratch layout (byte offsets)
   size_t o_blocks = 0, o_somm[2] = {0, 0}, o_gcopy[2] = {0, 0}, o_ctiles = 0, o_part = 0, o_res = 0,
-         o_dt = 0, o_sh0 = 0, o_sh1 = 0, o_ds64 = 0, o_ds32 = 0, scratch_total = 0;
+         o_dt = 0, o_sh0 = 0, o_sh1 = 0, o_ds64 = 0, o_ds32 = 0, o_rghost = 0, o_rbuf = 0, o_cbcopy = 0,
+         o_prol = 0, o_pidx = 0, o_wtab = 0, o_pw = 0, o_cb = 0, scratch_total = 0;
   // bound buffers
   double *reg[4] = {nullptr, nullptr, nullptr, nullptr};
   char *scratch = nullptr;
@@ -74,6 +84,10 @@ struct z4c_ctx {
   double *d_dt() const { return (double *)(scratch + o_dt); }
   float *d_sh(int q) const { return (float *)(scratch + (q == 0 ? o_sh0 : o_sh1)); }
   void *d_dstore(bool f32) const { return scratch + (f32 ? o_ds32 : o_ds64); }
+  bool smr() const { return !prol.empty() || !rghost.empty(); }
+  template <class T>
+  const T *at(size_t o) const { return (const T *)(scratch + o); }
+  double *d_cb() const { return (double *)(scratch + o_cb); }
   void drop_graph() {
     if (graph) {
       cudaGraphExecDestroy(graph);

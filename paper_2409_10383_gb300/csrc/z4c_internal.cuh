@@ -56,6 +56,35 @@ struct GhostCopy {
   int32_t dst_block, dst_cidx, src_block, src_cidx;
 };
 
+// Mesh refinement transfer (paper Sec. 3.1), FP64 registers only.
+// Restriction: the value at a coarse cell covered by fine block `src` is
+// sum_{a,b,c} w[pz][c] w[py][b] w[px][a] u[src, s + a + b e0 + c e0 e1] over
+// the 5^3 fine cells starting at storage cell s (weights by pattern id).
+struct RestrictRef {
+  int32_t dst;    // ghost mode: destination block; buffer mode: unused
+  int32_t didx;   // ghost mode: destination cell index; buffer mode: coarse-buffer slot
+  int32_t src;    // fine block
+  int32_t s;      // storage index of the stencil's lowest corner in src
+  int32_t wp[3];  // weight pattern per axis (x, y, z)
+  int32_t pad;
+};
+// Coarse-buffer slot <- active cell of a coarser block.
+struct CbCopy {
+  int32_t slot, src, scidx, pad;
+};
+// Prolongation of one parent coarse cell into its fine ghost children of
+// block dst: child (dx, dy, dz) at cidx0 + dx + dy e0 + dz e0 e1 is written
+// if bit dx + 2 dy + 4 dz of mask is set (children beyond the storage, with
+// an odd ghost width, are not); coarse values from 125 coarse-buffer slots
+// (x fastest) starting at idx[base].  Bits 8 + 3d .. 10 + 3d of mask hold
+// the stencil shift along axis d plus 2 (0..4): the 5 coarse cells are
+// parent + shift - 2 .. parent + shift + 2, shift != 0 only next to a
+// non-periodic outer boundary.
+struct ProlongRef {
+  int32_t dst, cidx0, base, mask;
+};
+constexpr int PROLONG_SHIFT_BIT = 8;
+
 // Which update the stage kernel applies after computing k = RHS(x):
 //   MODE_RHS:  rhs_out = k
 //   MODE_S1:   acc = u0 + cb k;  next = enforce(u0 + ca k)
@@ -84,6 +113,14 @@ constexpr int TX = 16;
 constexpr int TY = 8;
 
 // ---- launchers (defined in the kernel translation units) ----
+// refinement transfer: restriction into ghost cells (to_buffer = false) or
+// into coarse-buffer slots (true); buffer copies; prolongation from the buffer
+cudaError_t launch_restrict(double *reg, const DevBlock *blocks, const RestrictRef *list, int n,
+                            const double *wtab, bool to_buffer, double *cb, int ncb, cudaStream_t st);
+cudaError_t launch_cb_copy(const double *reg, const DevBlock *blocks, const CbCopy *list, int n, double *cb,
+                           int ncb, cudaStream_t st);
+cudaError_t launch_prolong(double *reg, const DevBlock *blocks, const ProlongRef *list, int n,
+                           const int32_t *idx, const double *cb, int ncb, const double *pw, cudaStream_t st);
 // FP32 fused pre-pass-schedule kernel built for 2 or 4 resident CTAs per SM
 cudaError_t launch_fused_pre_f32_occ2(int order, const StageArgs &a, const Tile *tiles, int ntiles,
                                       cudaStream_t st);

@@ -1,0 +1,30 @@
+// Launchers of the mesh-refinement transfer kernels (device code in z4c_smr.cuh).
+#include "z4c_smr.cuh"
+
+namespace z4c {
+
+cudaError_t launch_restrict(double *reg, const DevBlock *blocks, const RestrictRef *list, int n, const double *wtab,
+                            bool to_buffer, double *cb, int ncb, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const long long tot = (long long)n * NF;
+  restrict_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(reg, blocks, list, n, wtab, to_buffer ? 1 : 0, cb,
+                                                                  ncb);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cb_copy(const double *reg, const DevBlock *blocks, const CbCopy *list, int n, double *cb, int ncb,
+                           cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  cb_copy_kernel<<<(n + 255) / 256, 256, 0, st>>>(reg, blocks, list, n, cb, ncb);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_prolong(double *reg, const DevBlock *blocks, const ProlongRef *list, int n, const int32_t *idx,
+                           const double *cb, int ncb, const double *pw, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const long long tot = (long long)n * NF;
+  prolong_kernel<<<(unsigned)((tot + 127) / 128), 128, 0, st>>>(reg, blocks, list, n, idx, cb, ncb, pw);
+  return cudaGetLastError();
+}
+
+}  // namespace z4c

@@ -1,0 +1,118 @@
+// Mesh-refinement ghost transfer kernels (paper Sec. 3.1): restriction by
+// 5-point Lagrange interpolation per axis (3D tensor product) over fine
+// active cells, and prolongation by 5-point Lagrange interpolation per axis
+// from a coarse buffer.  Both are evaluated separably (x, then y, then z).
+// One thread per (list entry, field).  FP64 registers.  Launchers in z4c_smr.cu.
+#pragma once
+
+#include "z4c_internal.cuh"
+
+namespace z4c {
+
+__global__ void restrict_kernel(double *__restrict__ reg, const DevBlock *__restrict__ blocks,
+                                const RestrictRef *__restrict__ list, int n, const double *__restrict__ wtab,
+                                int to_buffer, double *__restrict__ cb, int ncb) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * NF) return;
+  const int e = t / NF, f = t % NF;
+  const RestrictRef r = list[e];
+  const DevBlock &F = blocks[r.src];
+  const int e0 = F.e[0], e01 = F.e[0] * F.e[1];
+  const double *src = reg + F.off + (int64_t)f * F.S + r.s;
+  const double *wx = wtab + 5 * r.wp[0], *wy = wtab + 5 * r.wp[1], *wz = wtab + 5 * r.wp[2];
+  double v = 0.0;
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    double vy = 0.0;
+#pragma unroll
+    for (int b = 0; b < 5; ++b) {
+      const double *row = src + c * e01 + b * e0;
+      double vx = 0.0;
+#pragma unroll
+      for (int a = 0; a < 5; ++a) vx = fma(wx[a], __ldg(row + a), vx);
+      vy = fma(wy[b], vx, vy);
+    }
+    v = fma(wz[c], vy, v);
+  }
+  if (to_buffer) {
+    cb[(int64_t)f * ncb + r.didx] = v;
+  } else {
+    const DevBlock &D = blocks[r.dst];
+    reg[D.off + (int64_t)f * D.S + r.didx] = v;
+  }
+}
+
+__global__ void cb_copy_kernel(const double *__restrict__ reg, const DevBlock *__restrict__ blocks,
+                               const CbCopy *__restrict__ list, int n, double *__restrict__ cb, int ncb) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const CbCopy c = list[t];
+  const DevBlock &S = blocks[c.src];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) cb[(int64_t)f * ncb + c.slot] = reg[S.off + (int64_t)f * S.S + c.scidx];
+}
+
+// pw[(5 * c + a)]: weight of the a-th of the 5 coarse points for child c
+// (0: offset -1/4, 1: +1/4) with stencil shift code s (shift + 2) at
+// pw + 10 * s
+__global__ void prolong_kernel(double *__restrict__ reg, const DevBlock *__restrict__ blocks,
+                               const ProlongRef *__restrict__ list, int n, const int32_t *__restrict__ idx,
+                               const double *__restrict__ cb, int ncb, const double *__restrict__ pw) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * NF) return;
+  const int e = t / NF, f = t % NF;
+  const ProlongRef p = list[e];
+  const int32_t *ix = idx + p.base;
+  const double *cf = cb + (int64_t)f * ncb;
+  double wx[2][5], wy[2][5], wz[2][5];
+  {
+    const double *px = pw + 10 * ((p.mask >> PROLONG_SHIFT_BIT) & 7);
+    const double *py = pw + 10 * ((p.mask >> (PROLONG_SHIFT_BIT + 3)) & 7);
+    const double *pz = pw + 10 * ((p.mask >> (PROLONG_SHIFT_BIT + 6)) & 7);
+#pragma unroll
+    for (int q = 0; q < 10; ++q) {
+      wx[q / 5][q % 5] = px[q];
+      wy[q / 5][q % 5] = py[q];
+      wz[q / 5][q % 5] = pz[q];
+    }
+  }
+  double acc[2][2][2] = {{{0, 0}, {0, 0}}, {{0, 0}, {0, 0}}};  // [z child][y child][x child]
+#pragma unroll
+  for (int c = 0; c < 5; ++c) {
+    double ry[2][2] = {{0, 0}, {0, 0}};  // [y child][x child]
+#pragma unroll
+    for (int b = 0; b < 5; ++b) {
+      double rx[2] = {0, 0};
+#pragma unroll
+      for (int a = 0; a < 5; ++a) {
+        const double v = __ldg(cf + ix[(c * 5 + b) * 5 + a]);
+        rx[0] = fma(wx[0][a], v, rx[0]);
+        rx[1] = fma(wx[1][a], v, rx[1]);
+      }
+#pragma unroll
+      for (int yc = 0; yc < 2; ++yc) {
+        ry[yc][0] = fma(wy[yc][b], rx[0], ry[yc][0]);
+        ry[yc][1] = fma(wy[yc][b], rx[1], ry[yc][1]);
+      }
+    }
+#pragma unroll
+    for (int zc = 0; zc < 2; ++zc)
+#pragma unroll
+      for (int yc = 0; yc < 2; ++yc) {
+        acc[zc][yc][0] = fma(wz[zc][c], ry[yc][0], acc[zc][yc][0]);
+        acc[zc][yc][1] = fma(wz[zc][c], ry[yc][1], acc[zc][yc][1]);
+      }
+  }
+  const DevBlock &D = blocks[p.dst];
+  double *out = reg + D.off + (int64_t)f * D.S + p.cidx0;
+  const int e0 = D.e[0], e01 = D.e[0] * D.e[1];
+#pragma unroll
+  for (int zc = 0; zc < 2; ++zc)
+#pragma unroll
+    for (int yc = 0; yc < 2; ++yc)
+#pragma unroll
+      for (int xc = 0; xc < 2; ++xc)
+        if (p.mask >> (xc + 2 * yc + 4 * zc) & 1) out[zc * e01 + yc * e0 + xc] = acc[zc][yc][xc];
+}
+
+}  // namespace z4c

@@ -128,14 +128,15 @@ class Z4c:
 
     def __init__(self, n=None, lo=None, h=None, ghosts=None, order=None, dom_lo=None, dom_hi=None,
                  periodic=None, ko_sigma=0.0, kappa1=0.0, kappa2=0.0, eta=2.0, chi_floor=1e-6, lapse=1,
-                 shift=1, precision=64, schedule=0, device="cuda", stream=None, instances=None, **_):
+                 shift=1, precision=64, schedule=0, device="cuda", stream=None, instances=None, level=None,
+                 **_):
         import torch
         self.torch = torch
         if instances is None:
             instances = [dict(n=n, lo=lo, h=h, ghosts=ghosts, order=order, dom_lo=dom_lo, dom_hi=dom_hi,
                               periodic=periodic, ko_sigma=ko_sigma, kappa1=kappa1, kappa2=kappa2, eta=eta,
                               chi_floor=chi_floor, lapse=lapse, shift=shift, precision=precision,
-                              schedule=schedule)]
+                              schedule=schedule, level=level)]
         self.instances = instances
         insts = (z4c_instance * len(instances))()
         self.blocks = []
@@ -153,9 +154,10 @@ class Z4c:
             nn = np.asarray(w["n"]).reshape(-1, 3)
             ll = np.asarray(w["lo"], float).reshape(-1, 3)
             hh = np.broadcast_to(np.asarray(w["h"], float), (len(nn),))
+            lev = np.zeros(len(nn), int) if w.get("level") is None else np.asarray(w["level"]).reshape(-1)
             for b in range(len(nn)):
                 B = z4c_block()
-                B.level, B.instance = 0, i
+                B.level, B.instance = int(lev[b]), i
                 B.n[:] = [int(v) for v in nn[b]]
                 B.lo[:] = [float(v) for v in ll[b]]
                 B.h = float(hh[b])
