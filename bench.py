@@ -389,6 +389,8 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=5)
     ap.add_argument("--no-smr", action="store_true")
     ap.add_argument("--smr-steps", type=int, default=50)
+    ap.add_argument("--smr-only", action="store_true",
+                    help="time only the refined two-puncture workload (prints its object)")
     args = ap.parse_args()
     workload = inputs.workload(args.workload)
 
@@ -406,6 +408,9 @@ def main():
         torch.cuda.set_device(0)
     from paper_2409_10383_gb300 import z4c
 
+    if args.smr_only:
+        print(json.dumps({"smr": measure_smr(z4c, torch, args.smr_steps, args.warmup)}), flush=True)
+        return
     res = {}
     if args.variant in ("fp64", "both"):
         res[64] = measure(z4c, torch, workload, 64, args, ws, local)

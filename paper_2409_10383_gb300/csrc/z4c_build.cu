@@ -426,6 +426,15 @@ int z4c_create_batch(const z4c_instance *instances, int ninstances, const z4c_bl
     if (r) return bail(r);
   }
   ctx->reg_elems = (size_t)off;
+  // prolongation slots transposed to [125][entries] so that the threads of a
+  // warp (neighbouring entries) read consecutive words
+  {
+    const size_t ne = ctx->prol.size();
+    std::vector<int32_t> tr(ctx->pidx.size());
+    for (size_t e = 0; e < ne; ++e)
+      for (size_t q = 0; q < 125; ++q) tr[q * ne + e] = ctx->pidx[e * 125 + q];
+    ctx->pidx.swap(tr);
+  }
 
   // scratch layout
   size_t o = 0;

@@ -47,7 +47,7 @@ struct z4c_ctx {
   std::vector<z4c::RestrictRef> rbuf;    // coarse-buffer slots <- restriction of a same-level block
   std::vector<z4c::CbCopy> cbcopy;       // coarse-buffer slots <- a coarser block's active cell
   std::vector<z4c::ProlongRef> prol;     // fine ghost cells <- prolongation from the buffer
-  std::vector<int32_t> pidx;             // 125 buffer slots per prolongation entry
+  std::vector<int32_t> pidx;             // buffer slots, [125][prolongation entries] once built
   std::vector<double> wtab;              // restriction weight patterns (5 each)
   double pw[50] = {0};                   // prolongation weights [shift + 2][child][5]
   int ncb = 0;                           // coarse-buffer slots

@@ -76,7 +76,8 @@ struct CbCopy {
 // block dst: child (dx, dy, dz) at cidx0 + dx + dy e0 + dz e0 e1 is written
 // if bit dx + 2 dy + 4 dz of mask is set (children beyond the storage, with
 // an odd ghost width, are not); coarse values from 125 coarse-buffer slots
-// (x fastest) starting at idx[base].  Bits 8 + 3d .. 10 + 3d of mask hold
+// (x fastest): slot q of entry e is idx[q * nentries + e] on the device
+// (base = 125 e in the host list before the transpose).  Bits 8 + 3d .. 10 + 3d of mask hold
 // the stencil shift along axis d plus 2 (0..4): the 5 coarse cells are
 // parent + shift - 2 .. parent + shift + 2, shift != 0 only next to a
 // non-periodic outer boundary.

@@ -2,7 +2,9 @@
 // 5-point Lagrange interpolation per axis (3D tensor product) over fine
 // active cells, and prolongation by 5-point Lagrange interpolation per axis
 // from a coarse buffer.  Both are evaluated separably (x, then y, then z).
-// One thread per (list entry, field).  FP64 registers.  Launchers in z4c_smr.cu.
+// One thread per (list entry, field), entries fastest: the threads of a warp
+// work on neighbouring entries of one field, so their stencils overlap in
+// memory and the loads coalesce.  FP64 registers.  Launchers in z4c_smr.cu.
 #pragma once
 
 #include "z4c_internal.cuh"
@@ -14,7 +16,7 @@ __global__ void restrict_kernel(double *__restrict__ reg, const DevBlock *__rest
                                 int to_buffer, double *__restrict__ cb, int ncb) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n * NF) return;
-  const int e = t / NF, f = t % NF;
+  const int e = t % n, f = t / n;
   const RestrictRef r = list[e];
   const DevBlock &F = blocks[r.src];
   const int e0 = F.e[0], e01 = F.e[0] * F.e[1];
@@ -60,9 +62,9 @@ __global__ void prolong_kernel(double *__restrict__ reg, const DevBlock *__restr
                                const double *__restrict__ cb, int ncb, const double *__restrict__ pw) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n * NF) return;
-  const int e = t / NF, f = t % NF;
+  const int e = t % n, f = t / n;
   const ProlongRef p = list[e];
-  const int32_t *ix = idx + p.base;
+  const int32_t *ix = idx + e;  // slot q of entry e at ix[q * n]
   const double *cf = cb + (int64_t)f * ncb;
   double wx[2][5], wy[2][5], wz[2][5];
   {
@@ -85,7 +87,7 @@ __global__ void prolong_kernel(double *__restrict__ reg, const DevBlock *__restr
       double rx[2] = {0, 0};
 #pragma unroll
       for (int a = 0; a < 5; ++a) {
-        const double v = __ldg(cf + ix[(c * 5 + b) * 5 + a]);
+        const double v = __ldg(cf + __ldg(ix + (int64_t)((c * 5 + b) * 5 + a) * n));
         rx[0] = fma(wx[0][a], v, rx[0]);
         rx[1] = fma(wx[1][a], v, rx[1]);
       }
