@@ -190,8 +190,12 @@ def measure(z4c, torch, workload, prec, args, ws, local):
     dt = workload["cfl"] * float(workload["h"][0])
     g.z4c_set_initial_data(workload["id_kind"], workload["id_par"])
     st = g.stream
-    # pick the kernel variant (schedule, occupancy) on this GPU; U0 unchanged
-    variant = g.z4c_autotune(3)
+    # pick the kernel variant (schedule, occupancy) on this GPU; U0 unchanged.
+    # --no-autotune keeps the built-in default (schedule 2; FP32 occupancy 4),
+    # e.g. for a profiler run whose serialised timings would mislead the tuner
+    variant = (2, 1 if prec == 64 else 4) if args.no_autotune else g.z4c_autotune(3)
+    if args.no_autotune:
+        g.z4c_set_variant(*variant)
 
     def barrier():
         torch.cuda.synchronize()
@@ -389,6 +393,8 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=5)
     ap.add_argument("--no-smr", action="store_true")
     ap.add_argument("--smr-steps", type=int, default=50)
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default kernel variant instead of timing the candidates")
     ap.add_argument("--smr-only", action="store_true",
                     help="time only the refined two-puncture workload (prints its object)")
     args = ap.parse_args()
