@@ -96,7 +96,13 @@ typedef struct z4c_block {
  *                 storing the y/z first derivatives of chi, gt, alpha, beta
  *                 (in scratch) followed by the fused kernel, which then forms
  *                 mixed second derivatives as one stencil on the stored
- *                 values (fewer operations, fewer registers); default 2 */
+ *                 values (fewer operations, fewer registers); default 2;
+ *                 3 (FP32-RHS only) as 2, but the fused kernel stages each
+ *                 field's stencil rows in shared memory with bulk
+ *                 asynchronous copies (TMA) for blocks that allow 16-byte
+ *                 aligned rows (order 6, 4 ghosts, n_x % 16 == 0,
+ *                 n_y % 8 == 0), schedule 2 for the others; FP64 instances
+ *                 given 3 use 2 */
 typedef struct z4c_params {
   double ko_sigma;
   double kappa1;
@@ -220,7 +226,10 @@ int z4c_set_state(z4c_ctx *ctx, int reg, const void *host, size_t bytes);
 int z4c_evolve_host(z4c_ctx *ctx, const void *host_in, void *host_out, size_t bytes, double dt,
                     int nsteps);
 
-/* Wait for the stream; reports any CUDA error. */
+/* Wait for the stream; reports any CUDA error, and Z4C_ERR_TIMEOUT if a
+ * kernel's bounded wait on its own bulk copies gave up since the last
+ * report (that launch's results are then invalid).  z4c_get_state,
+ * z4c_evolve_host, z4c_profile_steps and z4c_autotune report it too. */
 int z4c_sync(z4c_ctx *ctx);
 
 /* Measurement aid: run nsteps RK4 steps with plain (not graph) launches,
@@ -231,15 +240,18 @@ int z4c_sync(z4c_ctx *ctx);
  * Advances U0 exactly like z4c_rk4_step.  Synchronous. */
 int z4c_profile_steps(z4c_ctx *ctx, double dt, int nsteps, double *ms);
 
-/* Select a kernel variant explicitly: schedule 1 or 2 (see z4c_params) and
- * occupancy, the resident CTAs per SM the fused kernel's registers are
- * budgeted for: 1 always; 2 or 4 for the FP32-RHS schedule-2 kernel.  Other
- * combinations return Z4C_ERR_UNSUPPORTED.  Makes no CUDA call. */
+/* Select a kernel variant explicitly: schedule 1, 2 or 3 (see z4c_params;
+ * 3 applies to FP32-RHS blocks, FP64 blocks then use 2) and occupancy, the
+ * resident CTAs per SM the pre-pass-schedule fused kernel's registers are
+ * budgeted for: 1 always; 2 or 4 for the FP32-RHS kernel (with schedule 3:
+ * for the blocks that do not qualify for staging).  Other combinations
+ * return Z4C_ERR_UNSUPPORTED.  Makes no CUDA call. */
 int z4c_set_variant(z4c_ctx *ctx, int schedule, int occupancy);
 
 /* Pick the fastest kernel variant for this context on this GPU: the
- * schedule (1 or 2, see z4c_params) and, for the FP32-RHS fused kernel, the
- * number of resident CTAs per SM its registers are budgeted for (1, 2, 4).
+ * schedule (1 or 2, and 3 for FP32-RHS blocks that qualify, see z4c_params)
+ * and, for the FP32-RHS fused kernel, the number of resident CTAs per SM its
+ * registers are budgeted for (1, 2, 4).
  * Each candidate runs reps + 1 times the ghost fill and stage 1 of RK4 (which
  * reads U0 and overwrites only the accumulator and stage A, so U0 keeps its
  * value); the fastest is kept, FP64 and FP32-RHS kernels tuned separately.

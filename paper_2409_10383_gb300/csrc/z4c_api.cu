@@ -53,6 +53,18 @@ int fill_ghosts(z4c_ctx *ctx, double *reg, float *sh) {
   return Z4C_OK;
 }
 
+// A kernel whose bounded device-side wait gave up has set the status word:
+// report it (once) after the stream has drained.
+int status_check(z4c_ctx *ctx) {
+  int32_t st = 0;
+  CK(cudaMemcpyAsync(&st, ctx->d_status(), sizeof(st), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (st == 0) return Z4C_OK;
+  CK(cudaMemsetAsync(ctx->d_status(), 0, sizeof(int32_t), ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return fail(ctx, Z4C_ERR_TIMEOUT, "a bulk-copy wait in the staged FP32 kernel gave up; results of that launch are invalid");
+}
+
 StageArgs group_args(const z4c_ctx *ctx, StageArgs a, bool f32) {
   if (!f32) {
     a.x32 = nullptr;
@@ -65,7 +77,7 @@ StageArgs group_args(const z4c_ctx *ctx, StageArgs a, bool f32) {
 int launch_prepass_group(z4c_ctx *ctx, int g, const StageArgs &a) {
   const Group &G = ctx->grp[g];
   const int p = G.f32 ? 1 : 0;
-  if (G.empty() || ctx->sched[p] != 2) return Z4C_OK;
+  if (G.empty() || ctx->sched[p] < 2) return Z4C_OK;
   const int nw = (int)G.wtiles.size();
   CK(G.f32 ? launch_prepass_f32(G.order, a, ctx->d_wtiles(g), nw, ctx->stream)
            : launch_prepass_f64(G.order, a, ctx->d_wtiles(g), nw, ctx->stream));
@@ -75,16 +87,25 @@ int launch_prepass_group(z4c_ctx *ctx, int g, const StageArgs &a) {
 int launch_fused_group(z4c_ctx *ctx, int g, const StageArgs &a) {
   const Group &G = ctx->grp[g];
   if (G.empty()) return Z4C_OK;
-  const int p = G.f32 ? 1 : 0, nt = (int)G.tiles.size();
-  const bool pre = ctx->sched[p] == 2;
+  const int p = G.f32 ? 1 : 0;
+  const bool pre = ctx->sched[p] >= 2;
+  const Tile *tl = ctx->d_tiles(g);
+  int nt = (int)G.tiles.size();
+  if (G.f32 && ctx->sched[1] == 3 && !G.stiles.empty()) {
+    // staged kernel on the qualifying blocks, the pre-pass schedule on the rest
+    CK(launch_staged_f32(G.order, a, ctx->d_stiles(g), (int)G.stiles.size(), ctx->stream));
+    tl = ctx->d_rtiles(g);
+    nt = (int)G.rtiles.size();
+    if (!nt) return Z4C_OK;
+  }
   if (!G.f32)
-    CK(launch_fused_f64(G.order, a, ctx->d_tiles(g), nt, pre, ctx->stream));
+    CK(launch_fused_f64(G.order, a, tl, nt, pre, ctx->stream));
   else if (pre && ctx->occ[1] == 4)
-    CK(launch_fused_pre_f32_occ4(G.order, a, ctx->d_tiles(g), nt, ctx->stream));
+    CK(launch_fused_pre_f32_occ4(G.order, a, tl, nt, ctx->stream));
   else if (pre && ctx->occ[1] == 2)
-    CK(launch_fused_pre_f32_occ2(G.order, a, ctx->d_tiles(g), nt, ctx->stream));
+    CK(launch_fused_pre_f32_occ2(G.order, a, tl, nt, ctx->stream));
   else
-    CK(launch_fused_f32(G.order, a, ctx->d_tiles(g), nt, pre, ctx->stream));
+    CK(launch_fused_f32(G.order, a, tl, nt, pre, ctx->stream));
   return Z4C_OK;
 }
 
@@ -127,6 +148,7 @@ StageArgs stage_args(z4c_ctx *ctx, int s) {
   a.fa = FA[s];
   a.fb = FB[s];
   a.mode = MODES[s];
+  a.status = ctx->d_status();
   if (ctx->has[1]) {
     a.x32 = ctx->d_sh(s % 2);
     a.next32 = ctx->d_sh((s + 1) % 2);
@@ -305,7 +327,7 @@ int z4c_get_state(z4c_ctx *ctx, int reg, void *host, size_t bytes) {
     return fail(ctx, Z4C_ERR_BAD_ARG, "bad register, pointer or size");
   CK(cudaMemcpyAsync(host, ctx->reg[reg], bytes, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
-  return Z4C_OK;
+  return status_check(ctx);
 }
 
 int z4c_set_state(z4c_ctx *ctx, int reg, const void *host, size_t bytes) {
@@ -331,7 +353,7 @@ int z4c_evolve_host(z4c_ctx *ctx, const void *host_in, void *host_out, size_t by
   if (r) return r;
   CK(cudaMemcpyAsync(host_out, ctx->reg[0], bytes, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
-  return Z4C_OK;
+  return status_check(ctx);
 }
 
 int z4c_sync(z4c_ctx *ctx) {
@@ -339,7 +361,7 @@ int z4c_sync(z4c_ctx *ctx) {
   if (r) return r;
   CK(cudaStreamSynchronize(ctx->stream));
   CK(cudaGetLastError());
-  return Z4C_OK;
+  return status_check(ctx);
 }
 
 int z4c_profile_steps(z4c_ctx *ctx, double dt, int nsteps, double *ms) {
@@ -404,15 +426,17 @@ int z4c_profile_steps(z4c_ctx *ctx, double dt, int nsteps, double *ms) {
   cudaEventDestroy(ev[0]);
   cudaEventDestroy(ev[1]);
   for (int q = 0; q < 4; ++q) ms[q] = acc[q] / nsteps;
-  return Z4C_OK;
+  return status_check(ctx);
 }
 
 int z4c_set_variant(z4c_ctx *ctx, int schedule, int occupancy) {
   if (!ctx) return Z4C_ERR_BAD_ARG;
-  if (schedule != 1 && schedule != 2) return fail(ctx, Z4C_ERR_BAD_ARG, "schedule must be 1 or 2");
-  const bool ok = occupancy == 1 || (ctx->has[1] && schedule == 2 && (occupancy == 2 || occupancy == 4));
+  if (schedule < 1 || schedule > 3) return fail(ctx, Z4C_ERR_BAD_ARG, "schedule must be 1, 2 or 3");
+  const bool ok = (schedule == 3 ? ctx->has[1] : true) &&
+                  (occupancy == 1 || (ctx->has[1] && schedule >= 2 && (occupancy == 2 || occupancy == 4)));
   if (!ok) return fail(ctx, Z4C_ERR_UNSUPPORTED, "no kernel built for this schedule/occupancy");
-  ctx->sched[0] = ctx->sched[1] = schedule;
+  ctx->sched[0] = schedule == 3 ? 2 : schedule;  // schedule 3 is FP32-only
+  ctx->sched[1] = schedule;
   ctx->occ[1] = occupancy;
   ctx->drop_graph();
   return Z4C_OK;
@@ -440,6 +464,7 @@ int z4c_autotune(z4c_ctx *ctx, int reps, int *schedule_out, int *occupancy_out) 
     if (p == 1) {
       cands.push_back({2, 2});
       cands.push_back({2, 4});
+      if (ctx->has_staged()) cands.push_back({3, 4});
     }
     float best = 1e30f;
     Cand pick = {ctx->sched[p], p == 1 ? ctx->occ[1] : 1};
@@ -467,6 +492,8 @@ int z4c_autotune(z4c_ctx *ctx, int reps, int *schedule_out, int *occupancy_out) 
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  r = status_check(ctx);
+  if (r) return r;
   ctx->drop_graph();  // the next z4c_rk4_step captures the chosen kernels
   const int p = ctx->has[1] ? 1 : 0;
   if (schedule_out) *schedule_out = ctx->sched[p];
@@ -487,8 +514,14 @@ int z4c_launches_per_step(const z4c_ctx *ctx) {
   for (int p = 0; p < 2; ++p) per_stage += (ctx->gcopy[p].empty() ? 0 : 1) + (ctx->somm[p].empty() ? 0 : 1);
   per_stage += (ctx->rghost.empty() ? 0 : 1) + (ctx->cbcopy.empty() ? 0 : 1) + (ctx->rbuf.empty() ? 0 : 1) +
                (ctx->prol.empty() ? 0 : 1);
-  for (const Group &G : ctx->grp)
-    if (!G.empty()) per_stage += ctx->sched[G.f32 ? 1 : 0] == 2 ? 2 : 1;
+  for (const Group &G : ctx->grp) {
+    if (G.empty()) continue;
+    const int sc = ctx->sched[G.f32 ? 1 : 0];
+    if (sc == 3 && G.f32 && !G.stiles.empty())
+      per_stage += 2 + (G.rtiles.empty() ? 0 : 1);
+    else
+      per_stage += sc >= 2 ? 2 : 1;
+  }
   return 4 * per_stage;
 }
 

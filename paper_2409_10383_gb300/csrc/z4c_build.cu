@@ -38,7 +38,7 @@ int check_instance(const z4c_instance &I) {
   if (p.rhs_precision != 64 && p.rhs_precision != 32) return Z4C_ERR_UNSUPPORTED;
   if (p.lapse < 0 || p.lapse > 1 || p.shift < 0 || p.shift > 1) return Z4C_ERR_BAD_ARG;
   if (!(p.chi_floor > 0.0)) return Z4C_ERR_BAD_ARG;
-  if (p.schedule < 0 || p.schedule > 2) return Z4C_ERR_BAD_ARG;
+  if (p.schedule < 0 || p.schedule > 3) return Z4C_ERR_BAD_ARG;
   for (int d = 0; d < 3; ++d)
     if (!(I.mesh.hi[d] > I.mesh.lo[d])) return Z4C_ERR_BAD_MESH;
   return Z4C_OK;
@@ -360,7 +360,7 @@ int z4c_create_batch(const z4c_instance *instances, int ninstances, const z4c_bl
     const int p = f32 ? 1 : 0;
     ctx->has[p] = true;
     if (!sched_set[p]) {
-      ctx->sched[p] = I.params.schedule == 1 ? 1 : 2;
+      ctx->sched[p] = I.params.schedule == 1 ? 1 : (I.params.schedule == 3 && f32) ? 3 : 2;
       sched_set[p] = true;
     }
     const int g = I.ghosts, ord = I.fd_order;
@@ -411,11 +411,16 @@ int z4c_create_batch(const z4c_instance *instances, int ninstances, const z4c_bl
       D.f32 = f32 ? 1 : 0;
       ctx->dblocks.push_back(D);
       ctx->dt_host.push_back(0.0);
+      // the staged FP32 kernel copies 24-float rows from x = i0 with 16-byte
+      // aligned bulk copies and assumes full tiles
+      const bool staged = f32 && ord == 6 && g == 4 && n[0] % TX == 0 && n[1] % TY == 0 && e[0] % 4 == 0 &&
+                          D.off % 4 == 0;
       for (int k = 0; k < n[2]; ++k) {
         for (int j0 = 0; j0 < n[1]; j0 += TY)
           for (int i0 = 0; i0 < n[0]; i0 += TX) {
             G.tiles.push_back(Tile{b, i0, j0, k});
             ctx->ctiles.push_back(Tile{b, i0, j0, k});
+            if (f32 && ord == 6) (staged ? G.stiles : G.rtiles).push_back(Tile{b, i0, j0, k});
           }
         for (int j0 = -W; j0 < n[1] + W; j0 += TY)
           for (int i0 = -W; i0 < n[0] + W; i0 += TX) G.wtiles.push_back(Tile{b, i0, j0, k});
@@ -447,6 +452,8 @@ int z4c_create_batch(const z4c_instance *instances, int ninstances, const z4c_bl
   for (Group &G : ctx->grp) {
     G.o_tiles = take(sizeof(Tile) * G.tiles.size());
     G.o_wtiles = take(sizeof(Tile) * G.wtiles.size());
+    G.o_stiles = take(sizeof(Tile) * G.stiles.size());
+    G.o_rtiles = take(sizeof(Tile) * G.rtiles.size());
   }
   for (int p = 0; p < 2; ++p) {
     ctx->o_somm[p] = take(sizeof(CellRef) * ctx->somm[p].size());
@@ -470,6 +477,7 @@ int z4c_create_batch(const z4c_instance *instances, int ninstances, const z4c_bl
     ctx->o_ds32 = take(sizeof(float) * ctx->reg_elems);
   }
   if (ctx->has[0]) ctx->o_ds64 = take(sizeof(double) * ctx->reg_elems);
+  ctx->o_status = take(sizeof(int32_t));
   ctx->scratch_total = o;
   *out = ctx;
   return Z4C_OK;
@@ -523,6 +531,8 @@ int z4c_bind(z4c_ctx *ctx, void *u0, void *stage_a, void *stage_b, void *acc, vo
   for (const Group &G : ctx->grp) {
     CK(up(G.o_tiles, G.tiles.data(), sizeof(Tile) * G.tiles.size()));
     CK(up(G.o_wtiles, G.wtiles.data(), sizeof(Tile) * G.wtiles.size()));
+    CK(up(G.o_stiles, G.stiles.data(), sizeof(Tile) * G.stiles.size()));
+    CK(up(G.o_rtiles, G.rtiles.data(), sizeof(Tile) * G.rtiles.size()));
   }
   for (int p = 0; p < 2; ++p) {
     CK(up(ctx->o_somm[p], ctx->somm[p].data(), sizeof(CellRef) * ctx->somm[p].size()));
@@ -536,6 +546,7 @@ int z4c_bind(z4c_ctx *ctx, void *u0, void *stage_a, void *stage_b, void *acc, vo
   CK(up(ctx->o_wtab, ctx->wtab.data(), sizeof(double) * ctx->wtab.size()));
   CK(up(ctx->o_pw, ctx->pw, sizeof(double) * 50));
   CK(up(ctx->o_ctiles, ctx->ctiles.data(), sizeof(Tile) * ctx->ctiles.size()));
+  CK(cudaMemsetAsync(ctx->d_status(), 0, sizeof(int32_t), st));
   // the tables live in host vectors owned by ctx; wait so the copies are done
   CK(cudaStreamSynchronize(st));
   ctx->bound = true;

@@ -107,6 +107,7 @@ struct StageArgs {
   double fa, fb;      // next = base + fa dt k, acc = acc + fb dt k (classic RK4 weights)
   int32_t mode;
   int32_t next_full;  // FP32 mode: 1 = write every field of next in FP64, 0 = chi only
+  int32_t *status;    // device word; a kernel whose bounded wait gave up ORs in 1
 };
 
 // Interior tile shape of the RHS kernels.
@@ -122,6 +123,10 @@ cudaError_t launch_cb_copy(const double *reg, const DevBlock *blocks, const CbCo
                            int ncb, cudaStream_t st);
 cudaError_t launch_prolong(double *reg, const DevBlock *blocks, const ProlongRef *list, int n,
                            const int32_t *idx, const double *cb, int ncb, const double *pw, cudaStream_t st);
+// FP32 fused kernel with shared-memory staging (schedule 3), for blocks whose
+// rows allow 16-byte aligned bulk copies; the tiles of other blocks use the
+// pre-pass schedule
+cudaError_t launch_staged_f32(int order, const StageArgs &a, const Tile *tiles, int ntiles, cudaStream_t st);
 // FP32 fused pre-pass-schedule kernel built for 2 or 4 resident CTAs per SM
 cudaError_t launch_fused_pre_f32_occ2(int order, const StageArgs &a, const Tile *tiles, int ntiles,
                                       cudaStream_t st);

@@ -209,6 +209,7 @@ struct Phys {
 // stencil each (the tensor-product definition, evaluated in two passes).
 template <int ORD, class R, class SRC>
 struct Direct {
+  static constexpr bool kStagedKO = false;  // KO / advection evaluated from s by ko_adv
   const SRC &s;
   const int *st;
   Scales<R> sc;
@@ -228,6 +229,7 @@ constexpr int NDS = 11;
 
 template <int ORD, class R, class SRC, class DS>
 struct Pre {
+  static constexpr bool kStagedKO = false;
   const SRC &s;
   const DS &ds;  // stored derivatives at this cell (already multiplied by s1)
   const int *st;
@@ -528,17 +530,26 @@ __device__ __forceinline__ void rhs_point(const SRC &s, const DV &dv, const int 
   for (int i = 0; i < 3; ++i) k[BETAX + i] = p.shift ? Gam[i] - p.eta * beta[i] : R(0);
 
   // lopsided advection along the shift and Kreiss-Oliger dissipation
-  bool up[3];
-  R ab[3];
+  if constexpr (DV::kStagedKO) {
+    // already evaluated per field by the staging pass
 #pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    up[d] = beta[d] >= R(0);
-    ab[d] = fabs(beta[d]) * sc.slop;
-  }
+    for (int f = 0; f < NF; ++f) {
+      if (!p.shift && f >= BETAX) continue;
+      k[f] += dv.ko(f);
+    }
+  } else {
+    bool up[3];
+    R ab[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      up[d] = beta[d] >= R(0);
+      ab[d] = fabs(beta[d]) * sc.slop;
+    }
 #pragma unroll 1
-  for (int f = 0; f < NF; ++f) {
-    if (!p.shift && f >= BETAX) continue;
-    k[f] += ko_adv<ORD>(s, f, st, up, ab, sc.sko);
+    for (int f = 0; f < NF; ++f) {
+      if (!p.shift && f >= BETAX) continue;
+      k[f] += ko_adv<ORD>(s, f, st, up, ab, sc.sko);
+    }
   }
 }
 

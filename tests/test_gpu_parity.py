@@ -92,10 +92,11 @@ def test_rhs_parity_fp64(oracle, kind, order, nb, n, per, schedule):
         assert np.all(m.blocks(got)[b][:, ng] == 0)
 
 
-@pytest.mark.parametrize("schedule", [1, 2])
-@pytest.mark.parametrize("precision", [64, 32])
+@pytest.mark.parametrize("precision,schedule", [(64, 1), (64, 2), (32, 1), (32, 2), (32, 3)])
 def test_flat_space_is_exactly_static(oracle, precision, schedule):
-    w = H.small_workload("puncture", 6, (2, 1, 1), 12, id_kind=inputs.ID_FLAT, id_par=[])
+    # 16^3 blocks qualify for the staged FP32 kernel (schedule 3)
+    n = 16 if schedule == 3 else 12
+    w = H.small_workload("puncture", 6, (2, 1, 1), n, id_kind=inputs.ID_FLAT, id_par=[])
     g = H.gpu_ctx(w, precision, schedule)
     g.z4c_set_initial_data(inputs.ID_FLAT, [])
     g.z4c_fill_ghosts(0)
@@ -182,7 +183,7 @@ def _round_like_shadow(m, u):
     return v
 
 
-@pytest.mark.parametrize("schedule,occupancy", [(1, 1), (2, 1), (2, 2), (2, 4)])
+@pytest.mark.parametrize("schedule,occupancy", [(1, 1), (2, 1), (2, 2), (2, 4), (3, 4)])
 def test_fp32_rhs_error_budget(oracle, schedule, occupancy):
     """FP32 stencils and algebra (FP64 state, RK accumulation, 1/chi,
     enforcement).  Bounds, stated against what FP32 storage alone causes:
