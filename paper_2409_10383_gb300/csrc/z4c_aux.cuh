@@ -42,56 +42,56 @@ __global__ void sommerfeld_kernel(StageArgs a, const CellRef *__restrict__ cells
   if (t >= n) return;
   const CellRef c = cells[t];
   const DevBlock &b = a.blocks[c.block];
-  const int e0 = b.e[0], e1 = b.e[1];
-  const int idx[3] = {c.cidx % e0, (c.cidx / e0) % e1, c.cidx / (e0 * e1)};
-  const int st[3] = {1, e0, e0 * e1};
+  const int st[3] = {1, b.e[0], b.e[0] * b.e[1]};
+  const int idx[3] = {c.i, c.j, c.k};
   const int64_t off = b.off + c.cidx;
-  R x[3];
-  double r2 = 0.0;
+  // du/dt = -(x^d d_d u + u - u_inf) / r.  The one-sided (w0, w1, w2) =
+  // (-+3, +-4, -+1) at offsets (0, +-1, +-2) and centred (0, 1, -1) at
+  // (0, +1, -1) differences sum to zero, so 2h d_d u = w1 (u[o1] - u) +
+  // w2 (u[o2] - u).  Per cell: a1,2_d = -w1,2_d x^d / (2h r); per field:
+  // k = -(u - u_inf) / r + sum_d a1_d (u[o1_d] - u) + a2_d (u[o2_d] - u),
+  // which is exactly zero on a constant state equal to u_inf.
+  double xd[3], r2 = 0.0;
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    const double xd = b.lo[d] + (idx[d] - b.g + 0.5) * b.h;
-    x[d] = R(xd);
-    r2 += xd * xd;
+    xd[d] = b.lo[d] + (idx[d] - b.g + 0.5) * b.h;
+    r2 += xd[d] * xd[d];
   }
-  const R ir = R(1.0 / sqrt(r2));
-  const R ih2 = R(0.5 / b.h);
-  R k[NF];
-#pragma unroll 1
-  for (int f = 0; f < NF; ++f) {
-    R xdu = R(0);
+  const double ir = 1.0 / sqrt(r2);
+  R a1[3], a2[3];
+  int o1[3], o2[3];
 #pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      const int s = st[d];
-      R du;
-      if constexpr (F32) {
-        const float *p = a.x32 + off + (int64_t)f * b.S;
-        if (idx[d] < b.g)
-          du = R(-3) * p[0] + R(4) * p[s] - p[2 * s];
-        else if (idx[d] >= b.n[d] + b.g)
-          du = R(3) * p[0] - R(4) * p[-s] + p[-2 * s];
-        else
-          du = p[s] - p[-s];
-      } else {
-        const double *p = a.x64 + off + (int64_t)f * b.S;
-        if (idx[d] < b.g)
-          du = R(-3) * p[0] + R(4) * p[s] - p[2 * s];
-        else if (idx[d] >= b.n[d] + b.g)
-          du = R(3) * p[0] - R(4) * p[-s] + p[-2 * s];
-        else
-          du = p[s] - p[-s];
-      }
-      xdu += x[d] * (du * ih2);
-    }
-    R um;  // u - u_inf
+  for (int d = 0; d < 3; ++d) {
+    const int kind = (c.code >> (2 * d)) & 3;
+    const double q = -ir * xd[d] * (0.5 / b.h);
+    const double w1 = kind == SOMM_FORWARD ? 4.0 : kind == SOMM_BACKWARD ? -4.0 : 1.0;
+    const double w2 = kind == SOMM_FORWARD ? -1.0 : kind == SOMM_BACKWARD ? 1.0 : -1.0;
+    const int s1 = kind == SOMM_BACKWARD ? -1 : 1;
+    const int s2 = kind == SOMM_FORWARD ? 2 : kind == SOMM_BACKWARD ? -2 : -1;
+    a1[d] = R(q * w1);
+    a2[d] = R(q * w2);
+    o1[d] = s1 * st[d];
+    o2[d] = s2 * st[d];
+  }
+  const R mir = R(-ir);
+  R k[NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    // the FP32 shadow stores the gt diagonal minus one, i.e. u - u_inf there
+    const R *p;
+    R um;
     if constexpr (F32) {
-      const bool diag = (f == GXX || f == GYY || f == GZZ);
-      const float v = a.x32[off + (int64_t)f * b.S];
-      um = diag ? v : v - R(uinf_of(f));
+      p = a.x32 + off + (int64_t)f * b.S;
+      um = (f == CHI || f == ALPHA) ? p[0] - R(1) : p[0];
     } else {
-      um = a.x64[off + (int64_t)f * b.S] - uinf_of(f);
+      p = a.x64 + off + (int64_t)f * b.S;
+      um = p[0] - uinf_of(f);
     }
-    k[f] = -(xdu + um) * ir;
+    const R u = p[0];
+    R v = mir * um;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) v = fma(a1[d], p[o1[d]] - u, fma(a2[d], p[o2[d]] - u, v));
+    k[f] = v;
   }
   stage_epilogue<R>(a, c.block, off, b.S, k);
 }

@@ -237,7 +237,12 @@ struct GhostBuilder {
             for (int d = 0; d < 3; ++d) xw[d] = x[d] = blk(lb).lo[d] + (idx[d] - g + 0.5) * h;
             const int cidx = (k * e[1] + j) * e[0] + i;
             if (!inside(xw)) {
-              ctx->somm[p].push_back(CellRef{b, cidx});
+              CellRef c{b, cidx, (int16_t)i, (int16_t)j, (int16_t)k, 0};
+              for (int d = 0; d < 3; ++d) {
+                const int kind = idx[d] < g ? SOMM_FORWARD : idx[d] >= Lo.n[d] + g ? SOMM_BACKWARD : SOMM_CENTRED;
+                c.code |= (uint16_t)(kind << (2 * d));
+              }
+              ctx->somm[p].push_back(c);
               continue;
             }
             const int nb = owner_of(xw);

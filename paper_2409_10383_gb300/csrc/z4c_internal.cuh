@@ -46,10 +46,17 @@ struct Tile {
   int32_t block, i0, j0, k0;  // interior-relative origin
 };
 
-// One storage cell of one block.
+// One Sommerfeld cell (a ghost cell outside the domain) of one block: its
+// storage index and (i, j, k) storage coordinates, and per axis d the
+// difference it takes in bits 2d..2d+1 (SOMM_CENTRED, or one-sided pointing
+// into the block: SOMM_FORWARD for a cell below the interior, SOMM_BACKWARD
+// above it).
 struct CellRef {
   int32_t block, cidx;
+  int16_t i, j, k;
+  uint16_t code;
 };
+enum SommKind { SOMM_CENTRED = 0, SOMM_FORWARD = 1, SOMM_BACKWARD = 2 };
 
 // One same-level ghost copy: dst cell <- src cell, all fields.
 struct GhostCopy {
