@@ -191,9 +191,10 @@ def measure(z4c, torch, workload, prec, args, ws, local):
     g.z4c_set_initial_data(workload["id_kind"], workload["id_par"])
     st = g.stream
     # pick the kernel variant (schedule, occupancy) on this GPU; U0 unchanged.
-    # --no-autotune keeps the built-in default (schedule 2; FP32 occupancy 4),
-    # e.g. for a profiler run whose serialised timings would mislead the tuner
-    variant = (2, 1 if prec == 64 else 4) if args.no_autotune else g.z4c_autotune(3)
+    # --no-autotune keeps the built-in default (FP64 schedule 2; FP32 split
+    # schedule 4), e.g. for a profiler run whose serialised timings would
+    # mislead the tuner
+    variant = ((2, 1) if prec == 64 else (4, 4)) if args.no_autotune else g.z4c_autotune(3)
     if args.no_autotune:
         g.z4c_set_variant(*variant)
 
@@ -244,23 +245,32 @@ def measure(z4c, torch, workload, prec, args, ws, local):
     elif prec == 32 and order in FP32_OPS_PER_CELL_STAGE:
         # the slower of: FP32 flops at the FP32 peak, FP64-residue flops at
         # the FP64 peak, algorithmic bytes at the HBM bandwidth
+        # (the FP64 residue is costed in pipe instructions: a DADD or DMUL
+        # occupies the FP64 pipe as long as a DFMA, whose rate is peak64 / 2)
         o32, o64 = FP32_OPS_PER_CELL_STAGE[order], FP32_F64_RESIDUE_PER_CELL_STAGE[order]
         f32 = (o32["fadd"] + o32["fmul"] + 2 * o32["ffma"]) * cells
         f64 = (o64["dadd"] + o64["dmul"] + 2 * o64["dfma"]) * cells
+        i64 = (o64["dadd"] + o64["dmul"] + o64["dfma"]) * cells
         byt = ALG_BYTES_PER_ZONE_CYCLE / 4 * cells
         hbm = measured_peaks().get("hbm_gbs", 6800.0) * 1e9
-        t = {"fp32_alu": f32 / peak32, "fp64_residue": f64 / peak64, "hbm": byt / hbm}
+        t = {"fp32_alu": f32 / peak32, "fp64_residue": i64 / (peak64 / 2), "hbm": byt / hbm}
         kind = max(t, key=t.get)
         sec = interior_ms * 1e-3
         if kind == "hbm":
             roof = {"bound": "hbm", "achieved": byt / sec / 1e9, "peak": hbm / 1e9, "unit": "GB/s",
                     "peak_source": "MEASURED_PEAKS.json hbm_gbs (measured)"}
+        elif kind == "fp32_alu":
+            roof = {"bound": "alu", "achieved": f32 / sec / 1e12, "peak": peak32 / 1e12, "unit": "TFLOP/s",
+                    "peak_source": "measured FP32 FMA throughput (z4c_peak_fma), FMA = 2 flops"}
         else:
-            w, pk = (f32, peak32) if kind == "fp32_alu" else (f64, peak64)
-            roof = {"bound": "alu", "achieved": w / sec / 1e12, "peak": pk / 1e12, "unit": "TFLOP/s",
-                    "peak_source": "measured FMA throughput (z4c_peak_fma), FMA = 2 flops"}
+            roof = {"bound": "alu", "achieved": i64 / sec / 1e12, "peak": peak64 / 2 / 1e12,
+                    "unit": "T FP64-pipe instructions/s",
+                    "peak_source": "measured DFMA instruction rate (z4c_peak_fma FP64 / 2)",
+                    "fp64_residue_flops_per_cell_stage": f64 / cells}
         roof.update({"frac": t[kind] / sec, "limiter": kind, "traffic": None,
-                     "kernel": f"interior_pre_kernel<{order},true,OCC> (FP32 RHS, FP64 state/RK/enforcement)",
+                     "kernel": (f"interior_pre_kernel<{order},true,4,split> + split_epilogue_kernel (FP32 RHS, "
+                                "FP64 state/RK/enforcement)") if variant[0] == 4 else
+                               f"interior_pre_kernel<{order},true,{variant[1]}> (FP32 RHS, FP64 state/RK/enforcement)",
                      "bound_ms_per_launch": {k: v * 1e3 for k, v in t.items()},
                      "fracs": {k: v / sec for k, v in t.items()}})
     else:

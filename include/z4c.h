@@ -92,7 +92,7 @@ typedef struct z4c_block {
  *   rhs_precision 64: everything FP64; 32: stencils and RHS algebra in FP32,
  *                 state, RK accumulation, 1/chi, constraint enforcement and
  *                 constraint norms in FP64
- *   schedule      0 default, 1 one fused kernel per stage, 2 a pre-pass
+ *   schedule      0 default (below), 1 one fused kernel per stage, 2 a pre-pass
  *                 storing the y/z first derivatives of chi, gt, alpha, beta
  *                 (in scratch) followed by the fused kernel, which then forms
  *                 mixed second derivatives as one stencil on the stored
@@ -101,8 +101,11 @@ typedef struct z4c_block {
  *                 field's stencil rows in shared memory with bulk
  *                 asynchronous copies (TMA) for blocks that allow 16-byte
  *                 aligned rows (order 6, 4 ghosts, n_x % 16 == 0,
- *                 n_y % 8 == 0), schedule 2 for the others; FP64 instances
- *                 given 3 use 2 */
+ *                 n_y % 8 == 0), schedule 2 for the others; 4 (FP32-RHS
+ *                 only) as 2, but the RHS kernel stores k in FP32 and a
+ *                 second kernel applies the RK stage update and the FP64
+ *                 enforcement at high occupancy.  FP64 instances given 3
+ *                 or 4 use 2.  Default (0): 2 for FP64, 4 for FP32-RHS */
 typedef struct z4c_params {
   double ko_sigma;
   double kappa1;
@@ -240,16 +243,18 @@ int z4c_sync(z4c_ctx *ctx);
  * Advances U0 exactly like z4c_rk4_step.  Synchronous. */
 int z4c_profile_steps(z4c_ctx *ctx, double dt, int nsteps, double *ms);
 
-/* Select a kernel variant explicitly: schedule 1, 2 or 3 (see z4c_params;
- * 3 applies to FP32-RHS blocks, FP64 blocks then use 2) and occupancy, the
- * resident CTAs per SM the pre-pass-schedule fused kernel's registers are
- * budgeted for: 1 always; 2 or 4 for the FP32-RHS kernel (with schedule 3:
- * for the blocks that do not qualify for staging).  Other combinations
- * return Z4C_ERR_UNSUPPORTED.  Makes no CUDA call. */
+/* Select a kernel variant explicitly: schedule 1 to 4 (see z4c_params;
+ * 3 and 4 apply to FP32-RHS blocks, FP64 blocks then use 2) and occupancy,
+ * the resident CTAs per SM the pre-pass-schedule fused kernel's registers
+ * are budgeted for: 1 always; 2 or 4 for the FP32-RHS kernel (with schedule
+ * 3: for the blocks that do not qualify for staging); schedule 4 is built
+ * for 4 only.  Other combinations return Z4C_ERR_UNSUPPORTED.  Makes no
+ * CUDA call. */
 int z4c_set_variant(z4c_ctx *ctx, int schedule, int occupancy);
 
 /* Pick the fastest kernel variant for this context on this GPU: the
- * schedule (1 or 2, and 3 for FP32-RHS blocks that qualify, see z4c_params)
+ * schedule (1 or 2; for FP32-RHS blocks also 4, and 3 where blocks qualify;
+ * see z4c_params)
  * and, for the FP32-RHS fused kernel, the number of resident CTAs per SM its
  * registers are budgeted for (1, 2, 4).
  * Each candidate runs reps + 1 times the ghost fill and stage 1 of RK4 (which

@@ -91,6 +91,10 @@ int launch_fused_group(z4c_ctx *ctx, int g, const StageArgs &a) {
   const bool pre = ctx->sched[p] >= 2;
   const Tile *tl = ctx->d_tiles(g);
   int nt = (int)G.tiles.size();
+  if (G.f32 && ctx->sched[1] == 4) {
+    CK(launch_split_f32(G.order, a, tl, nt, ctx->stream));
+    return Z4C_OK;
+  }
   if (G.f32 && ctx->sched[1] == 3 && !G.stiles.empty()) {
     // staged kernel on the qualifying blocks, the pre-pass schedule on the rest
     CK(launch_staged_f32(G.order, a, ctx->d_stiles(g), (int)G.stiles.size(), ctx->stream));
@@ -149,6 +153,7 @@ StageArgs stage_args(z4c_ctx *ctx, int s) {
   a.fb = FB[s];
   a.mode = MODES[s];
   a.status = ctx->d_status();
+  a.kbuf = ctx->d_kbuf();
   if (ctx->has[1]) {
     a.x32 = ctx->d_sh(s % 2);
     a.next32 = ctx->d_sh((s + 1) % 2);
@@ -241,6 +246,8 @@ int z4c_rhs(z4c_ctx *ctx, int reg, void *rhs_out) {
   a.x64 = ctx->reg[reg];
   a.rhs_out = (double *)rhs_out;
   a.mode = MODE_RHS;
+  a.status = ctx->d_status();
+  a.kbuf = ctx->d_kbuf();
   if (ctx->has[1]) {
     // shadow of the register in the second shadow buffer (the first may hold U0's)
     CK(launch_to_shadow(ctx->reg[reg], ctx->d_sh(1), ctx->d_blocks(), (int)ctx->dblocks.size(), ctx->max_S,
@@ -431,11 +438,12 @@ int z4c_profile_steps(z4c_ctx *ctx, double dt, int nsteps, double *ms) {
 
 int z4c_set_variant(z4c_ctx *ctx, int schedule, int occupancy) {
   if (!ctx) return Z4C_ERR_BAD_ARG;
-  if (schedule < 1 || schedule > 3) return fail(ctx, Z4C_ERR_BAD_ARG, "schedule must be 1, 2 or 3");
-  const bool ok = (schedule == 3 ? ctx->has[1] : true) &&
-                  (occupancy == 1 || (ctx->has[1] && schedule >= 2 && (occupancy == 2 || occupancy == 4)));
+  if (schedule < 1 || schedule > 4) return fail(ctx, Z4C_ERR_BAD_ARG, "schedule must be 1 to 4");
+  const bool ok = (schedule >= 3 ? ctx->has[1] : true) &&
+                  (schedule == 4 ? occupancy == 4
+                                 : occupancy == 1 || (ctx->has[1] && schedule >= 2 && (occupancy == 2 || occupancy == 4)));
   if (!ok) return fail(ctx, Z4C_ERR_UNSUPPORTED, "no kernel built for this schedule/occupancy");
-  ctx->sched[0] = schedule == 3 ? 2 : schedule;  // schedule 3 is FP32-only
+  ctx->sched[0] = schedule >= 3 ? 2 : schedule;  // schedules 3 and 4 are FP32-only
   ctx->sched[1] = schedule;
   ctx->occ[1] = occupancy;
   ctx->drop_graph();
@@ -465,6 +473,7 @@ int z4c_autotune(z4c_ctx *ctx, int reps, int *schedule_out, int *occupancy_out) 
       cands.push_back({2, 2});
       cands.push_back({2, 4});
       if (ctx->has_staged()) cands.push_back({3, 4});
+      cands.push_back({4, 4});
     }
     float best = 1e30f;
     Cand pick = {ctx->sched[p], p == 1 ? ctx->occ[1] : 1};
@@ -519,6 +528,8 @@ int z4c_launches_per_step(const z4c_ctx *ctx) {
     const int sc = ctx->sched[G.f32 ? 1 : 0];
     if (sc == 3 && G.f32 && !G.stiles.empty())
       per_stage += 2 + (G.rtiles.empty() ? 0 : 1);
+    else if (sc == 4 && G.f32)
+      per_stage += 3;
     else
       per_stage += sc >= 2 ? 2 : 1;
   }

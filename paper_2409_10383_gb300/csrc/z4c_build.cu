@@ -38,7 +38,7 @@ int check_instance(const z4c_instance &I) {
   if (p.rhs_precision != 64 && p.rhs_precision != 32) return Z4C_ERR_UNSUPPORTED;
   if (p.lapse < 0 || p.lapse > 1 || p.shift < 0 || p.shift > 1) return Z4C_ERR_BAD_ARG;
   if (!(p.chi_floor > 0.0)) return Z4C_ERR_BAD_ARG;
-  if (p.schedule < 0 || p.schedule > 3) return Z4C_ERR_BAD_ARG;
+  if (p.schedule < 0 || p.schedule > 4) return Z4C_ERR_BAD_ARG;
   for (int d = 0; d < 3; ++d)
     if (!(I.mesh.hi[d] > I.mesh.lo[d])) return Z4C_ERR_BAD_MESH;
   return Z4C_OK;
@@ -365,7 +365,9 @@ int z4c_create_batch(const z4c_instance *instances, int ninstances, const z4c_bl
     const int p = f32 ? 1 : 0;
     ctx->has[p] = true;
     if (!sched_set[p]) {
-      ctx->sched[p] = I.params.schedule == 1 ? 1 : (I.params.schedule == 3 && f32) ? 3 : 2;
+      // default (0): FP64 pre-pass + fused kernel; FP32-RHS split schedule 4
+      const int sc = I.params.schedule;
+      ctx->sched[p] = sc == 1 ? 1 : sc == 2 ? 2 : !f32 ? 2 : sc == 0 ? 4 : sc;
       sched_set[p] = true;
     }
     const int g = I.ghosts, ord = I.fd_order;
@@ -483,6 +485,12 @@ int z4c_create_batch(const z4c_instance *instances, int ninstances, const z4c_bl
   }
   if (ctx->has[0]) ctx->o_ds64 = take(sizeof(double) * ctx->reg_elems);
   ctx->o_status = take(sizeof(int32_t));
+  {  // schedule 4: the FP32 RHS of the largest FP32 group's tiles
+    size_t nt = 0;
+    for (const Group &G : ctx->grp)
+      if (G.f32) nt = std::max(nt, G.tiles.size());
+    ctx->o_kbuf = take(sizeof(float) * NF * TX * TY * nt);
+  }
   ctx->scratch_total = o;
   *out = ctx;
   return Z4C_OK;

@@ -61,7 +61,7 @@ struct z4c_ctx {
   // scratch layout (byte offsets)
   size_t o_blocks = 0, o_somm[2] = {0, 0}, o_gcopy[2] = {0, 0}, o_ctiles = 0, o_part = 0, o_res = 0,
          o_dt = 0, o_sh0 = 0, o_sh1 = 0, o_ds64 = 0, o_ds32 = 0, o_rghost = 0, o_rbuf = 0, o_cbcopy = 0,
-         o_prol = 0, o_pidx = 0, o_wtab = 0, o_pw = 0, o_cb = 0, o_status = 0, scratch_total = 0;
+         o_prol = 0, o_pidx = 0, o_wtab = 0, o_pw = 0, o_cb = 0, o_status = 0, o_kbuf = 0, scratch_total = 0;
   // bound buffers
   double *reg[4] = {nullptr, nullptr, nullptr, nullptr};
   char *scratch = nullptr;
@@ -71,8 +71,9 @@ struct z4c_ctx {
   bool dt_dirty = true;
   // kernel variant per precision: schedule (1 one kernel, 2 pre-pass + fused,
   // 3 FP32 only: pre-pass + shared-memory staged kernel where the block
-  // qualifies) and occupancy (resident CTAs per SM the pre-pass-schedule
-  // FP32 kernel is built for)
+  // qualifies, 4 FP32 only: pre-pass + RHS kernel storing k + stage-update
+  // kernel) and occupancy (resident CTAs per SM the pre-pass-schedule FP32
+  // kernel is built for)
   int sched[2] = {2, 2}, occ[2] = {1, 4};
   // graph of one RK4 step
   cudaGraphExec_t graph = nullptr;
@@ -84,6 +85,7 @@ struct z4c_ctx {
   const z4c::Tile *d_stiles(int g) const { return (const z4c::Tile *)(scratch + grp[g].o_stiles); }
   const z4c::Tile *d_rtiles(int g) const { return (const z4c::Tile *)(scratch + grp[g].o_rtiles); }
   int32_t *d_status() const { return (int32_t *)(scratch + o_status); }
+  float *d_kbuf() const { return (float *)(scratch + o_kbuf); }
   bool has_staged() const { return !grp[3].stiles.empty(); }
   const z4c::CellRef *d_somm(int p) const { return (const z4c::CellRef *)(scratch + o_somm[p]); }
   const z4c::GhostCopy *d_gcopy(int p) const { return (const z4c::GhostCopy *)(scratch + o_gcopy[p]); }

@@ -92,7 +92,9 @@ __global__ void __launch_bounds__(TX * TY) dydz_kernel(StageArgs a, const Tile *
 // second derivatives of the eleven fields from the pre-pass arrays.
 // OCC = minimum resident CTAs per SM the register allocation must allow
 // (1: up to 255 registers per thread; 4: 128), chosen by the autotuner.
-template <int ORD, bool F32, int OCC>
+// SPLIT (FP32 only): store k in a.kbuf for split_epilogue_kernel instead of
+// applying the stage update here.
+template <int ORD, bool F32, int OCC, bool SPLIT = false>
 __global__ void __launch_bounds__(TX * TY, OCC) interior_pre_kernel(StageArgs a, const Tile *__restrict__ tiles) {
   using R = typename std::conditional<F32, float, double>::type;
   const Tile t = tiles[blockIdx.x];
@@ -117,6 +119,12 @@ __global__ void __launch_bounds__(TX * TY, OCC) interior_pre_kernel(StageArgs a,
     const Scales<float> sc = scales_of(b, 0.0f);
     const Pre<ORD, float, Src<float, true>, Src<float, false>> dv{s, ds, st, sc};
     rhs_point<ORD, float>(s, dv, st, sc, p, ichi, k);
+    if constexpr (SPLIT) {
+      float *kt = a.kbuf + (int64_t)blockIdx.x * NF * (TX * TY) + threadIdx.y * TX + threadIdx.x;
+#pragma unroll
+      for (int f = 0; f < NF; ++f) kt[f * (TX * TY)] = k[f];
+      return;
+    }
   } else {
     const Src<double, false> s{a.x64 + b.off, cidx, b.S};
     const Scales<double> sc = scales_of(b, 0.0);

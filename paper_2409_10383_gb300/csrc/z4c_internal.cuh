@@ -115,6 +115,7 @@ struct StageArgs {
   int32_t mode;
   int32_t next_full;  // FP32 mode: 1 = write every field of next in FP64, 0 = chi only
   int32_t *status;    // device word; a kernel whose bounded wait gave up ORs in 1
+  float *kbuf;        // schedule 4: the FP32 RHS per tile, [tile][field][TX * TY]
 };
 
 // Interior tile shape of the RHS kernels.
@@ -134,6 +135,10 @@ cudaError_t launch_prolong(double *reg, const DevBlock *blocks, const ProlongRef
 // rows allow 16-byte aligned bulk copies; the tiles of other blocks use the
 // pre-pass schedule
 cudaError_t launch_staged_f32(int order, const StageArgs &a, const Tile *tiles, int ntiles, cudaStream_t st);
+// FP32 split schedule (4): the pre-pass-schedule RHS kernel stores k (FP32)
+// per tile in a.kbuf, then an epilogue kernel applies the RK stage update and
+// the FP64 enforcement at high occupancy
+cudaError_t launch_split_f32(int order, const StageArgs &a, const Tile *tiles, int ntiles, cudaStream_t st);
 // FP32 fused pre-pass-schedule kernel built for 2 or 4 resident CTAs per SM
 cudaError_t launch_fused_pre_f32_occ2(int order, const StageArgs &a, const Tile *tiles, int ntiles,
                                       cudaStream_t st);

@@ -80,13 +80,14 @@ def test_sizes_and_unbound_calls(L):
     assert sc.value >= 2 * 22 * 38 ** 3 * 4  # two FP32 shadows
     assert L.z4c_rk4_step(ctx, 0.01, 1) == z4c.Z4C_ERR_NOT_BOUND
     assert b"z4c_bind" in L.z4c_last_error(ctx)
-    # periodic, default schedule: ghost fill + pre-pass + fused interior per stage
-    assert L.z4c_launches_per_step(ctx) == 12
+    # periodic FP32-RHS, default split schedule: ghost fill + pre-pass + RHS
+    # kernel + stage-update kernel per stage
+    assert L.z4c_launches_per_step(ctx) == 16
     L.z4c_destroy(ctx)
     rc, ctx = z4c.z4c_create(_mesh(), [_block()], 3, 4, _params(64, schedule=1))
     assert rc == 0 and L.z4c_launches_per_step(ctx) == 8  # single fused kernel
     L.z4c_destroy(ctx)
-    assert z4c.z4c_create(_mesh(), [_block()], 3, 4, _params(64, schedule=4))[0] == z4c.Z4C_ERR_BAD_ARG
+    assert z4c.z4c_create(_mesh(), [_block()], 3, 4, _params(64, schedule=5))[0] == z4c.Z4C_ERR_BAD_ARG
     rc, ctx = z4c.z4c_create(_mesh(), [_block()], 3, 4, _params(64))
     assert L.z4c_set_variant(ctx, 2, 4) == z4c.Z4C_ERR_UNSUPPORTED  # FP64 has one occupancy
     assert L.z4c_set_variant(ctx, 3, 1) == z4c.Z4C_ERR_UNSUPPORTED  # schedule 3 is FP32-RHS only
@@ -95,4 +96,5 @@ def test_sizes_and_unbound_calls(L):
     rc, ctx = z4c.z4c_create(_mesh(), [_block()], 3, 4, _params(32))
     assert L.z4c_set_variant(ctx, 2, 2) == 0 and L.z4c_set_variant(ctx, 1, 4) == z4c.Z4C_ERR_UNSUPPORTED
     assert L.z4c_set_variant(ctx, 3, 4) == 0
+    assert L.z4c_set_variant(ctx, 4, 4) == 0 and L.z4c_set_variant(ctx, 4, 1) == z4c.Z4C_ERR_UNSUPPORTED
     L.z4c_destroy(ctx)

@@ -92,12 +92,14 @@ def test_rhs_parity_fp64(oracle, kind, order, nb, n, per, schedule):
         assert np.all(m.blocks(got)[b][:, ng] == 0)
 
 
-@pytest.mark.parametrize("precision,schedule", [(64, 1), (64, 2), (32, 1), (32, 2), (32, 3)])
+@pytest.mark.parametrize("precision,schedule", [(64, 1), (64, 2), (32, 1), (32, 2), (32, 3), (32, 4)])
 def test_flat_space_is_exactly_static(oracle, precision, schedule):
     # 16^3 blocks qualify for the staged FP32 kernel (schedule 3)
     n = 16 if schedule == 3 else 12
     w = H.small_workload("puncture", 6, (2, 1, 1), n, id_kind=inputs.ID_FLAT, id_par=[])
     g = H.gpu_ctx(w, precision, schedule)
+    if schedule == 4:
+        g.z4c_set_variant(4, 4)
     g.z4c_set_initial_data(inputs.ID_FLAT, [])
     g.z4c_fill_ghosts(0)
     assert np.all(g.z4c_rhs(0).cpu().numpy() == 0.0)
@@ -183,7 +185,7 @@ def _round_like_shadow(m, u):
     return v
 
 
-@pytest.mark.parametrize("schedule,occupancy", [(1, 1), (2, 1), (2, 2), (2, 4), (3, 4)])
+@pytest.mark.parametrize("schedule,occupancy", [(1, 1), (2, 1), (2, 2), (2, 4), (3, 4), (4, 4)])
 def test_fp32_rhs_error_budget(oracle, schedule, occupancy):
     """FP32 stencils and algebra (FP64 state, RK accumulation, 1/chi,
     enforcement).  Bounds, stated against what FP32 storage alone causes:
