@@ -92,7 +92,12 @@ int launch_fused_group(z4c_ctx *ctx, int g, const StageArgs &a) {
   const Tile *tl = ctx->d_tiles(g);
   int nt = (int)G.tiles.size();
   if (G.f32 && ctx->sched[1] == 4) {
-    CK(launch_split_f32(G.order, a, tl, nt, ctx->stream));
+    for (const Group::ExtRange &e : G.eranges) {
+      StageArgs ar = a;
+      ar.kbuf = a.kbuf + (size_t)e.first * NF * TX * TY;
+      CK(launch_split_rhs_f32(G.order, e.ext, ar, tl + e.first, e.count, ctx->stream));
+    }
+    CK(launch_split_epilogue(a, tl, nt, ctx->stream));
     return Z4C_OK;
   }
   if (G.f32 && ctx->sched[1] == 3 && !G.stiles.empty()) {
@@ -529,7 +534,7 @@ int z4c_launches_per_step(const z4c_ctx *ctx) {
     if (sc == 3 && G.f32 && !G.stiles.empty())
       per_stage += 2 + (G.rtiles.empty() ? 0 : 1);
     else if (sc == 4 && G.f32)
-      per_stage += 3;
+      per_stage += 2 + (int)G.eranges.size();
     else
       per_stage += sc >= 2 ? 2 : 1;
   }

@@ -438,6 +438,22 @@ int z4c_create_batch(const z4c_instance *instances, int ninstances, const z4c_bl
     if (r) return bail(r);
   }
   ctx->reg_elems = (size_t)off;
+  // FP32 groups: tiles sorted by the cubic storage extent of their block
+  // (stable, so the order within a block is kept), one range per extent
+  for (Group &G : ctx->grp) {
+    if (!G.f32 || G.tiles.empty()) continue;
+    auto ext_of = [&](const Tile &t) {
+      const DevBlock &D = ctx->dblocks[t.block];
+      return (D.e[0] == D.e[1] && D.e[1] == D.e[2]) ? D.e[0] : 0;
+    };
+    std::stable_sort(G.tiles.begin(), G.tiles.end(),
+                     [&](const Tile &x, const Tile &y) { return ext_of(x) < ext_of(y); });
+    for (int q = 0; q < (int)G.tiles.size(); ++q) {
+      const int e = ext_of(G.tiles[q]);
+      if (G.eranges.empty() || G.eranges.back().ext != e) G.eranges.push_back({e, q, 0});
+      ++G.eranges.back().count;
+    }
+  }
   // prolongation slots transposed to [125][entries] so that the threads of a
   // warp (neighbouring entries) read consecutive words
   {

@@ -31,6 +31,13 @@ struct Group {
   // FP32 order 6: the tiles split by whether their block qualifies for the
   // shared-memory staged kernel (schedule 3)
   std::vector<Tile> stiles, rtiles;
+  // FP32: tiles are sorted by their block's cubic storage extent (0: not
+  // cubic); ranges [first, first + count) of one extent, for the split
+  // schedule's specialised RHS kernels
+  struct ExtRange {
+    int ext, first, count;
+  };
+  std::vector<ExtRange> eranges;
   size_t o_tiles = 0, o_wtiles = 0, o_stiles = 0, o_rtiles = 0;
   bool empty() const { return tiles.empty(); }
 };

@@ -93,15 +93,20 @@ __global__ void __launch_bounds__(TX * TY) dydz_kernel(StageArgs a, const Tile *
 // OCC = minimum resident CTAs per SM the register allocation must allow
 // (1: up to 255 registers per thread; 4: 128), chosen by the autotuner.
 // SPLIT (FP32 only): store k in a.kbuf for split_epilogue_kernel instead of
-// applying the stage update here.
-template <int ORD, bool F32, int OCC, bool SPLIT = false>
+// applying the stage update here (k of tile blockIdx.x at kbuf + blockIdx.x
+// NF TX TY; the launcher offsets kbuf for a sub-range of a tile list).
+// EXT > 0: every block of the launch has cubic storage EXT^3 (n + 2g = EXT
+// along all axes), so all stencil offsets are compile-time constants.
+template <int ORD, bool F32, int OCC, bool SPLIT = false, int EXT = 0>
 __global__ void __launch_bounds__(TX * TY, OCC) interior_pre_kernel(StageArgs a, const Tile *__restrict__ tiles) {
   using R = typename std::conditional<F32, float, double>::type;
   const Tile t = tiles[blockIdx.x];
   const DevBlock &b = a.blocks[t.block];
   const int i = t.i0 + threadIdx.x, j = t.j0 + threadIdx.y, kk = t.k0;
   if (i >= b.n[0] || j >= b.n[1]) return;
-  const int g = b.g, e0 = b.e[0], e1 = b.e[1];
+  const int g = b.g;
+  const int e0 = EXT > 0 ? EXT : b.e[0], e1 = EXT > 0 ? EXT : b.e[1];
+  const int32_t S = EXT > 0 ? EXT * EXT * EXT : b.S;
   const int32_t cidx = ((kk + g) * e1 + (j + g)) * e0 + (i + g);
   const int st[3] = {1, e0, e0 * e1};
   const int64_t off = b.off + cidx;
@@ -113,9 +118,9 @@ __global__ void __launch_bounds__(TX * TY, OCC) interior_pre_kernel(StageArgs a,
     ichi = 1.0 / fmax(a.x64[off], b.chi_floor);
   const Phys<R> p{R(b.kappa1), R(b.kappa2), R(b.eta), b.lapse, b.shift};
   R k[NF];
-  const Src<R, false> ds{reinterpret_cast<const R *>(a.dstore) + b.off, cidx, b.S};
+  const Src<R, false> ds{reinterpret_cast<const R *>(a.dstore) + b.off, cidx, S};
   if constexpr (F32) {
-    const Src<float, true> s{a.x32 + b.off, cidx, b.S};
+    const Src<float, true> s{a.x32 + b.off, cidx, S};
     const Scales<float> sc = scales_of(b, 0.0f);
     const Pre<ORD, float, Src<float, true>, Src<float, false>> dv{s, ds, st, sc};
     rhs_point<ORD, float>(s, dv, st, sc, p, ichi, k);
@@ -126,12 +131,12 @@ __global__ void __launch_bounds__(TX * TY, OCC) interior_pre_kernel(StageArgs a,
       return;
     }
   } else {
-    const Src<double, false> s{a.x64 + b.off, cidx, b.S};
+    const Src<double, false> s{a.x64 + b.off, cidx, S};
     const Scales<double> sc = scales_of(b, 0.0);
     const Pre<ORD, double, Src<double, false>, Src<double, false>> dv{s, ds, st, sc};
     rhs_point<ORD, double>(s, dv, st, sc, p, ichi, k);
   }
-  stage_epilogue<R>(a, t.block, off, b.S, k);
+  stage_epilogue<R>(a, t.block, off, S, k);
 }
 
 }  // namespace z4c

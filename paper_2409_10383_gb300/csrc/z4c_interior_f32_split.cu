@@ -24,16 +24,10 @@ __global__ void __launch_bounds__(TX * TY, 8) split_epilogue_kernel(StageArgs a,
   stage_epilogue<float>(a, t.block, b.off + cidx, b.S, k);
 }
 
-cudaError_t launch_split_f32(int order, const StageArgs &a, const Tile *tiles, int ntiles, cudaStream_t st) {
+cudaError_t launch_split_epilogue(const StageArgs &a, const Tile *tiles, int ntiles, cudaStream_t st) {
   if (ntiles <= 0) return cudaSuccess;
-  dim3 block(TX, TY);
-  if (order == 4)
-    interior_pre_kernel<4, true, 4, true><<<ntiles, block, 0, st>>>(a, tiles);
-  else
-    interior_pre_kernel<6, true, 4, true><<<ntiles, block, 0, st>>>(a, tiles);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  split_epilogue_kernel<<<ntiles, block, 0, st>>>(a, tiles);
+  split_epilogue_kernel<<<ntiles, dim3(TX, TY), 0, st>>>(a, tiles);
   return cudaGetLastError();
 }
+
 }  // namespace z4c

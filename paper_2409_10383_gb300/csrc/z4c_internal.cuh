@@ -138,7 +138,14 @@ cudaError_t launch_staged_f32(int order, const StageArgs &a, const Tile *tiles, 
 // FP32 split schedule (4): the pre-pass-schedule RHS kernel stores k (FP32)
 // per tile in a.kbuf, then an epilogue kernel applies the RK stage update and
 // the FP64 enforcement at high occupancy
-cudaError_t launch_split_f32(int order, const StageArgs &a, const Tile *tiles, int ntiles, cudaStream_t st);
+// RHS kernel of one extent range (ext = cubic storage extent the kernel is
+// specialised for, 0 = runtime strides; a.kbuf already offset to the range's
+// first tile), and the stage-update kernel over the whole tile list
+cudaError_t launch_split_rhs_f32(int order, int ext, const StageArgs &a, const Tile *tiles, int ntiles,
+                                 cudaStream_t st);
+cudaError_t launch_split_epilogue(const StageArgs &a, const Tile *tiles, int ntiles, cudaStream_t st);
+// cubic storage extents with a specialised split RHS kernel (per order)
+bool split_ext_built(int order, int ext);
 // FP32 fused pre-pass-schedule kernel built for 2 or 4 resident CTAs per SM
 cudaError_t launch_fused_pre_f32_occ2(int order, const StageArgs &a, const Tile *tiles, int ntiles,
                                       cudaStream_t st);
