@@ -107,7 +107,11 @@ int launch_fused_group(z4c_ctx *ctx, int g, const StageArgs &a) {
     nt = (int)G.rtiles.size();
     if (!nt) return Z4C_OK;
   }
-  if (!G.f32)
+  if (!G.f32 && pre) {
+    for (const Group::ExtRange &e : G.eranges)
+      CK(G.order == 6 ? launch_fused_pre_f64_ext6(e.ext, a, tl + e.first, e.count, ctx->stream)
+                      : launch_fused_pre_f64_ext4(e.ext, a, tl + e.first, e.count, ctx->stream));
+  } else if (!G.f32)
     CK(launch_fused_f64(G.order, a, tl, nt, pre, ctx->stream));
   else if (pre && ctx->occ[1] == 4)
     CK(launch_fused_pre_f32_occ4(G.order, a, tl, nt, ctx->stream));
@@ -535,6 +539,8 @@ int z4c_launches_per_step(const z4c_ctx *ctx) {
       per_stage += 2 + (G.rtiles.empty() ? 0 : 1);
     else if (sc == 4 && G.f32)
       per_stage += 2 + (int)G.eranges.size();
+    else if (sc >= 2 && !G.f32)
+      per_stage += 1 + (int)G.eranges.size();
     else
       per_stage += sc >= 2 ? 2 : 1;
   }

@@ -438,10 +438,10 @@ int z4c_create_batch(const z4c_instance *instances, int ninstances, const z4c_bl
     if (r) return bail(r);
   }
   ctx->reg_elems = (size_t)off;
-  // FP32 groups: tiles sorted by the cubic storage extent of their block
-  // (stable, so the order within a block is kept), one range per extent
+  // tiles sorted by the cubic storage extent of their block (stable, so the
+  // order within a block is kept), one range per extent
   for (Group &G : ctx->grp) {
-    if (!G.f32 || G.tiles.empty()) continue;
+    if (G.tiles.empty()) continue;
     auto ext_of = [&](const Tile &t) {
       const DevBlock &D = ctx->dblocks[t.block];
       return (D.e[0] == D.e[1] && D.e[1] == D.e[2]) ? D.e[0] : 0;

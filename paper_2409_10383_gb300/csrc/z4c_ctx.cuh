@@ -31,9 +31,9 @@ struct Group {
   // FP32 order 6: the tiles split by whether their block qualifies for the
   // shared-memory staged kernel (schedule 3)
   std::vector<Tile> stiles, rtiles;
-  // FP32: tiles are sorted by their block's cubic storage extent (0: not
-  // cubic); ranges [first, first + count) of one extent, for the split
-  // schedule's specialised RHS kernels
+  // tiles are sorted by their block's cubic storage extent (0: not cubic);
+  // ranges [first, first + count) of one extent, for the kernels
+  // specialised on it (FP64 pre-pass schedule, FP32 split schedule)
   struct ExtRange {
     int ext, first, count;
   };

@@ -146,6 +146,10 @@ cudaError_t launch_split_rhs_f32(int order, int ext, const StageArgs &a, const T
 cudaError_t launch_split_epilogue(const StageArgs &a, const Tile *tiles, int ntiles, cudaStream_t st);
 // cubic storage extents with a specialised split RHS kernel (per order)
 bool split_ext_built(int order, int ext);
+// FP64 fused pre-pass-schedule kernel for one extent range (ext as above;
+// extents without a specialised kernel use runtime strides)
+cudaError_t launch_fused_pre_f64_ext6(int ext, const StageArgs &a, const Tile *tiles, int ntiles, cudaStream_t st);
+cudaError_t launch_fused_pre_f64_ext4(int ext, const StageArgs &a, const Tile *tiles, int ntiles, cudaStream_t st);
 // FP32 fused pre-pass-schedule kernel built for 2 or 4 resident CTAs per SM
 cudaError_t launch_fused_pre_f32_occ2(int order, const StageArgs &a, const Tile *tiles, int ntiles,
                                       cudaStream_t st);
