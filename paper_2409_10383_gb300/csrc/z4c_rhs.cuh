@@ -545,10 +545,25 @@ __device__ __forceinline__ void rhs_point(const SRC &s, const DV &dv, const int 
       up[d] = beta[d] >= R(0);
       ab[d] = fabs(beta[d]) * sc.slop;
     }
+    // one field at a time (an unrolled loop exceeds the register budget)
+    if constexpr (sizeof(R) == 4) {
+      // FP32: the result goes to a shared-memory slot per field and cell, so
+      // that k[] is only indexed by compile-time constants (a runtime index
+      // into a register array costs a compare-and-select per element)
+      __shared__ R kko[NF][TX * TY];
+      const int tid = threadIdx.y * TX + threadIdx.x;
 #pragma unroll 1
-    for (int f = 0; f < NF; ++f) {
-      if (!p.shift && f >= BETAX) continue;
-      k[f] += ko_adv<ORD>(s, f, st, up, ab, sc.sko);
+      for (int f = 0; f < NF; ++f)
+        kko[f][tid] = (!p.shift && f >= BETAX) ? R(0) : ko_adv<ORD>(s, f, st, up, ab, sc.sko);
+#pragma unroll
+      for (int f = 0; f < NF; ++f) k[f] += kko[f][tid];
+    } else {
+      // FP64 (k[] lives in local memory here; the FP64 pipe is the bound)
+#pragma unroll 1
+      for (int f = 0; f < NF; ++f) {
+        if (!p.shift && f >= BETAX) continue;
+        k[f] += ko_adv<ORD>(s, f, st, up, ab, sc.sko);
+      }
     }
   }
 }
