@@ -39,12 +39,20 @@ int fill_ghosts(z4c_ctx *ctx, double *reg, float *sh) {
     const DevBlock *B = ctx->d_blocks();
     const double *wtab = ctx->at<double>(ctx->o_wtab);
     // phase 1: everything reads active cells only
-    CK(launch_restrict(reg, B, ctx->at<RestrictRef>(ctx->o_rghost), (int)ctx->rghost.size(), wtab, false,
-                       ctx->d_cb(), ctx->ncb, ctx->stream));
+    if (ctx->rb_mode) {
+      double *rb = (double *)(ctx->scratch + ctx->o_rb);
+      CK(launch_restrict_blocks(reg, B, ctx->at<int32_t>(ctx->o_rblocks), (int)ctx->rblocks.size(), wtab,
+                                ctx->at<int32_t>(ctx->o_krow), rb, ctx->stream));
+      CK(launch_rb_scatter(reg, B, ctx->at<RbCopy>(ctx->o_rbcopy), (int)ctx->rbcopy.size(), rb, ctx->d_cb(),
+                           ctx->ncb, ctx->stream));
+    } else {
+      CK(launch_restrict(reg, B, ctx->at<RestrictRef>(ctx->o_rghost), (int)ctx->rghost.size(), wtab, false,
+                         ctx->d_cb(), ctx->ncb, ctx->stream));
+      CK(launch_restrict(reg, B, ctx->at<RestrictRef>(ctx->o_rbuf), (int)ctx->rbuf.size(), wtab, true,
+                         ctx->d_cb(), ctx->ncb, ctx->stream));
+    }
     CK(launch_cb_copy(reg, B, ctx->at<CbCopy>(ctx->o_cbcopy), (int)ctx->cbcopy.size(), ctx->d_cb(), ctx->ncb,
                       ctx->stream));
-    CK(launch_restrict(reg, B, ctx->at<RestrictRef>(ctx->o_rbuf), (int)ctx->rbuf.size(), wtab, true, ctx->d_cb(),
-                       ctx->ncb, ctx->stream));
     // phase 2: prolongation from the coarse buffer
     CK(launch_prolong(reg, B, ctx->at<ProlongRef>(ctx->o_prol), (int)ctx->prol.size(),
                       ctx->at<int32_t>(ctx->o_pidx), ctx->d_cb(), ctx->ncb, ctx->at<double>(ctx->o_pw),
@@ -530,8 +538,11 @@ int z4c_launches_per_step(const z4c_ctx *ctx) {
   if (!ctx) return Z4C_ERR_BAD_ARG;
   int per_stage = 0;
   for (int p = 0; p < 2; ++p) per_stage += (ctx->gcopy[p].empty() ? 0 : 1) + (ctx->somm[p].empty() ? 0 : 1);
-  per_stage += (ctx->rghost.empty() ? 0 : 1) + (ctx->cbcopy.empty() ? 0 : 1) + (ctx->rbuf.empty() ? 0 : 1) +
-               (ctx->prol.empty() ? 0 : 1);
+  if (ctx->rb_mode)
+    per_stage += 2;  // block restriction + scatter
+  else
+    per_stage += (ctx->rghost.empty() ? 0 : 1) + (ctx->rbuf.empty() ? 0 : 1);
+  per_stage += (ctx->cbcopy.empty() ? 0 : 1) + (ctx->prol.empty() ? 0 : 1);
   for (const Group &G : ctx->grp) {
     if (G.empty()) continue;
     const int sc = ctx->sched[G.f32 ? 1 : 0];

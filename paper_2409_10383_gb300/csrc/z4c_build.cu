@@ -182,6 +182,7 @@ struct GhostBuilder {
       s = std::min<long long>(std::max<long long>(s, 0), n - 5);
       r.wp[d] = pattern((int)(s - 2 * c));
       st[d] = s + I.ghosts;
+      r.cc |= (int32_t)(c << (8 * d));
     }
     r.src = I.first + nb;
     r.s = storage_index(nb, st);
@@ -438,6 +439,36 @@ int z4c_create_batch(const z4c_instance *instances, int ninstances, const z4c_bl
     if (r) return bail(r);
   }
   ctx->reg_elems = (size_t)off;
+  // block-structured restriction when every fine block that is restricted
+  // has at most RB_NMAX cells per axis
+  {
+    bool ok = !(ctx->rghost.empty() && ctx->rbuf.empty());
+    for (const auto *lst : {&ctx->rghost, &ctx->rbuf})
+      for (const RestrictRef &r : *lst)
+        for (int d = 0; d < 3; ++d) ok &= ctx->blocks[r.src].n[d] <= RB_NMAX;
+    if (ok) {
+      ctx->rb_mode = true;
+      for (int key = -4; key < 4; ++key) {  // the same weights as GhostBuilder::pattern
+        double xs[5];
+        for (int q = 0; q < 5; ++q) xs[q] = key + q - 0.5;
+        ctx->krow[key + 4] = (int32_t)(ctx->wtab.size() / 5);
+        for (int q = 0; q < 5; ++q) ctx->wtab.push_back(lagrange5(xs, q, 0.0));
+      }
+      std::map<int, int> rbi;
+      auto add = [&](const RestrictRef &r, int32_t dst, int32_t didx) {
+        auto it = rbi.find(r.src);
+        if (it == rbi.end()) {
+          it = rbi.emplace(r.src, (int)ctx->rblocks.size()).first;
+          ctx->rblocks.push_back(r.src);
+        }
+        const z4c_block &B = ctx->blocks[r.src];
+        const int c0 = r.cc & 255, c1 = (r.cc >> 8) & 255, c2 = (r.cc >> 16) & 255;
+        ctx->rbcopy.push_back(RbCopy{dst, didx, it->second, (c2 * (B.n[1] / 2) + c1) * (B.n[0] / 2) + c0});
+      };
+      for (const RestrictRef &r : ctx->rghost) add(r, r.dst, r.didx);
+      for (const RestrictRef &r : ctx->rbuf) add(r, -1, r.didx);
+    }
+  }
   // tiles sorted by the cubic storage extent of their block (stable, so the
   // order within a block is kept), one range per extent
   for (Group &G : ctx->grp) {
@@ -484,6 +515,10 @@ int z4c_create_batch(const z4c_instance *instances, int ninstances, const z4c_bl
   }
   ctx->o_rghost = take(sizeof(RestrictRef) * ctx->rghost.size());
   ctx->o_rbuf = take(sizeof(RestrictRef) * ctx->rbuf.size());
+  ctx->o_rblocks = take(sizeof(int32_t) * ctx->rblocks.size());
+  ctx->o_rbcopy = take(sizeof(RbCopy) * ctx->rbcopy.size());
+  ctx->o_krow = take(sizeof(int32_t) * 8);
+  ctx->o_rb = take(sizeof(double) * NF * RB_NC3 * ctx->rblocks.size());
   ctx->o_cbcopy = take(sizeof(CbCopy) * ctx->cbcopy.size());
   ctx->o_prol = take(sizeof(ProlongRef) * ctx->prol.size());
   ctx->o_pidx = take(sizeof(int32_t) * ctx->pidx.size());
@@ -569,6 +604,9 @@ int z4c_bind(z4c_ctx *ctx, void *u0, void *stage_a, void *stage_b, void *acc, vo
   }
   CK(up(ctx->o_rghost, ctx->rghost.data(), sizeof(RestrictRef) * ctx->rghost.size()));
   CK(up(ctx->o_rbuf, ctx->rbuf.data(), sizeof(RestrictRef) * ctx->rbuf.size()));
+  CK(up(ctx->o_rblocks, ctx->rblocks.data(), sizeof(int32_t) * ctx->rblocks.size()));
+  CK(up(ctx->o_rbcopy, ctx->rbcopy.data(), sizeof(RbCopy) * ctx->rbcopy.size()));
+  CK(up(ctx->o_krow, ctx->krow, sizeof(int32_t) * 8));
   CK(up(ctx->o_cbcopy, ctx->cbcopy.data(), sizeof(CbCopy) * ctx->cbcopy.size()));
   CK(up(ctx->o_prol, ctx->prol.data(), sizeof(ProlongRef) * ctx->prol.size()));
   CK(up(ctx->o_pidx, ctx->pidx.data(), sizeof(int32_t) * ctx->pidx.size()));

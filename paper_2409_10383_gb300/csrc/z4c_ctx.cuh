@@ -61,6 +61,13 @@ struct z4c_ctx {
   std::vector<double> wtab;              // restriction weight patterns (5 each)
   double pw[50] = {0};                   // prolongation weights [shift + 2][child][5]
   int ncb = 0;                           // coarse-buffer slots
+  // block-structured restriction (every fine block with restriction targets
+  // has at most RB_NMAX cells per axis): the fine blocks, the scatter list,
+  // wtab rows of the weight pattern keys -4..3
+  bool rb_mode = false;
+  std::vector<int32_t> rblocks;
+  std::vector<z4c::RbCopy> rbcopy;
+  int32_t krow[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   std::vector<double> dt_host;           // time step per block
   size_t reg_elems = 0;
   int max_S = 0;
@@ -68,7 +75,8 @@ struct z4c_ctx {
   // scratch layout (byte offsets)
   size_t o_blocks = 0, o_somm[2] = {0, 0}, o_gcopy[2] = {0, 0}, o_ctiles = 0, o_part = 0, o_res = 0,
          o_dt = 0, o_sh0 = 0, o_sh1 = 0, o_ds64 = 0, o_ds32 = 0, o_rghost = 0, o_rbuf = 0, o_cbcopy = 0,
-         o_prol = 0, o_pidx = 0, o_wtab = 0, o_pw = 0, o_cb = 0, o_status = 0, o_kbuf = 0, scratch_total = 0;
+         o_prol = 0, o_pidx = 0, o_wtab = 0, o_pw = 0, o_cb = 0, o_status = 0, o_kbuf = 0, o_rblocks = 0,
+         o_rbcopy = 0, o_krow = 0, o_rb = 0, scratch_total = 0;
   // bound buffers
   double *reg[4] = {nullptr, nullptr, nullptr, nullptr};
   char *scratch = nullptr;

@@ -73,7 +73,17 @@ struct RestrictRef {
   int32_t src;    // fine block
   int32_t s;      // storage index of the stencil's lowest corner in src
   int32_t wp[3];  // weight pattern per axis (x, y, z)
-  int32_t pad;
+  int32_t cc;     // the coarse cell in src's coarse lattice: c_x | c_y << 8 | c_z << 16
+};
+// Block-structured restriction (fine blocks of at most RB_NMAX cells per
+// axis): every coarse cell of a listed fine block is restricted into the
+// block's slab of rb (RB_NC3 values per field), then scattered: to a coarse
+// ghost cell (dst >= 0: block, storage index didx) or a coarse-buffer slot
+// (dst < 0: slot didx); ci = coarse cell index (c_z nc_y + c_y) nc_x + c_x.
+constexpr int RB_NMAX = 16;
+constexpr int RB_NC3 = (RB_NMAX / 2) * (RB_NMAX / 2) * (RB_NMAX / 2);
+struct RbCopy {
+  int32_t dst, didx, rb, ci;
 };
 // Coarse-buffer slot <- active cell of a coarser block.
 struct CbCopy {
@@ -127,6 +137,10 @@ constexpr int TY = 8;
 // into coarse-buffer slots (true); buffer copies; prolongation from the buffer
 cudaError_t launch_restrict(double *reg, const DevBlock *blocks, const RestrictRef *list, int n,
                             const double *wtab, bool to_buffer, double *cb, int ncb, cudaStream_t st);
+cudaError_t launch_restrict_blocks(const double *reg, const DevBlock *blocks, const int32_t *rblocks, int nrb,
+                                   const double *wtab, const int32_t *krow, double *rb, cudaStream_t st);
+cudaError_t launch_rb_scatter(double *reg, const DevBlock *blocks, const RbCopy *list, int n, const double *rb,
+                              double *cb, int ncb, cudaStream_t st);
 cudaError_t launch_cb_copy(const double *reg, const DevBlock *blocks, const CbCopy *list, int n, double *cb,
                            int ncb, cudaStream_t st);
 cudaError_t launch_prolong(double *reg, const DevBlock *blocks, const ProlongRef *list, int n,

@@ -12,6 +12,21 @@ cudaError_t launch_restrict(double *reg, const DevBlock *blocks, const RestrictR
   return cudaGetLastError();
 }
 
+cudaError_t launch_restrict_blocks(const double *reg, const DevBlock *blocks, const int32_t *rblocks, int nrb,
+                                   const double *wtab, const int32_t *krow, double *rb, cudaStream_t st) {
+  if (nrb <= 0) return cudaSuccess;
+  restrict_block_kernel<<<dim3(nrb, NF), 256, 0, st>>>(reg, blocks, rblocks, wtab, krow, rb);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rb_scatter(double *reg, const DevBlock *blocks, const RbCopy *list, int n, const double *rb,
+                              double *cb, int ncb, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const long long tot = (long long)n * NF;
+  rb_scatter_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, st>>>(reg, blocks, list, n, rb, cb, ncb);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_cb_copy(const double *reg, const DevBlock *blocks, const CbCopy *list, int n, double *cb, int ncb,
                            cudaStream_t st) {
   if (n <= 0) return cudaSuccess;

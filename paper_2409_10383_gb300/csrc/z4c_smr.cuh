@@ -44,6 +44,89 @@ __global__ void restrict_kernel(double *__restrict__ reg, const DevBlock *__rest
   }
 }
 
+// Restriction of every coarse cell of one fine block (blockIdx.x indexes
+// rblocks) for one field (blockIdx.y), by three passes over the block's
+// active cells staged in shared memory: x, then y, then z, each the 5-point
+// Lagrange sum with the same start rule, weights and evaluation order as
+// restrict_kernel, so the results are identical; a coarse cell's x-pass
+// partial sums are shared by every coarse cell in its (y, z) neighbourhood.
+// krow[key + 4] = wtab row of the weight pattern key = start - 2c.
+__global__ void __launch_bounds__(256) restrict_block_kernel(const double *__restrict__ reg,
+                                                             const DevBlock *__restrict__ blocks,
+                                                             const int32_t *__restrict__ rblocks,
+                                                             const double *__restrict__ wtab,
+                                                             const int32_t *__restrict__ krow,
+                                                             double *__restrict__ rb) {
+  __shared__ double fine[RB_NMAX * RB_NMAX * RB_NMAX];       // then the y-pass output
+  __shared__ double rx[RB_NMAX * RB_NMAX * (RB_NMAX / 2)];   // x-pass output
+  const DevBlock &B = blocks[rblocks[blockIdx.x]];
+  const int f = blockIdx.y;
+  const int nx = B.n[0], ny = B.n[1], nz = B.n[2];
+  const int cx = nx / 2, cy = ny / 2, cz = nz / 2;
+  const int g = B.g, e0 = B.e[0], e1 = B.e[1];
+  const double *src = reg + B.off + (int64_t)f * B.S;
+  auto start = [](int c, int n) {
+    const int nc = n / 2;
+    int s = c < nc / 2 ? 2 * c - 1 : 2 * c - 2;
+    return s < 0 ? 0 : s > n - 5 ? n - 5 : s;
+  };
+  for (int q = threadIdx.x; q < nx * ny * nz; q += blockDim.x) {
+    const int i = q % nx, j = (q / nx) % ny, k = q / (nx * ny);
+    fine[q] = src[((k + g) * e1 + (j + g)) * e0 + (i + g)];
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < cx * ny * nz; q += blockDim.x) {  // (c_x, j, k)
+    const int c = q % cx, jk = q / cx;
+    const int s = start(c, nx);
+    const double *w = wtab + 5 * krow[s - 2 * c + 4];
+    const double *row = fine + jk * nx + s;
+    double v = 0.0;
+#pragma unroll
+    for (int a = 0; a < 5; ++a) v = fma(w[a], row[a], v);
+    rx[q] = v;
+  }
+  __syncthreads();
+  double *ry = fine;
+  for (int q = threadIdx.x; q < cx * cy * nz; q += blockDim.x) {  // (c_x, c_y, k)
+    const int c0 = q % cx, c = (q / cx) % cy, k = q / (cx * cy);
+    const int s = start(c, ny);
+    const double *w = wtab + 5 * krow[s - 2 * c + 4];
+    double v = 0.0;
+#pragma unroll
+    for (int b = 0; b < 5; ++b) v = fma(w[b], rx[(k * ny + s + b) * cx + c0], v);
+    ry[q] = v;
+  }
+  __syncthreads();
+  double *out = rb + ((int64_t)blockIdx.x * NF + f) * RB_NC3;
+  for (int q = threadIdx.x; q < cx * cy * cz; q += blockDim.x) {  // (c_x, c_y, c_z)
+    const int cxy = q % (cx * cy), c = q / (cx * cy);
+    const int s = start(c, nz);
+    const double *w = wtab + 5 * krow[s - 2 * c + 4];
+    double v = 0.0;
+#pragma unroll
+    for (int cc = 0; cc < 5; ++cc) v = fma(w[cc], ry[(s + cc) * cx * cy + cxy], v);
+    out[q] = v;
+  }
+}
+
+// Scatter of block-restricted values to coarse ghost cells and coarse-buffer
+// slots; one thread per (entry, field), entries fastest.
+__global__ void rb_scatter_kernel(double *__restrict__ reg, const DevBlock *__restrict__ blocks,
+                                  const RbCopy *__restrict__ list, int n, const double *__restrict__ rb,
+                                  double *__restrict__ cb, int ncb) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n * NF) return;
+  const int e = t % n, f = t / n;
+  const RbCopy r = list[e];
+  const double v = rb[((int64_t)r.rb * NF + f) * RB_NC3 + r.ci];
+  if (r.dst >= 0) {
+    const DevBlock &D = blocks[r.dst];
+    reg[D.off + (int64_t)f * D.S + r.didx] = v;
+  } else {
+    cb[(int64_t)f * ncb + r.didx] = v;
+  }
+}
+
 __global__ void cb_copy_kernel(const double *__restrict__ reg, const DevBlock *__restrict__ blocks,
                                const CbCopy *__restrict__ list, int n, double *__restrict__ cb, int ncb) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;

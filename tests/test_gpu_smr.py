@@ -52,6 +52,22 @@ def test_smr_ghost_fill_parity(oracle, order, periodic, centre):
     assert np.abs(got - u).max() <= 1e-13, np.abs(got - u).max()
 
 
+def test_smr_ghost_fill_parity_wide_blocks(oracle):
+    """Fine blocks of 24^3 (wider than the block-structured restriction
+    handles): the per-entry restriction kernel."""
+    from paper_2409_10383_gb300.z4c import Z4c
+    w = smr_workload(nb=2, n=24, radii=(0.05,))
+    m = oracle_of(oracle, w)
+    assert (m.level == 1).sum() == 8 and (m.level == 0).sum() == 7
+    g = Z4c.from_workload(w)
+    u = m.zeros() + inputs.noise(m.size(), 43)
+    g.z4c_set_state(u, reg=2)
+    g.z4c_fill_ghosts(2)
+    got = g.z4c_get_state(2)
+    m.fill_ghosts(u)
+    assert np.abs(got - u).max() <= 1e-13, np.abs(got - u).max()
+
+
 def test_smr_puncture_rk4_parity(oracle):
     from paper_2409_10383_gb300.z4c import Z4c
     w = smr_workload()
