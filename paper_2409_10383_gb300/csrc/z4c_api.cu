@@ -53,7 +53,11 @@ int fill_ghosts(z4c_ctx *ctx, double *reg, float *sh) {
     }
     CK(launch_cb_copy(reg, B, ctx->at<CbCopy>(ctx->o_cbcopy), (int)ctx->cbcopy.size(), ctx->d_cb(), ctx->ncb,
                       ctx->stream));
-    // phase 2: prolongation from the coarse buffer
+    // phase 2: prolongation from the coarse buffer (whole ghost regions as
+    // boxes, the other parents one by one)
+    CK(launch_prolong_boxes(reg, B, ctx->at<PBox>(ctx->o_pbox), (int)ctx->pbox.size(),
+                            ctx->at<int32_t>(ctx->o_pslots), ctx->at<int32_t>(ctx->o_paxtab), ctx->d_cb(),
+                            ctx->ncb, ctx->at<double>(ctx->o_pw), ctx->stream));
     CK(launch_prolong(reg, B, ctx->at<ProlongRef>(ctx->o_prol), (int)ctx->prol.size(),
                       ctx->at<int32_t>(ctx->o_pidx), ctx->d_cb(), ctx->ncb, ctx->at<double>(ctx->o_pw),
                       ctx->stream));
@@ -542,7 +546,7 @@ int z4c_launches_per_step(const z4c_ctx *ctx) {
     per_stage += 2;  // block restriction + scatter
   else
     per_stage += (ctx->rghost.empty() ? 0 : 1) + (ctx->rbuf.empty() ? 0 : 1);
-  per_stage += (ctx->cbcopy.empty() ? 0 : 1) + (ctx->prol.empty() ? 0 : 1);
+  per_stage += (ctx->cbcopy.empty() ? 0 : 1) + (ctx->prol.empty() ? 0 : 1) + (ctx->pbox.empty() ? 0 : 1);
   for (const Group &G : ctx->grp) {
     if (G.empty()) continue;
     const int sc = ctx->sched[G.f32 ? 1 : 0];

@@ -7,6 +7,7 @@
 // prolongations.  Everything is laid out in the caller's scratch buffer.  No
 // CUDA call happens before z4c_bind.
 #include <algorithm>
+#include <climits>
 #include <array>
 #include <cmath>
 #include <cstring>
@@ -219,6 +220,88 @@ struct GhostBuilder {
     return s;
   }
 
+  // Stencil start (global level-(L-1) index, shifted into a non-periodic
+  // domain) and pw row of the fine cell with global level-L index gi.
+  void stencil_of(long long gi, double hc, int d, long long &start, int &row) const {
+    const long long P = gi >= 0 ? gi / 2 : -((-gi + 1) / 2);  // floor(gi / 2)
+    long long sh = 0;
+    if (!I.mesh.periodic) {
+      const long long nd = iround((I.mesh.hi[d] - I.mesh.lo[d]) / hc);
+      sh = std::max<long long>(std::min<long long>(P - 2, nd - 5), 0) - (P - 2);
+    }
+    start = P - 2 + sh;
+    row = (int)(10 * (sh + 2) + 5 * (gi - 2 * P));
+  }
+
+  // Ghost regions of block lb (index r0 + 3 r1 + 9 r2 with r_d = 0 below,
+  // 1 beside, 2 above the interior along d) that lie inside the domain and
+  // wholly in coarser blocks become PBox entries, when the ghost width is
+  // even (no parent straddles two regions), at most 4, and the block has at
+  // most 16 cells per axis.
+  void boxes(int lb, bool boxed[27], int &err) {
+    const int g = I.ghosts, L = blk(lb).level;
+    if (g % 2 != 0 || g > 4 || L == 0) return;
+    for (int d = 0; d < 3; ++d)
+      if (Lo.n[d] > 16) return;
+    const double h = hb(lb), hc = 2.0 * h;
+    const int e[3] = {Lo.n[0] + 2 * g, Lo.n[1] + 2 * g, Lo.n[2] + 2 * g};
+    for (int r = 0; r < 27; ++r) {
+      if (r == 13) continue;  // the interior
+      int lo[3], hi[3];
+      for (int d = 0, q = r; d < 3; ++d, q /= 3) {
+        const int rd = q % 3;
+        lo[d] = rd == 0 ? 0 : rd == 1 ? g : g + Lo.n[d];
+        hi[d] = rd == 0 ? g : rd == 1 ? g + Lo.n[d] : e[d];
+      }
+      bool all = true;
+      for (int k = lo[2]; k < hi[2] && all; ++k)
+        for (int j = lo[1]; j < hi[1] && all; ++j)
+          for (int i = lo[0]; i < hi[0] && all; ++i) {
+            const int idx[3] = {i, j, k};
+            double x[3];
+            for (int d = 0; d < 3; ++d) x[d] = blk(lb).lo[d] + (idx[d] - g + 0.5) * h;
+            all = inside(x) && blk(owner_of(x)).level == L - 1;
+          }
+      if (!all) continue;
+      PBox B{};
+      B.dst = I.first + lb;
+      B.ax = (int)ctx->paxtab.size();
+      long long cmin[3], cmax[3];
+      for (int d = 0; d < 3; ++d) {
+        B.o[d] = (int16_t)lo[d];
+        B.nf[d] = (uint8_t)(hi[d] - lo[d]);
+        cmin[d] = LLONG_MAX;
+        cmax[d] = LLONG_MIN;
+        for (int s = lo[d]; s < hi[d]; ++s) {
+          long long st;
+          int row;
+          stencil_of(Lo.go[lb][d] + s - g, hc, d, st, row);
+          cmin[d] = std::min(cmin[d], st);
+          cmax[d] = std::max(cmax[d], st + 4);
+        }
+        B.nc[d] = (uint8_t)(cmax[d] - cmin[d] + 1);
+      }
+      const int ncb = B.nc[0] * B.nc[1] * B.nc[2];
+      if (ncb > PB_C || B.nf[0] * B.nc[1] * B.nc[2] > PB_X || B.nf[0] * B.nf[1] * B.nc[2] > PB_Y) continue;
+      for (int d = 0; d < 3; ++d)
+        for (int s = lo[d]; s < hi[d]; ++s) {
+          long long st;
+          int row;
+          stencil_of(Lo.go[lb][d] + s - g, hc, d, st, row);
+          ctx->paxtab.push_back((int32_t)((row << 16) | (int)(st - cmin[d])));
+        }
+      B.tab = (int)ctx->pslots.size();
+      for (long long z = cmin[2]; z <= cmax[2]; ++z)
+        for (long long y = cmin[1]; y <= cmax[1]; ++y)
+          for (long long x = cmin[0]; x <= cmax[0]; ++x) {
+            const long long q[3] = {x, y, z};
+            ctx->pslots.push_back(coarse_slot(L - 1, q, err));
+          }
+      ctx->pbox.push_back(B);
+      boxed[r] = true;
+    }
+  }
+
   int build() {
     const int g = I.ghosts;
     const int e[3] = {Lo.n[0] + 2 * g, Lo.n[1] + 2 * g, Lo.n[2] + 2 * g};
@@ -227,6 +310,13 @@ struct GhostBuilder {
       const int b = I.first + lb, L = blk(lb).level;
       const double h = hb(lb);
       std::map<std::array<long long, 3>, int> parents;  // prolongation parents already listed
+      bool boxed[27] = {false};
+      boxes(lb, boxed, err);
+      auto region_of = [&](const int idx[3]) {
+        int r = 0;
+        for (int d = 2; d >= 0; --d) r = 3 * r + (idx[d] < g ? 0 : idx[d] < Lo.n[d] + g ? 1 : 2);
+        return r;
+      };
       for (int k = 0; k < e[2]; ++k)
         for (int j = 0; j < e[1]; ++j)
           for (int i = 0; i < e[0]; ++i) {
@@ -256,6 +346,7 @@ struct GhostBuilder {
               r.didx = cidx;
               ctx->rghost.push_back(r);
             } else if (ln == L - 1) {
+              if (boxed[region_of(idx)]) continue;  // filled by prolong_box_kernel
               // parent coarse cell (global index at level L-1, unwrapped)
               std::array<long long, 3> pc;
               const double hc = 2.0 * h;
@@ -521,6 +612,9 @@ int z4c_create_batch(const z4c_instance *instances, int ninstances, const z4c_bl
   ctx->o_rb = take(sizeof(double) * NF * RB_NC3 * ctx->rblocks.size());
   ctx->o_cbcopy = take(sizeof(CbCopy) * ctx->cbcopy.size());
   ctx->o_prol = take(sizeof(ProlongRef) * ctx->prol.size());
+  ctx->o_pbox = take(sizeof(PBox) * ctx->pbox.size());
+  ctx->o_pslots = take(sizeof(int32_t) * ctx->pslots.size());
+  ctx->o_paxtab = take(sizeof(int32_t) * ctx->paxtab.size());
   ctx->o_pidx = take(sizeof(int32_t) * ctx->pidx.size());
   ctx->o_wtab = take(sizeof(double) * ctx->wtab.size());
   ctx->o_pw = take(sizeof(double) * 50);
@@ -609,6 +703,9 @@ int z4c_bind(z4c_ctx *ctx, void *u0, void *stage_a, void *stage_b, void *acc, vo
   CK(up(ctx->o_krow, ctx->krow, sizeof(int32_t) * 8));
   CK(up(ctx->o_cbcopy, ctx->cbcopy.data(), sizeof(CbCopy) * ctx->cbcopy.size()));
   CK(up(ctx->o_prol, ctx->prol.data(), sizeof(ProlongRef) * ctx->prol.size()));
+  CK(up(ctx->o_pbox, ctx->pbox.data(), sizeof(PBox) * ctx->pbox.size()));
+  CK(up(ctx->o_pslots, ctx->pslots.data(), sizeof(int32_t) * ctx->pslots.size()));
+  CK(up(ctx->o_paxtab, ctx->paxtab.data(), sizeof(int32_t) * ctx->paxtab.size()));
   CK(up(ctx->o_pidx, ctx->pidx.data(), sizeof(int32_t) * ctx->pidx.size()));
   CK(up(ctx->o_wtab, ctx->wtab.data(), sizeof(double) * ctx->wtab.size()));
   CK(up(ctx->o_pw, ctx->pw, sizeof(double) * 50));

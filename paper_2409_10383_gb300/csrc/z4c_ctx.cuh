@@ -58,6 +58,8 @@ struct z4c_ctx {
   std::vector<z4c::CbCopy> cbcopy;       // coarse-buffer slots <- a coarser block's active cell
   std::vector<z4c::ProlongRef> prol;     // fine ghost cells <- prolongation from the buffer
   std::vector<int32_t> pidx;             // buffer slots, [125][prolongation entries] once built
+  std::vector<z4c::PBox> pbox;           // ghost regions prolonged as boxes
+  std::vector<int32_t> pslots, paxtab;   // their coarse-box slots and per-axis stencil tables
   std::vector<double> wtab;              // restriction weight patterns (5 each)
   double pw[50] = {0};                   // prolongation weights [shift + 2][child][5]
   int ncb = 0;                           // coarse-buffer slots
@@ -76,7 +78,8 @@ struct z4c_ctx {
   size_t o_blocks = 0, o_somm[2] = {0, 0}, o_gcopy[2] = {0, 0}, o_ctiles = 0, o_part = 0, o_res = 0,
          o_dt = 0, o_sh0 = 0, o_sh1 = 0, o_ds64 = 0, o_ds32 = 0, o_rghost = 0, o_rbuf = 0, o_cbcopy = 0,
          o_prol = 0, o_pidx = 0, o_wtab = 0, o_pw = 0, o_cb = 0, o_status = 0, o_kbuf = 0, o_rblocks = 0,
-         o_rbcopy = 0, o_krow = 0, o_rb = 0, scratch_total = 0;
+         o_rbcopy = 0, o_krow = 0, o_rb = 0, o_pbox = 0, o_pslots = 0,
+         o_paxtab = 0, scratch_total = 0;
   // bound buffers
   double *reg[4] = {nullptr, nullptr, nullptr, nullptr};
   char *scratch = nullptr;
@@ -110,7 +113,7 @@ struct z4c_ctx {
   double *d_dt() const { return (double *)(scratch + o_dt); }
   float *d_sh(int q) const { return (float *)(scratch + (q == 0 ? o_sh0 : o_sh1)); }
   void *d_dstore(bool f32) const { return scratch + (f32 ? o_ds32 : o_ds64); }
-  bool smr() const { return !prol.empty() || !rghost.empty(); }
+  bool smr() const { return !prol.empty() || !rghost.empty() || !pbox.empty(); }
   template <class T>
   const T *at(size_t o) const { return (const T *)(scratch + o); }
   double *d_cb() const { return (double *)(scratch + o_cb); }

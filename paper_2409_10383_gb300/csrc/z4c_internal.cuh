@@ -102,6 +102,18 @@ struct ProlongRef {
   int32_t dst, cidx0, base, mask;
 };
 constexpr int PROLONG_SHIFT_BIT = 8;
+// Box prolongation: one ghost region (face, edge or corner) of fine block
+// dst that lies wholly in one coarser block.  Fine cells: storage origin o,
+// extents nf; coarse values from the coarse-buffer slots slots[tab + q] of a
+// box of nc cells (x fastest).  Per fine index along axis d (entries ax +
+// (0 | nf0 | nf0 + nf1) + i): the stencil's first coarse cell in the box
+// (low 16 bits) and the pw row (high 16 bits).  Smem bounds per box below.
+struct PBox {
+  int32_t dst, tab, ax;
+  int16_t o[3];
+  uint8_t nf[3], nc[3];
+};
+constexpr int PB_C = 1024, PB_X = 1536, PB_Y = 1536;
 
 // Which update the stage kernel applies after computing k = RHS(x):
 //   MODE_RHS:  rhs_out = k
@@ -141,6 +153,9 @@ cudaError_t launch_restrict_blocks(const double *reg, const DevBlock *blocks, co
                                    const double *wtab, const int32_t *krow, double *rb, cudaStream_t st);
 cudaError_t launch_rb_scatter(double *reg, const DevBlock *blocks, const RbCopy *list, int n, const double *rb,
                               double *cb, int ncb, cudaStream_t st);
+cudaError_t launch_prolong_boxes(double *reg, const DevBlock *blocks, const PBox *boxes, int nbox,
+                                 const int32_t *slots, const int32_t *axtab, const double *cb, int ncb,
+                                 const double *pw, cudaStream_t st);
 cudaError_t launch_cb_copy(const double *reg, const DevBlock *blocks, const CbCopy *list, int n, double *cb,
                            int ncb, cudaStream_t st);
 cudaError_t launch_prolong(double *reg, const DevBlock *blocks, const ProlongRef *list, int n,

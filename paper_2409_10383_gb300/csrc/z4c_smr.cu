@@ -27,6 +27,14 @@ cudaError_t launch_rb_scatter(double *reg, const DevBlock *blocks, const RbCopy 
   return cudaGetLastError();
 }
 
+cudaError_t launch_prolong_boxes(double *reg, const DevBlock *blocks, const PBox *boxes, int nbox,
+                                 const int32_t *slots, const int32_t *axtab, const double *cb, int ncb,
+                                 const double *pw, cudaStream_t st) {
+  if (nbox <= 0) return cudaSuccess;
+  prolong_box_kernel<<<dim3(nbox, NF), 128, 0, st>>>(reg, blocks, boxes, slots, axtab, cb, ncb, pw);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_cb_copy(const double *reg, const DevBlock *blocks, const CbCopy *list, int n, double *cb, int ncb,
                            cudaStream_t st) {
   if (n <= 0) return cudaSuccess;

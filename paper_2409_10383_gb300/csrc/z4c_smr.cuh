@@ -200,4 +200,64 @@ __global__ void prolong_kernel(double *__restrict__ reg, const DevBlock *__restr
         if (p.mask >> (xc + 2 * yc + 4 * zc) & 1) out[zc * e01 + yc * e0 + xc] = acc[zc][yc][xc];
 }
 
+// Prolongation of whole ghost regions (one CTA per box and field): the box's
+// coarse values gathered into shared memory, then x, y and z passes of the
+// 5-point Lagrange sums; the x-pass partial sums are shared by every fine
+// cell with the same x, the y-pass ones by every fine cell with the same
+// (x, y).  Per fine cell the same weights, stencil shift and evaluation order
+// as prolong_kernel, so the values are identical.
+__global__ void __launch_bounds__(128) prolong_box_kernel(double *__restrict__ reg,
+                                                          const DevBlock *__restrict__ blocks,
+                                                          const PBox *__restrict__ boxes,
+                                                          const int32_t *__restrict__ slots,
+                                                          const int32_t *__restrict__ axtab,
+                                                          const double *__restrict__ cb, int ncb,
+                                                          const double *__restrict__ pw) {
+  __shared__ double CY[PB_Y > PB_C ? PB_Y : PB_C];  // coarse box, then the y-pass output
+  __shared__ double X[PB_X];
+  const PBox B = boxes[blockIdx.x];
+  const int f = blockIdx.y;
+  const int f0 = B.nf[0], f1 = B.nf[1], f2 = B.nf[2];
+  const int c0 = B.nc[0], c1 = B.nc[1], c2 = B.nc[2];
+  const double *cf = cb + (int64_t)f * ncb;
+  const int32_t *ax = axtab + B.ax;
+  for (int q = threadIdx.x; q < c0 * c1 * c2; q += blockDim.x) CY[q] = cf[slots[B.tab + q]];
+  __syncthreads();
+  for (int q = threadIdx.x; q < f0 * c1 * c2; q += blockDim.x) {  // [z'][y'][i]
+    const int i = q % f0, r = q / f0;
+    const int32_t e = ax[i];
+    const double *w = pw + (e >> 16);
+    const double *row = CY + r * c0 + (e & 0xffff);
+    double v = 0.0;
+#pragma unroll
+    for (int a = 0; a < 5; ++a) v = fma(w[a], row[a], v);
+    X[q] = v;
+  }
+  __syncthreads();
+  for (int q = threadIdx.x; q < f0 * f1 * c2; q += blockDim.x) {  // [z'][j][i]
+    const int i = q % f0, j = (q / f0) % f1, z = q / (f0 * f1);
+    const int32_t e = ax[f0 + j];
+    const double *w = pw + (e >> 16);
+    const int s = e & 0xffff;
+    double v = 0.0;
+#pragma unroll
+    for (int b = 0; b < 5; ++b) v = fma(w[b], X[(z * c1 + s + b) * f0 + i], v);
+    CY[q] = v;
+  }
+  __syncthreads();
+  const DevBlock &D = blocks[B.dst];
+  double *out = reg + D.off + (int64_t)f * D.S;
+  const int e0 = D.e[0], e1 = D.e[1];
+  for (int q = threadIdx.x; q < f0 * f1 * f2; q += blockDim.x) {
+    const int i = q % f0, j = (q / f0) % f1, k = q / (f0 * f1);
+    const int32_t e = ax[f0 + f1 + k];
+    const double *w = pw + (e >> 16);
+    const int s = e & 0xffff;
+    double v = 0.0;
+#pragma unroll
+    for (int c = 0; c < 5; ++c) v = fma(w[c], CY[((s + c) * f1 + j) * f0 + i], v);
+    out[((B.o[2] + k) * e1 + (B.o[1] + j)) * e0 + (B.o[0] + i)] = v;
+  }
+}
+
 }  // namespace z4c
