@@ -38,19 +38,21 @@ NOMINAL_FP64 = 1.25e12     # GB300 FP64, nominal (profiling recipe)
 L2_BYTES = 129 * 2 ** 20
 
 # Executed FP64 operations per interior cell per stage of the dominant kernel
-# (interior_pre_kernel<6,false>: fused RHS + RK stage + enforcement, mixed
-# derivatives from the pre-pass), from the ncu instruction counters (dadd,
-# dfma, dmul; exact integers per cell) of an 8 x 32^3 order-6 capture
-# (profiles/interior_fp64_single_puncture.md): flops = dadd + dmul + 2 dfma.
-FP64_OPS_PER_CELL_STAGE = {6: dict(dadd=951, dfma=1531, dmul=500)}
-# DRAM bytes per launch of that capture (read + write) per interior cell
-FP64_DRAM_BYTES_PER_CELL = {6: (154618880 + 194336512) / 262144}
-# FP32-RHS kernel (interior_pre_kernel<6,true,OCC>): executed FP32 and FP64
-# operations per interior cell per stage, from the ncu instruction counters
-# of an 8 x 32^3 order-6 capture (profiles/interior_fp32_single_puncture.md);
-# the arithmetic is the same in every occupancy build.
-FP32_OPS_PER_CELL_STAGE = {6: dict(fadd=955, ffma=1447, fmul=524)}
-FP32_F64_RESIDUE_PER_CELL_STAGE = {6: dict(dadd=47, dfma=22, dmul=23)}
+# (interior_pre_kernel<6,false,1,false,72>: fused RHS + RK stage +
+# enforcement, mixed derivatives from the pre-pass, strides of the 72^3
+# storage of a 64^3 block with 4 ghosts), from the ncu instruction counters
+# (dadd, dfma, dmul; exact integers per cell) of a one-block 64^3 order-6
+# capture, stage-1 launch (profiles/interior_fp64_single_puncture.md):
+# flops = dadd + dmul + 2 dfma.
+FP64_OPS_PER_CELL_STAGE = {6: dict(dadd=1038, dfma=1539, dmul=482)}
+# DRAM bytes (read + write) per interior cell of that launch
+FP64_DRAM_BYTES_PER_CELL = {6: (121399296 + 90127104) / 262144}
+# FP32-RHS split schedule (interior_pre_kernel<6,true,4,split,72> storing k
+# + split_epilogue_kernel): executed FP32 operations and the FP64 residue per
+# interior cell per stage, same capture (profiles/interior_fp32_single_puncture.md)
+FP32_OPS_PER_CELL_STAGE = {6: dict(fadd=1044, ffma=1469, fmul=502)}
+FP32_F64_RESIDUE_PER_CELL_STAGE = {6: dict(dadd=47, dfma=22, dmul=25)}
+FP32_DRAM_BYTES_PER_CELL = {6: (62101248 + 4799744 + 77097984 + 28476160) / 262144}
 # algorithmic HBM bytes per zone-cycle (fused 3-register RK4, 22 FP64 fields;
 # the same for the FP32-RHS path, whose state stays FP64)
 ALG_BYTES_PER_ZONE_CYCLE = 352 * 8
@@ -233,11 +235,12 @@ def measure(z4c, torch, workload, prec, args, ws, local):
         flops = (ops["dadd"] + ops["dmul"] + 2 * ops["dfma"]) * cells
         insts = (ops["dadd"] + ops["dmul"] + ops["dfma"]) * cells
         achieved = flops / (interior_ms * 1e-3)
+        ext = int(workload["n"][0][0]) + 2 * int(workload["ghosts"])  # storage extent the kernel is built for
         roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak64 / 1e12, "unit": "TFLOP/s",
                 "frac": achieved / peak64,
                 "traffic": FP64_DRAM_BYTES_PER_CELL[order] * cells,
-                "traffic_note": "ncu dram bytes of an 8 x 32^3 capture scaled by cells",
-                "kernel": f"interior_pre_kernel<{order},false> (fused RHS + RK stage + enforcement)",
+                "traffic_note": "ncu dram bytes of a one-block 64^3 capture (stage 1) scaled by cells",
+                "kernel": f"interior_pre_kernel<{order},false,1,false,{ext}> (fused RHS + RK stage + enforcement)",
                 "peak_source": "measured DFMA throughput (z4c_peak_fma), FMA = 2 flops",
                 "peak_nominal": NOMINAL_FP64 / 1e12,
                 "fp64_issue_frac": insts / (interior_ms * 1e-3) / (peak64 / 2),
@@ -267,8 +270,10 @@ def measure(z4c, torch, workload, prec, args, ws, local):
                     "unit": "T FP64-pipe instructions/s",
                     "peak_source": "measured DFMA instruction rate (z4c_peak_fma FP64 / 2)",
                     "fp64_residue_flops_per_cell_stage": f64 / cells}
-        roof.update({"frac": t[kind] / sec, "limiter": kind, "traffic": None,
-                     "kernel": (f"interior_pre_kernel<{order},true,4,split> + split_epilogue_kernel (FP32 RHS, "
+        roof.update({"frac": t[kind] / sec, "limiter": kind,
+                     "traffic": FP32_DRAM_BYTES_PER_CELL[order] * cells if variant[0] == 4 else None,
+                     "traffic_note": "ncu dram bytes of both split-schedule kernels, one 64^3 block, scaled by cells",
+                     "kernel": (f"interior_pre_kernel<{order},true,4,split,ext> + split_epilogue_kernel (FP32 RHS, "
                                 "FP64 state/RK/enforcement)") if variant[0] == 4 else
                                f"interior_pre_kernel<{order},true,{variant[1]}> (FP32 RHS, FP64 state/RK/enforcement)",
                      "bound_ms_per_launch": {k: v * 1e3 for k, v in t.items()},
