@@ -223,6 +223,36 @@ def test_fp32_rhs_error_budget(oracle, schedule, occupancy):
     assert abs(n32[0] / n64[0] - 1) <= 1e-5, (n32[0], n64[0])
 
 
+def test_fp32_split_and_occupancy_builds_are_bit_identical(oracle):
+    """The pre-pass-schedule FP32 kernel at occupancy 1/2/4 and the split
+    schedule (RHS kernel with extent-specialised strides + stage-update
+    kernel) differ only in organisation: the same arithmetic in the same
+    order, so their RHS and their RK4 steps agree bit for bit.  (The staged
+    schedule 3 reads derivatives back from shared memory, where the compiler
+    fuses multiply-adds differently; it is held to the FP32 error budget
+    against the FP64 oracle in test_fp32_rhs_error_budget instead.)  16^3
+    blocks use the extent-24 kernels."""
+    w = H.small_workload("puncture", 6, (2, 1, 1), 16)
+    m = H.oracle_mesh(oracle, w)
+    u = m.initial_data(w["id_kind"], w["id_par"])
+    m.fill_ghosts(u)
+    H.perturb(m, u, 77, 1e-3)
+    dt = 0.25 * float(w["h"][0])
+    rhs, steps = {}, {}
+    for sch, occ in ((2, 1), (2, 2), (2, 4), (4, 4)):
+        g = H.gpu_ctx(w, precision=32, schedule=sch)
+        g.z4c_set_variant(sch, occ)
+        g.z4c_set_state(u, reg=1)
+        rhs[(sch, occ)] = g.z4c_rhs(1).cpu().numpy().copy()
+        g.z4c_set_state(u)
+        g.z4c_rk4_step(dt, 2)
+        steps[(sch, occ)] = g.z4c_get_state()
+        g.close()
+    for v in rhs:
+        assert np.array_equal(rhs[v], rhs[(2, 1)]), v
+        assert np.array_equal(steps[v], steps[(2, 1)]), v
+
+
 def test_autotune_keeps_state_and_picks_a_built_variant(oracle):
     """The autotuner runs only stage 1 (U0 unchanged) and leaves a valid
     variant; evolution after tuning still matches the oracle."""
