@@ -71,6 +71,8 @@ def lib():
             "orc_constraints": (None, [mp, P, D, P, P]),
             "orc_initial_data": (None, [mp, P, I, P]),
             "orc_set_threads": (I, [I]),
+            "orc_block_indicators": (None, [mp, P, P, P]),
+            "orc_track_punctures": (I, [mp, P, I, P, D, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(_lib, name)
@@ -227,6 +229,23 @@ class Mesh:
         lib().orc_constraints(ctypes.byref(self._c), _ptr(u), float(r_mask),
                               _ptr(pc) if pc is not None else None, _ptr(norms))
         return norms, pc
+
+    def block_indicators(self, u: np.ndarray):
+        """Per block (min chi, max |grad chi|) over interior cells; the
+        ghosts of u must be filled."""
+        cmin, gmax = np.zeros(self.nblocks), np.zeros(self.nblocks)
+        lib().orc_block_indicators(ctypes.byref(self._c), _ptr(u), _ptr(cmin), _ptr(gmax))
+        return cmin, gmax
+
+    def track_punctures(self, u: np.ndarray, xyz, dt: float):
+        """One tracker step of each puncture: (new positions, beta at the old
+        ones); the ghosts of u must be filled."""
+        x = np.ascontiguousarray(np.asarray(xyz, dtype=np.float64).reshape(-1, 3)).copy()
+        beta = np.zeros_like(x)
+        if lib().orc_track_punctures(ctypes.byref(self._c), _ptr(u), len(x), _ptr(x), float(dt),
+                                     _ptr(beta)) != 0:
+            raise ValueError("a puncture lies outside every block")
+        return x, beta
 
 
 def fd(kind: int, order: int, f: np.ndarray, i: int, j: int, k: int, dir1: int, dir2: int = 0,

@@ -54,6 +54,11 @@
  *   R13 along a non-periodic axis the 5 coarse cells of a prolongation
  *      stencil are shifted (by at most 2) to lie inside the domain, as the
  *      restriction stencil is kept inside the active region.
+ *   R17 refinement indicators (Sec. 3.2): per block, min chi and max |grad
+ *      chi| over interior cells, the gradient by the block's centred
+ *      first-derivative stencil.
+ *   R18 puncture tracker (Sec. 3.3): dx/dt = -beta(x), one forward-Euler step
+ *      per call, beta by 4-point Lagrange interpolation per axis.
  *
  * Field order (fixed): chi, gt_xx gt_xy gt_xz gt_yy gt_yz gt_zz, Khat,
  * At_xx .. At_zz, Gam^x Gam^y Gam^z, Theta, alpha, beta^x beta^y beta^z.
@@ -1146,4 +1151,97 @@ int orc_set_threads(int n) {
   (void)n;
   return 1;
 #endif
+}
+
+/* ------------------------------------------------------------------ */
+/* diagnostics beside the step (Sec. 3.2 refinement criteria, Sec. 3.3  */
+/* puncture trackers)                                                   */
+/* ------------------------------------------------------------------ */
+
+/* Refinement indicators of every block (Sec. 3.2): over the block's
+ * interior cells, chi_min[b] = min chi (the chi-min criterion) and
+ * dchi_max[b] = max |grad chi| (the d-chi criterion), the gradient by the
+ * centred first-derivative stencil of order m->order (reading R17).  Ghost
+ * cells must be filled. */
+void orc_block_indicators(const orc_mesh *m, const double *u, double *chi_min, double *dchi_max) {
+  for (int b = 0; b < m->nblocks; ++b) {
+    const long e0 = ext(m, b, 0), e1 = ext(m, b, 1);
+    const long st[3] = {1, e0, e0 * e1};
+    const double *chi = u + blk_offset(m, b) + (long)F_CHI * e0 * e1 * ext(m, b, 2);
+    const int g = m->ghosts;
+    double mn = INFINITY, mx = 0.0;
+    for (int k = g; k < g + m->n[3 * b + 2]; ++k)
+      for (int j = g; j < g + m->n[3 * b + 1]; ++j)
+        for (int i = g; i < g + m->n[3 * b]; ++i) {
+          const double *p = chi + ((long)k * e1 + j) * e0 + i;
+          if (*p < mn) mn = *p;
+          double s = 0.0;
+          for (int d = 0; d < 3; ++d) {
+            const double q = d1(p, st[d], m->order, m->h[b]);
+            s += q * q;
+          }
+          const double a = sqrt(s);
+          if (a > mx) mx = a;
+        }
+    chi_min[b] = mn;
+    dchi_max[b] = mx;
+  }
+}
+
+/* The first block (in block order) whose closed box [lo, lo + n h] contains
+ * x, within 1e-12 h; -1 if none. */
+static int block_containing(const orc_mesh *m, const double x[3]) {
+  for (int b = 0; b < m->nblocks; ++b) {
+    int in = 1;
+    for (int d = 0; d < 3; ++d) {
+      const double t = (x[d] - m->lo[3 * b + d]) / m->h[b];
+      in &= t >= -1e-12 && t <= m->n[3 * b + d] + 1e-12;
+    }
+    if (in) return b;
+  }
+  return -1;
+}
+
+/* Puncture tracker (Sec. 3.3): a puncture moves with dx/dt = -beta(x).  One
+ * forward-Euler step x <- x - dt beta(x) per call (reading R18), beta from
+ * block_containing(x) by 4-point Lagrange interpolation per axis (3D tensor
+ * product) over the cell centres i0 .. i0 + 3, i0 = floor((x - lo)/h - 1/2)
+ * - 1.  Ghost cells must be filled.  beta_out (nullable): the 3 components
+ * per puncture.  Returns 0, or -1 if a puncture lies in no block. */
+int orc_track_punctures(const orc_mesh *m, const double *u, int np, double *xyz, double dt,
+                        double *beta_out) {
+  for (int q = 0; q < np; ++q) {
+    double x[3] = {xyz[3 * q], xyz[3 * q + 1], xyz[3 * q + 2]};
+    if (m->periodic) wrap(m, x);
+    const int b = block_containing(m, x);
+    if (b < 0) return -1;
+    const long e0 = ext(m, b, 0), e1 = ext(m, b, 1), S = e0 * e1 * ext(m, b, 2);
+    const double h = m->h[b];
+    long s0[3];
+    double w[3][4];
+    for (int d = 0; d < 3; ++d) {
+      const double lo = m->lo[3 * b + d];
+      const long i0 = (long)floor((x[d] - lo) / h - 0.5) - 1;
+      s0[d] = i0 + m->ghosts;
+      double xs[4];
+      for (int a = 0; a < 4; ++a) xs[a] = lo + (i0 + a + 0.5) * h;
+      for (int a = 0; a < 4; ++a) w[d][a] = lagrange(xs, 4, a, x[d]);
+    }
+    const double *base = u + blk_offset(m, b);
+    double beta[3];
+    for (int c = 0; c < 3; ++c) {
+      const double *f = base + (long)(F_BETAX + c) * S;
+      double v = 0.0;
+      for (int kz = 0; kz < 4; ++kz)
+        for (int jy = 0; jy < 4; ++jy)
+          for (int ix = 0; ix < 4; ++ix)
+            v += w[2][kz] * w[1][jy] * w[0][ix] * f[((s0[2] + kz) * e1 + s0[1] + jy) * e0 + s0[0] + ix];
+      beta[c] = v;
+    }
+    for (int d = 0; d < 3; ++d) {
+      xyz[3 * q + d] -= dt * beta[d];
+      if (beta_out) beta_out[3 * q + d] = beta[d];
+    }
+  }
+  return 0;
 }
