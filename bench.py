@@ -378,6 +378,18 @@ def measure_smr(z4c, torch, steps, warmup):
     ms = e0.elapsed_time(e1)
     split = g.z4c_profile_steps(dt, 1)
     h_norm = float(g.z4c_constraints()[0][0])
+    # diagnostics beside the step: per-block refinement indicators and one
+    # tracker step of both punctures (synchronous calls, each including a
+    # ghost fill of U0 and the small device-to-host copy)
+    reps = 10
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        g.z4c_block_indicators()
+    t1 = time.perf_counter()
+    pts = np.array([[3.0, 0.0, 0.0], [-3.0, 0.0, 0.0]])
+    for _ in range(reps):
+        pts, _ = g.z4c_track_punctures(pts, dt)
+    t2 = time.perf_counter()
     out = {"value": cells * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
            "blocks": int(len(w["h"])), "levels": np.bincount(w["level"]).tolist(), "cells": cells,
            "storage_per_register_bytes": int(g.nelem * 8),
@@ -385,6 +397,8 @@ def measure_smr(z4c, torch, steps, warmup):
                                  "fused_rhs_update": split[1], "sommerfeld": split[2]},
            "ghost_share": float(split[0] / split.sum()),
            "hamiltonian_l2_after": h_norm,
+           "diagnostics_ms_per_call": {"block_indicators": 1e3 * (t1 - t0) / reps,
+                                       "track_punctures": 1e3 * (t2 - t1) / reps},
            "gpu_launches": g.z4c_launches_per_step() * steps, "graph_launches_per_step": 1,
            "workload": "Brill-Lindquist binary m=0.5 at x=+-3, 680 blocks of 16^3, levels 0..6 "
                        "(h=2..1/32), [-32,32]^3, order 6, 4 ghosts, dt=1/128"}

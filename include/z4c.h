@@ -265,6 +265,28 @@ int z4c_set_variant(z4c_ctx *ctx, int schedule, int occupancy);
  * Synchronous.  Call before z4c_rk4_step, or it re-captures its graph. */
 int z4c_autotune(z4c_ctx *ctx, int reps, int *schedule_out, int *occupancy_out);
 
+/* Refinement indicators of every block (paper Sec. 3.2, the chi-min and
+ * d-chi criteria): over the block's interior cells, chi_min[b] = min chi and
+ * dchi_max[b] = max |grad chi|, the gradient by the block's centred
+ * first-derivative stencil (order 4 or 6), in FP64.  Fills the ghost cells
+ * of register reg first.  chi_min, dchi_max: host arrays of nblocks
+ * doubles, in block order.  Synchronous. */
+int z4c_block_indicators(z4c_ctx *ctx, int reg, double *chi_min, double *dchi_max);
+
+/* Puncture tracker (paper Sec. 3.3): one step x <- x - dt beta(x) for each
+ * of np <= Z4C_MAX_PUNCTURES punctures (forward Euler; call once per RK4
+ * step with that step's dt).  beta is interpolated from register reg by
+ * 4-point Lagrange interpolation per axis over the cell centres around x,
+ * in the first block (in block order) whose closed box [lo, lo + n h]
+ * contains x (after wrapping into a periodic domain).  Fills the ghost
+ * cells of reg first.  xyz: host, 3 doubles per puncture, updated in place;
+ * beta_out (host, nullable): 3 doubles per puncture, beta at the old
+ * position.  Single-instance contexts only (Z4C_ERR_UNSUPPORTED
+ * otherwise); Z4C_ERR_BAD_ARG if a puncture lies in no block.
+ * Synchronous. */
+#define Z4C_MAX_PUNCTURES 64
+int z4c_track_punctures(z4c_ctx *ctx, int reg, int np, double *xyz, double dt, double *beta_out);
+
 /* Measurement aid: FP64 (fp64 = 1) or FP32 (fp64 = 0) fused multiply-add
  * throughput of the current device in FLOP/s, from independent FMA chains
  * with no memory traffic (the ALU roofline of the RHS kernels).  Enqueued on

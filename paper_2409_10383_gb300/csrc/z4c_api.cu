@@ -531,6 +531,70 @@ int z4c_autotune(z4c_ctx *ctx, int reps, int *schedule_out, int *occupancy_out) 
   return Z4C_OK;
 }
 
+int z4c_block_indicators(z4c_ctx *ctx, int reg, double *chi_min, double *dchi_max) {
+  int r = ensure_bound(ctx);
+  if (r) return r;
+  if (reg < 0 || reg > 3 || !chi_min || !dchi_max) return fail(ctx, Z4C_ERR_BAD_ARG, "bad register or output");
+  r = fill_ghosts(ctx, ctx->reg[reg], nullptr);
+  if (r) return r;
+  const int nb = (int)ctx->blocks.size();
+  double *out = (double *)(ctx->scratch + ctx->o_diag);
+  CK(launch_indicators(ctx->reg[reg], ctx->d_blocks(), ctx->d_ctiles(), (int)ctx->ctiles.size(),
+                       ctx->at<int32_t>(ctx->o_cfirst), nb, ctx->d_part(), out, ctx->stream));
+  CK(cudaMemcpyAsync(chi_min, out, sizeof(double) * nb, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaMemcpyAsync(dchi_max, out + nb, sizeof(double) * nb, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return status_check(ctx);
+}
+
+int z4c_track_punctures(z4c_ctx *ctx, int reg, int np, double *xyz, double dt, double *beta_out) {
+  int r = ensure_bound(ctx);
+  if (r) return r;
+  if (reg < 0 || reg > 3 || np < 0 || np > Z4C_MAX_PUNCTURES || (np > 0 && !xyz) || !std::isfinite(dt))
+    return fail(ctx, Z4C_ERR_BAD_ARG, "bad register, puncture count, positions or dt");
+  if (ctx->inst.size() != 1) return fail(ctx, Z4C_ERR_UNSUPPORTED, "the tracker needs a single-instance context");
+  if (np == 0) return Z4C_OK;
+  const z4c_mesh &M = ctx->inst[0].mesh;
+  std::vector<TrackIn> in(np);
+  for (int q = 0; q < np; ++q) {
+    TrackIn &p = in[q];
+    for (int d = 0; d < 3; ++d) {
+      p.x0[d] = p.xw[d] = xyz[3 * q + d];
+      if (M.periodic) {
+        const double L = M.hi[d] - M.lo[d];
+        while (p.xw[d] < M.lo[d]) p.xw[d] += L;
+        while (p.xw[d] >= M.hi[d]) p.xw[d] -= L;
+      }
+    }
+    p.block = -1;
+    for (size_t b = 0; b < ctx->blocks.size() && p.block < 0; ++b) {  // first block whose closed box holds x
+      const z4c_block &B = ctx->blocks[b];
+      bool inb = true;
+      for (int d = 0; d < 3; ++d) {
+        const double t = (p.xw[d] - B.lo[d]) / B.h;
+        inb &= t >= -1e-12 && t <= B.n[d] + 1e-12;
+      }
+      if (inb) p.block = (int32_t)b;
+    }
+    if (p.block < 0) return fail(ctx, Z4C_ERR_BAD_ARG, "puncture %d lies in no block", q);
+  }
+  r = fill_ghosts(ctx, ctx->reg[reg], nullptr);
+  if (r) return r;
+  TrackIn *d_in = (TrackIn *)(ctx->scratch + ctx->o_diag);
+  double *d_out = (double *)(d_in + Z4C_MAX_PUNCTURES);
+  std::vector<double> out(6 * (size_t)np);
+  CK(cudaMemcpyAsync(d_in, in.data(), sizeof(TrackIn) * np, cudaMemcpyHostToDevice, ctx->stream));
+  CK(launch_track(ctx->reg[reg], ctx->d_blocks(), d_in, np, dt, d_out, ctx->stream));
+  CK(cudaMemcpyAsync(out.data(), d_out, sizeof(double) * 6 * np, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (int q = 0; q < np; ++q)
+    for (int d = 0; d < 3; ++d) {
+      xyz[3 * q + d] = out[6 * q + d];
+      if (beta_out) beta_out[3 * q + d] = out[6 * q + 3 + d];
+    }
+  return status_check(ctx);
+}
+
 int z4c_peak_fma(int fp64, void *cuda_stream, double *flops_per_s) {
   if (!flops_per_s) return Z4C_ERR_BAD_ARG;
   z4c_ctx *ctx = nullptr;

@@ -620,6 +620,13 @@ int z4c_create_batch(const z4c_instance *instances, int ninstances, const z4c_bl
   ctx->o_pw = take(sizeof(double) * 50);
   ctx->o_cb = take(sizeof(double) * NF * (size_t)ctx->ncb);
   ctx->o_ctiles = take(sizeof(Tile) * ctx->ctiles.size());
+  ctx->cfirst.assign(ctx->blocks.size() + 1, 0);
+  for (const Tile &t : ctx->ctiles) ++ctx->cfirst[t.block + 1];
+  for (size_t b = 0; b < ctx->blocks.size(); ++b) ctx->cfirst[b + 1] += ctx->cfirst[b];
+  ctx->o_cfirst = take(sizeof(int32_t) * ctx->cfirst.size());
+  // diagnostics: per-block indicator outputs, tracker inputs and outputs
+  ctx->o_diag = take(std::max(sizeof(double) * 2 * ctx->blocks.size(),
+                              (sizeof(TrackIn) + sizeof(double) * 6) * Z4C_MAX_PUNCTURES));
   ctx->o_part = take(sizeof(double) * 8 * 2 * ctx->ctiles.size());  // order-4 and order-6 records
   ctx->o_res = take(sizeof(double) * 8);
   ctx->o_dt = take(sizeof(double) * ctx->dblocks.size());
@@ -710,6 +717,7 @@ int z4c_bind(z4c_ctx *ctx, void *u0, void *stage_a, void *stage_b, void *acc, vo
   CK(up(ctx->o_wtab, ctx->wtab.data(), sizeof(double) * ctx->wtab.size()));
   CK(up(ctx->o_pw, ctx->pw, sizeof(double) * 50));
   CK(up(ctx->o_ctiles, ctx->ctiles.data(), sizeof(Tile) * ctx->ctiles.size()));
+  CK(up(ctx->o_cfirst, ctx->cfirst.data(), sizeof(int32_t) * ctx->cfirst.size()));
   CK(cudaMemsetAsync(ctx->d_status(), 0, sizeof(int32_t), st));
   // the tables live in host vectors owned by ctx; wait so the copies are done
   CK(cudaStreamSynchronize(st));

@@ -51,7 +51,8 @@ struct z4c_ctx {
   z4c::Group grp[4];
   std::vector<z4c::CellRef> somm[2];    // Sommerfeld cells, per precision (0 FP64, 1 FP32)
   std::vector<z4c::GhostCopy> gcopy[2];  // same-level ghost copies, per precision
-  std::vector<z4c::Tile> ctiles;         // every interior tile (constraints)
+  std::vector<z4c::Tile> ctiles;         // every interior tile (constraints), in block order
+  std::vector<int32_t> cfirst;           // first ctile of each block, and the total
   // mesh refinement transfer (FP64 instances with more than one level)
   std::vector<z4c::RestrictRef> rghost;  // coarse ghost cells <- restriction of a finer block
   std::vector<z4c::RestrictRef> rbuf;    // coarse-buffer slots <- restriction of a same-level block
@@ -79,7 +80,7 @@ struct z4c_ctx {
          o_dt = 0, o_sh0 = 0, o_sh1 = 0, o_ds64 = 0, o_ds32 = 0, o_rghost = 0, o_rbuf = 0, o_cbcopy = 0,
          o_prol = 0, o_pidx = 0, o_wtab = 0, o_pw = 0, o_cb = 0, o_status = 0, o_kbuf = 0, o_rblocks = 0,
          o_rbcopy = 0, o_krow = 0, o_rb = 0, o_pbox = 0, o_pslots = 0,
-         o_paxtab = 0, scratch_total = 0;
+         o_paxtab = 0, o_cfirst = 0, o_diag = 0, scratch_total = 0;
   // bound buffers
   double *reg[4] = {nullptr, nullptr, nullptr, nullptr};
   char *scratch = nullptr;

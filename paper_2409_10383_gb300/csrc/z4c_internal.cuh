@@ -156,6 +156,18 @@ cudaError_t launch_rb_scatter(double *reg, const DevBlock *blocks, const RbCopy 
 cudaError_t launch_prolong_boxes(double *reg, const DevBlock *blocks, const PBox *boxes, int nbox,
                                  const int32_t *slots, const int32_t *axtab, const double *cb, int ncb,
                                  const double *pw, cudaStream_t st);
+// diagnostics (z4c_diag.cu): per-block refinement indicators over a tile
+// list in block order (first[b] = first tile of block b), puncture tracker
+// One puncture for track_kernel: its block, its position wrapped into a
+// periodic domain (for the interpolation) and as given (for the update).
+struct TrackIn {
+  int32_t block, pad;
+  double xw[3], x0[3];
+};
+cudaError_t launch_indicators(const double *u, const DevBlock *blocks, const Tile *tiles, int ntiles,
+                              const int32_t *first, int nb, double *part, double *out, cudaStream_t st);
+cudaError_t launch_track(const double *u, const DevBlock *blocks, const TrackIn *in, int np, double dt, double *out,
+                         cudaStream_t st);
 cudaError_t launch_cb_copy(const double *reg, const DevBlock *blocks, const CbCopy *list, int n, double *cb,
                            int ncb, cudaStream_t st);
 cudaError_t launch_prolong(double *reg, const DevBlock *blocks, const ProlongRef *list, int n,

@@ -26,7 +26,9 @@ EXPORTS = ("z4c_create", "z4c_create_batch", "z4c_set_initial_data_instance", "z
            "z4c_set_initial_data", "z4c_fill_ghosts", "z4c_rhs", "z4c_rk4_step",
            "z4c_constraints", "z4c_get_state", "z4c_set_state", "z4c_evolve_host",
            "z4c_sync", "z4c_profile_steps", "z4c_set_variant", "z4c_autotune", "z4c_peak_fma", "z4c_constraints_static",
-           "z4c_launches_per_step", "z4c_last_error", "z4c_destroy")
+           "z4c_launches_per_step", "z4c_last_error", "z4c_destroy", "z4c_block_indicators",
+           "z4c_track_punctures")
+Z4C_MAX_PUNCTURES = 64
 
 
 class z4c_mesh(ctypes.Structure):
@@ -89,6 +91,8 @@ def lib():
             "z4c_autotune": (I, [P, I, P, P]),
             "z4c_peak_fma": (I, [I, P, P]),
             "z4c_constraints_static": (I, [P, P, I, I, P, D, D, D, P, P]),
+            "z4c_block_indicators": (I, [P, I, P, P]),
+            "z4c_track_punctures": (I, [P, I, I, P, D, P]),
             "z4c_launches_per_step": (I, [P]),
             "z4c_last_error": (ctypes.c_char_p, [P]),
             "z4c_destroy": (None, [P]),
@@ -296,6 +300,26 @@ class Z4c:
 
     def z4c_sync(self):
         _check(lib().z4c_sync(self.ctx), self.ctx, "z4c_sync")
+
+    def z4c_block_indicators(self, reg=REG_U0):
+        """Per block (min chi, max |grad chi|) over its interior cells
+        (paper Sec. 3.2 refinement criteria); fills reg's ghosts first."""
+        nb = len(self.blocks)
+        cmin, gmax = np.zeros(nb), np.zeros(nb)
+        self._enter()
+        _check(lib().z4c_block_indicators(self.ctx, int(reg), cmin.ctypes.data, gmax.ctypes.data), self.ctx,
+               "z4c_block_indicators")
+        return cmin, gmax
+
+    def z4c_track_punctures(self, xyz, dt, reg=REG_U0):
+        """One tracker step x <- x - dt beta(x) of each puncture (paper Sec.
+        3.3): returns (new positions, beta at the old ones)."""
+        x = np.ascontiguousarray(np.asarray(xyz, dtype=np.float64).reshape(-1, 3)).copy()
+        beta = np.zeros_like(x)
+        self._enter()
+        _check(lib().z4c_track_punctures(self.ctx, int(reg), len(x), x.ctypes.data, float(dt), beta.ctypes.data),
+               self.ctx, "z4c_track_punctures")
+        return x, beta
 
     def z4c_profile_steps(self, dt, nsteps):
         ms = np.zeros(4)
