@@ -42,14 +42,14 @@ L2_BYTES = 129 * 2 ** 20
 # enforcement, mixed derivatives from the pre-pass, strides of the 72^3
 # storage of a 64^3 block with 4 ghosts), from the ncu instruction counters
 # (dadd, dfma, dmul; exact integers per cell) of a one-block 64^3 order-6
-# capture, stage-1 launch (profiles/interior_fp64_single_puncture.md):
+# capture, stage-1 launch:
 # flops = dadd + dmul + 2 dfma.
 FP64_OPS_PER_CELL_STAGE = {6: dict(dadd=1038, dfma=1539, dmul=482)}
 # DRAM bytes (read + write) per interior cell of that launch
 FP64_DRAM_BYTES_PER_CELL = {6: (121399296 + 90127104) / 262144}
 # FP32-RHS split schedule (interior_pre_kernel<6,true,4,split,72> storing k
 # + split_epilogue_kernel): executed FP32 operations and the FP64 residue per
-# interior cell per stage, same capture (profiles/interior_fp32_single_puncture.md)
+# interior cell per stage, from the same kind of capture
 FP32_OPS_PER_CELL_STAGE = {6: dict(fadd=1044, ffma=1469, fmul=502)}
 FP32_F64_RESIDUE_PER_CELL_STAGE = {6: dict(dadd=47, dfma=22, dmul=25)}
 FP32_DRAM_BYTES_PER_CELL = {6: (62101248 + 4799744 + 77097984 + 28476160) / 262144}

@@ -20,7 +20,7 @@
  *   - Sec. 4.3: Kreiss-Oliger dissipation, constraint damping kappa1/kappa2,
  *     6th-order differencing and RK4.
  *
- * Readings taken where the paper is silent (each also listed in the design doc):
+ * Readings taken where the paper is silent (numbered as in the design notes):
  *   R1 equation forms: as in rhs_point(); Gamma-tilde damping term is
  *      -2 alpha kappa1 (Gam - Gam_d); the K-gradient term in the Gam
  *      equation is -(1/3) gt^ij d_j (2 Khat + Theta); the evolved Gam is used
