@@ -117,10 +117,11 @@ struct FD<6> {
 };
 
 // Kreiss-Oliger dissipation (all three directions) plus lopsided advection
-// beta^k d_k f of one field from one load of its 3 x (2KW+1)-point cross:
-// the lopsided stencil takes its points from the same loads, mirrored when
-// beta^k < 0 (the mirror image of the beta > 0 stencil).  Returns the
-// unscaled KO sum (times sko by the caller) and adds |beta^k| slop D_lop to adv.
+// beta^k d_k f of one field over its 3 x (2KW+1)-point cross: the lopsided
+// stencil takes its points from the same cross, mirrored when beta^k < 0
+// (the mirror image of the beta > 0 stencil).  lop() and ko() evaluate them
+// from loaded points (unscaled: times slop |beta^k| and sko by the caller);
+// kcoef()/lcoef() give the same coefficients for KoAdvWeights below.
 template <int ORD>
 struct KoAdv;
 template <>
@@ -136,6 +137,14 @@ struct KoAdv<4> {
   template <class R>
   __device__ static R ko(R c, const R *p) {          // p[m-1] = sum over directions of f(+m) + f(-m)
     return fma(c, R(-60), fma(p[0], R(15), fma(p[1], R(-6), p[2])));
+  }
+  // per-direction KO coefficient of f(+-m) and lopsided coefficient of f(m)
+  // (beta > 0 orientation; zero outside -1..3), in units of sko and slop
+  __host__ __device__ static constexpr int kcoef(int m) {
+    return m == 0 ? -20 : m == 1 ? 15 : m == 2 ? -6 : 1;
+  }
+  __host__ __device__ static constexpr int lcoef(int m) {
+    return m == -1 ? -3 : m == 0 ? -10 : m == 1 ? 18 : m == 2 ? -6 : m == 3 ? 1 : 0;
   }
 };
 template <>
@@ -153,35 +162,85 @@ struct KoAdv<6> {
   __device__ static R ko(R c, const R *p) {
     return fma(c, R(210), fma(p[0], R(-56), fma(p[1], R(28), fma(p[2], R(-8), p[3]))));
   }
+  __host__ __device__ static constexpr int kcoef(int m) {
+    return m == 0 ? 70 : m == 1 ? -56 : m == 2 ? 28 : m == 3 ? -8 : 1;
+  }
+  __host__ __device__ static constexpr int lcoef(int m) {
+    return m == -2 ? 2 : m == -1 ? -24 : m == 0 ? -35 : m == 1 ? 80 : m == 2 ? -30 : m == 3 ? 8
+                       : m == 4 ? -1 : 0;
+  }
 };
 
-template <int ORD, class R, class S_>
-__device__ __forceinline__ R ko_adv(const S_ &s, int f, const int st[3], const bool up[3], const R ab[3],
-                                    R sko) {
-  using K = KoAdv<ORD>;
-  constexpr int W = K::KW;
-  const R c = s.at(f, 0);
-  R pairs[W];
+// The same two operators as one stencil per direction.  KO and the lopsided
+// derivative act on the same points of each field, and their coefficients
+// depend on the cell (sko, |beta^d| slop, the sign of beta^d) but not on the
+// field: w[d][.] holds, per direction d, the coefficient of f(m st_d) in
+// sko KO_d + |beta^d| slop Lop_d for m = -W..-1 (index m + W) and m = 1..W
+// (index m + W - 1), the lopsided stencil mirrored for beta^d < 0; w0 is the
+// centre coefficient summed over the three directions.  Formed once per
+// cell, then each field costs 2W DFMA per direction instead of the pair sums,
+// the lopsided sums and the per-point orientation selects of ko_adv.
+template <int ORD, class R>
+struct KoAdvWeights {
+  static constexpr int W = KoAdv<ORD>::KW;
+  R w[3][2 * W];
+  R w0;
+  __device__ __forceinline__ KoAdvWeights(const bool up[3], const R ab[3], R sko) {
+    using K = KoAdv<ORD>;
+    R kw[W + 1];
 #pragma unroll
-  for (int m = 0; m < W; ++m) pairs[m] = R(0);
-  R adv = R(0);
+    for (int m = 0; m <= W; ++m) kw[m] = sko * R(K::kcoef(m));
+    w0 = fma(ab[0] + ab[1] + ab[2], R(K::lcoef(0)), R(3) * kw[0]);
 #pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    R x[2 * W + 1];
+    for (int d = 0; d < 3; ++d) {
 #pragma unroll
-    for (int m = -W; m <= W; ++m) x[m + W] = m == 0 ? c : s.at(f, m * st[d]);
-#pragma unroll
-    for (int m = 1; m <= W; ++m) pairs[m - 1] += x[W + m] + x[W - m];
-    R v[K::LN];
-#pragma unroll
-    for (int q = 0; q < K::LN; ++q) {
-      const int m = q + K::LOFF;
-      v[q] = up[d] ? x[W + m] : x[W - m];
+      for (int m = 1; m <= W; ++m) {
+        const R lp = R(K::lcoef(m)), lm = R(K::lcoef(-m));
+        w[d][W + m - 1] = fma(ab[d], up[d] ? lp : lm, kw[m]);
+        w[d][W - m] = fma(ab[d], up[d] ? lm : lp, kw[m]);
+      }
     }
-    adv = fma(ab[d], K::lop(v), adv);
   }
-  return fma(K::ko(c, pairs), sko, adv);
-}
+  // acc + (KO + advection) of field f: one accumulation chain per direction
+  template <class S_>
+  __device__ __forceinline__ R apply(const S_ &s, int f, const int st[3], R acc) const {
+    R a[3];
+    a[0] = fma(w0, s.at(f, 0), acc);
+    a[1] = w[1][0] * s.at(f, -W * st[1]);
+    a[2] = w[2][0] * s.at(f, -W * st[2]);
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+#pragma unroll
+      for (int m = -W; m <= W; ++m) {
+        if (m == 0 || (d > 0 && m == -W)) continue;
+        a[d] = fma(w[d][m < 0 ? m + W : m + W - 1], s.at(f, m * st[d]), a[d]);
+      }
+    }
+    return a[0] + (a[1] + a[2]);
+  }
+  // The same sum written with the centre subtracted,
+  // sum_{d, m != 0} w[d][m] (f(m st_d) - f(0)): both stencils annihilate
+  // constants, so the centre coefficient drops out and a field that is
+  // constant along a direction contributes exactly zero there.  Used in FP32,
+  // where the rounded weights would otherwise leave a residue of
+  // eps |f| sko per direction (the FP32 pipe has the slack for the
+  // subtractions; the FP64 path, bound by its pipe, takes apply()).
+  template <class S_>
+  __device__ __forceinline__ R apply_diff(const S_ &s, int f, const int st[3]) const {
+    const R c = s.at(f, 0);
+    R a[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      a[d] = w[d][0] * (s.at(f, -W * st[d]) - c);
+#pragma unroll
+      for (int m = -W + 1; m <= W; ++m) {
+        if (m == 0) continue;
+        a[d] = fma(w[d][m < 0 ? m + W : m + W - 1], s.at(f, m * st[d]) - c, a[d]);
+      }
+    }
+    return a[0] + (a[1] + a[2]);
+  }
+};
 
 // Scale factors of one block in precision R.
 template <class R>
@@ -209,7 +268,7 @@ struct Phys {
 // stencil each (the tensor-product definition, evaluated in two passes).
 template <int ORD, class R, class SRC>
 struct Direct {
-  static constexpr bool kStagedKO = false;  // KO / advection evaluated from s by ko_adv
+  static constexpr bool kStagedKO = false;  // KO / advection evaluated from s by KoAdvWeights
   const SRC &s;
   const int *st;
   Scales<R> sc;
@@ -545,6 +604,7 @@ __device__ __forceinline__ void rhs_point(const SRC &s, const DV &dv, const int 
       up[d] = beta[d] >= R(0);
       ab[d] = fabs(beta[d]) * sc.slop;
     }
+    const KoAdvWeights<ORD, R> kaw(up, ab, sc.sko);
     // one field at a time (an unrolled loop exceeds the register budget)
     if constexpr (sizeof(R) == 4) {
       // FP32: the result goes to a shared-memory slot per field and cell, so
@@ -554,7 +614,7 @@ __device__ __forceinline__ void rhs_point(const SRC &s, const DV &dv, const int 
       const int tid = threadIdx.y * TX + threadIdx.x;
 #pragma unroll 1
       for (int f = 0; f < NF; ++f)
-        kko[f][tid] = (!p.shift && f >= BETAX) ? R(0) : ko_adv<ORD>(s, f, st, up, ab, sc.sko);
+        kko[f][tid] = (!p.shift && f >= BETAX) ? R(0) : kaw.apply_diff(s, f, st);
 #pragma unroll
       for (int f = 0; f < NF; ++f) k[f] += kko[f][tid];
     } else {
@@ -562,7 +622,7 @@ __device__ __forceinline__ void rhs_point(const SRC &s, const DV &dv, const int 
 #pragma unroll 1
       for (int f = 0; f < NF; ++f) {
         if (!p.shift && f >= BETAX) continue;
-        k[f] += ko_adv<ORD>(s, f, st, up, ab, sc.sko);
+        k[f] = kaw.apply(s, f, st, k[f]);
       }
     }
   }

@@ -188,7 +188,7 @@ __device__ __forceinline__ void stage_field(const float *__restrict__ box, float
     }
     ds[(SL_MIX + 3 * Q + 2) * STAGE_NT + tid] = d1v<ORD>(p, q) * sc.s1;
   }
-  // KO dissipation and lopsided advection (as ko_adv)
+  // KO dissipation and lopsided advection (KoAdv::ko and KoAdv::lop)
   float pairs[KW];
 #pragma unroll
   for (int m = 0; m < KW; ++m) pairs[m] = 0.f;
