@@ -29,11 +29,15 @@
  *      final state) has the algebraic constraints enforced, then ghosts
  *      filled before its right-hand side is evaluated.
  *   R3 KO dissipation per direction: sigma (-1)^(N+1) / (2^(2N) h) times the
- *      centred 2N-th undivided difference, N = 3 (4th order) or 4 (6th).
+ *      centred 2N-th undivided difference, N = order/2 + 1 (2 for 2nd order,
+ *      3 for 4th, 4 for 6th), so that the stencil reaches exactly the ghost
+ *      width order/2 + 1.
  *   R4 mixed second derivatives are the tensor product of the centred first
  *      derivative stencils.
  *   R5 lopsided advection stencils for beta^k >= 0 lean towards +k; for
- *      beta^k < 0 the mirror image.
+ *      beta^k < 0 the mirror image.  Order p uses offsets -(p/2-1)..p/2+1:
+ *      -2..4 (6th), -1..3 (4th) and 0..2 (2nd, the one-sided 3-point
+ *      difference; reading R19).
  *   R6 chi_g = max(chi, chi_floor) wherever 1/chi appears; chi itself is
  *      never clipped.
  *   R7 Sommerfeld outer boundary: every ghost cell whose centre lies outside
@@ -54,6 +58,13 @@
  *   R13 along a non-periodic axis the 5 coarse cells of a prolongation
  *      stencil are shifted (by at most 2) to lie inside the domain, as the
  *      restriction stencil is kept inside the active region.
+ *   R19 2nd-order differencing with 2 ghosts (Sec. 3.1 footnote): the
+ *      transfer stencils take NP = N_g + 1 = 3 points per axis (3rd-order
+ *      Lagrange, Sec. 3.1.1) instead of 5; restriction starts at 2c (lower
+ *      half) or 2c-1 (upper half), prolongation takes parent-1..parent+1,
+ *      shifted by at most 1 into the domain.  In general the starts are
+ *      2c-(NP-3)/2, 2c-(NP-1)/2 and parent-(NP-1)/2.  3 and 4 ghosts keep
+ *      NP = 5 (R12).
  *   R17 refinement indicators (Sec. 3.2): per block, min chi and max |grad
  *      chi| over interior cells, the gradient by the block's centred
  *      first-derivative stencil.
@@ -91,7 +102,7 @@ static const int SYM[3][3] = {{0, 1, 2}, {1, 3, 4}, {2, 4, 5}};
 typedef struct {
   int32_t nblocks;
   int32_t ghosts;
-  int32_t order;     /* 4 or 6 */
+  int32_t order;     /* 2, 4 or 6 */
   int32_t periodic;  /* 1: periodic box; 0: Sommerfeld outer boundary */
   int32_t lapse;     /* 0 harmonic, 1 one-plus-log */
   int32_t shift;     /* 0 frozen, 1 Gamma-driver */
@@ -163,6 +174,10 @@ typedef struct {
   double den;
 } stencil;
 
+static const double C_D1_2[3] = {-1, 0, 1};
+static const double C_D2_2[3] = {1, -2, 1};
+static const double C_LP_2[3] = {-3, 4, -1};
+static const double C_KO_2[5] = {1, -4, 6, -4, 1};
 static const double C_D1_4[5] = {1, -8, 0, 8, -1};
 static const double C_D1_6[7] = {-1, 9, -45, 0, 45, -9, 1};
 static const double C_D2_4[5] = {-1, 16, -30, 16, -1};
@@ -173,19 +188,23 @@ static const double C_KO_4[7] = {1, -6, 15, -20, 15, -6, 1};
 static const double C_KO_6[9] = {1, -8, 28, -56, 70, -56, 28, -8, 1};
 
 static stencil st_d1(int order) {
+  if (order == 2) return (stencil){C_D1_2, 3, -1, 2.0};
   stencil s = order == 4 ? (stencil){C_D1_4, 5, -2, 12.0} : (stencil){C_D1_6, 7, -3, 60.0};
   return s;
 }
 static stencil st_d2(int order) {
+  if (order == 2) return (stencil){C_D2_2, 3, -1, 1.0};
   stencil s = order == 4 ? (stencil){C_D2_4, 5, -2, 12.0} : (stencil){C_D2_6, 7, -3, 180.0};
   return s;
 }
 static stencil st_lop(int order) {
+  if (order == 2) return (stencil){C_LP_2, 3, 0, 2.0};
   stencil s = order == 4 ? (stencil){C_LP_4, 5, -1, 12.0} : (stencil){C_LP_6, 7, -2, 60.0};
   return s;
 }
 /* KO: den = 2^(2N); sign (-1)^(N+1) applied in ko() */
 static stencil st_ko(int order) {
+  if (order == 2) return (stencil){C_KO_2, 5, -2, 16.0};
   stencil s = order == 4 ? (stencil){C_KO_4, 7, -3, 64.0} : (stencil){C_KO_6, 9, -4, 256.0};
   return s;
 }
@@ -229,7 +248,7 @@ static double dlop(const double *p, long s, int order, double h, double beta) {
 
 static double ko(const double *p, long s, int order, double h, double sigma) {
   stencil st = st_ko(order);
-  int N = order == 4 ? 3 : 4;
+  int N = order / 2 + 1;
   double sign = (N + 1) % 2 == 0 ? 1.0 : -1.0;
   return sign * sigma / (st.den * h) * apply(p, s, st);
 }
@@ -684,32 +703,38 @@ static double lagrange(const double *xs, int n, int i, double x) {
   return w;
 }
 
+/* Points per axis of the transfer stencils: N_g + 1 = 3 with 2 ghosts
+ * (Sec. 3.1.1; reading R19), 5 otherwise (R12). */
+static int transfer_points(const orc_mesh *m) { return m->ghosts == 2 ? 3 : 5; }
+
 /* Restriction (Sec. 3.1.1): value of field f at the centre xc of a coarse
- * cell (spacing 2h) covered by fine block F, by 5-point Lagrange
+ * cell (spacing 2h) covered by fine block F, by NP-point Lagrange
  * interpolation per axis (3D tensor product) over fine cells that always lie
- * inside F's active region: the stencil starts at 2c-1 for coarse cells in
- * the lower half of F and at 2c-2 in the upper half, clamped to [0, n-5]. */
+ * inside F's active region: the stencil starts at 2c-(NP-3)/2 for coarse
+ * cells in the lower half of F and at 2c-(NP-1)/2 in the upper half (NP = 5:
+ * 2c-1, 2c-2; NP = 3: 2c, 2c-1), clamped to [0, n-NP]. */
 static double restrict_at(const orc_mesh *m, const double *u, int F, int f, const double xc[3]) {
   const double h = m->h[F];
+  const int NP = transfer_points(m);
   int s[3];
   double w[3][5];
   for (int d = 0; d < 3; ++d) {
     int n = m->n[3 * F + d], nc = n / 2;
     int c = (int)floor((xc[d] - m->lo[3 * F + d]) / (2.0 * h));
-    int st = c < nc / 2 ? 2 * c - 1 : 2 * c - 2;
+    int st = c < nc / 2 ? 2 * c - (NP - 3) / 2 : 2 * c - (NP - 1) / 2;
     if (st < 0) st = 0;
-    if (st > n - 5) st = n - 5;
+    if (st > n - NP) st = n - NP;
     double xs[5];
-    for (int q = 0; q < 5; ++q) xs[q] = m->lo[3 * F + d] + (st + q + 0.5) * h;
-    for (int q = 0; q < 5; ++q) w[d][q] = lagrange(xs, 5, q, xc[d]);
+    for (int q = 0; q < NP; ++q) xs[q] = m->lo[3 * F + d] + (st + q + 0.5) * h;
+    for (int q = 0; q < NP; ++q) w[d][q] = lagrange(xs, NP, q, xc[d]);
     s[d] = st + m->ghosts;
   }
   long e0 = ext(m, F, 0), e1 = ext(m, F, 1), e2 = ext(m, F, 2);
   const double *base = u + blk_offset(m, F) + (long)f * e0 * e1 * e2;
   double v = 0.0;
-  for (int c = 0; c < 5; ++c)
-    for (int b = 0; b < 5; ++b)
-      for (int a = 0; a < 5; ++a)
+  for (int c = 0; c < NP; ++c)
+    for (int b = 0; b < NP; ++b)
+      for (int a = 0; a < NP; ++a)
         v += w[2][c] * w[1][b] * w[0][a] * base[((long)(s[2] + c) * e1 + (s[1] + b)) * e0 + (s[0] + a)];
   return v;
 }
@@ -747,13 +772,14 @@ static int coarse_value(const orc_mesh *m, const double *u, const double xq_in[3
  * owns that point,
  *   - same level: a copy of the active value;
  *   - one level finer: the restriction of the finer block's active data;
- *   - one level coarser: the prolongation, 5-point Lagrange per axis over the
- *     coarse cells parent-2..parent+2, evaluated at the fine centre (offset
- *     +-1/4 coarse spacing); along a non-periodic axis the 5 cells are
- *     shifted to lie inside the domain (reading R13); taken from the
- *     block's coarse buffer: the coarse
- *     values (coarse_value) over its extent widened by W = ceil(g/2) + 2
- *     coarse cells (ghost depth plus stencil reach) on every side.
+ *   - one level coarser: the prolongation, NP-point Lagrange per axis over
+ *     the coarse cells parent-R..parent+R (R = (NP-1)/2: 2, or 1 with 2
+ *     ghosts), evaluated at the fine centre (offset +-1/4 coarse spacing);
+ *     along a non-periodic axis the NP cells are shifted to lie inside the
+ *     domain (readings R13, R19); taken from the block's coarse buffer: the
+ *     coarse values (coarse_value) over its extent widened by
+ *     W = ceil(g/2) + R coarse cells (ghost depth plus stencil reach) on
+ *     every side.
  * Ghost cells outside a non-periodic domain are Sommerfeld cells, untouched.
  * Returns 0, or -1 if a stencil needs data that is missing or two levels
  * apart. */
@@ -768,7 +794,8 @@ int orc_fill_ghosts(const orc_mesh *m, double *u) {
     double *base = u + blk_offset(m, b);
     const int L = level_of(m, b);
     const double hc = 2.0 * m->h[b];
-    const int W = (m->ghosts + 1) / 2 + 2;
+    const int NP = transfer_points(m), RP = (NP - 1) / 2;
+    const int W = (m->ghosts + 1) / 2 + RP;
     double *cb = NULL;   /* coarse buffer [cell][field], cells (nc+2W)^3 */
     char *cbad = NULL;
     long cbn[3] = {0, 0, 0}, cb0[3] = {0, 0, 0};
@@ -822,25 +849,25 @@ int orc_fill_ghosts(const orc_mesh *m, double *u) {
             long p[3];
             double w[3][5];
             for (int d = 0; d < 3; ++d) {
-              /* stencil start (global level-(L-1) index): parent - 2, shifted
-               * into a non-periodic domain (reading R13) */
-              long st = (long)floor((x[d] - m->dom_lo[d]) / hc) - 2;
+              /* stencil start (global level-(L-1) index): parent - RP,
+               * shifted into a non-periodic domain (readings R13, R19) */
+              long st = (long)floor((x[d] - m->dom_lo[d]) / hc) - RP;
               if (!m->periodic) {
                 long nd = (long)llround((m->dom_hi[d] - m->dom_lo[d]) / hc);
-                if (st > nd - 5) st = nd - 5;
+                if (st > nd - NP) st = nd - NP;
                 if (st < 0) st = 0;
               }
-              p[d] = st + 2 - cb0[d]; /* stencil centre, buffer index */
+              p[d] = st + RP - cb0[d]; /* stencil centre, buffer index */
               double xs[5];
-              for (int a = 0; a < 5; ++a) xs[a] = m->dom_lo[d] + (st + a + 0.5) * hc;
-              for (int a = 0; a < 5; ++a) w[d][a] = lagrange(xs, 5, a, x[d]);
+              for (int a = 0; a < NP; ++a) xs[a] = m->dom_lo[d] + (st + a + 0.5) * hc;
+              for (int a = 0; a < NP; ++a) w[d][a] = lagrange(xs, NP, a, x[d]);
             }
             double v[NF];
             for (int f = 0; f < NF; ++f) v[f] = 0.0;
-            for (int c = 0; c < 5; ++c)
-              for (int bb = 0; bb < 5; ++bb)
-                for (int a = 0; a < 5; ++a) {
-                  long c0 = p[0] + a - 2, c1 = p[1] + bb - 2, c2 = p[2] + c - 2;
+            for (int c = 0; c < NP; ++c)
+              for (int bb = 0; bb < NP; ++bb)
+                for (int a = 0; a < NP; ++a) {
+                  long c0 = p[0] + a - RP, c1 = p[1] + bb - RP, c2 = p[2] + c - RP;
                   if (c0 < 0 || c1 < 0 || c2 < 0 || c0 >= cbn[0] || c1 >= cbn[1] || c2 >= cbn[2]) {
                     err = 1;
                     continue;

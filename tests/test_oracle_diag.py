@@ -34,7 +34,7 @@ def fill(m, fchi=None, fbeta=None):
     return u
 
 
-@pytest.mark.parametrize("order", [4, 6])
+@pytest.mark.parametrize("order", [2, 4, 6])
 def test_indicators_linear_chi(oracle, order):
     """chi = 1 + a.x: every centred stencil gives grad chi = a exactly, and
     the minimum sits at the corner cell nearest -a."""

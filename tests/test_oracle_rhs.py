@@ -80,7 +80,7 @@ def test_initial_data_matches_closed_forms(oracle):
 
 
 # --------------------------------------------------------------------------
-@pytest.mark.parametrize("order", [4, 6])
+@pytest.mark.parametrize("order", [2, 4, 6])
 def test_gauge_wave_rhs_converges_to_exact_time_derivative(oracle, order):
     errs = []
     for n in (16, 32, 64):
@@ -95,11 +95,12 @@ def test_gauge_wave_rhs_converges_to_exact_time_derivative(oracle, order):
     errs = np.array(errs)
     e = errs.max(axis=1)
     assert np.all(order_of(e)[-1:] > order - 0.3), e
-    # Theta stays a pure truncation error and every field converges
-    assert errs[-1, 17] < 1e-4
+    # Theta's exact RHS is zero: what remains is truncation error, of order h^p
+    assert errs[-1, 17] < (1e-2 if order == 2 else 1e-4)
+    assert order_of(errs[:, 17])[-1] > order - 0.3, errs[:, 17]
 
 
-@pytest.mark.parametrize("order", [4, 6])
+@pytest.mark.parametrize("order", [2, 4, 6])
 def test_static_schwarzschild_rhs_converges_to_zero(oracle, order):
     """Isotropic Schwarzschild with the static lapse is stationary: with
     1+log slicing and K = 0 every RHS must vanish in the continuum (pins the
@@ -118,7 +119,8 @@ def test_static_schwarzschild_rhs_converges_to_zero(oracle, order):
     assert order_of(errs)[-1] > order - 0.5, errs
 
 
-@pytest.mark.parametrize("order,ns,box", [(4, (8, 16, 32), (2.5, 3.5)), (6, (6, 12, 24), (2.0, 3.5))])
+@pytest.mark.parametrize("order,ns,box", [(2, (8, 16, 32), (2.5, 3.5)), (4, (8, 16, 32), (2.5, 3.5)),
+                                          (6, (6, 12, 24), (2.0, 3.5))])
 def test_kerr_schild_rhs_converges_to_zero(oracle, order, ns, box):
     """Schwarzschild in Kerr-Schild form is stationary with non-zero shift:
     with its own lapse and shift every non-gauge RHS vanishes in the
@@ -136,7 +138,7 @@ def test_kerr_schild_rhs_converges_to_zero(oracle, order, ns, box):
     errs = np.array(errs)
     ords = order_of(errs.max(axis=1))
     assert np.all(ords > order - 0.6), (ords, errs)
-    assert np.all(errs[-1] < 1e-6 if order == 4 else errs[-1] < 1e-8)
+    assert np.all(errs[-1] < {2: 1e-3, 4: 1e-6, 6: 1e-8}[order])
 
 
 # --------------------------------------------------------------------------
@@ -177,7 +179,7 @@ def transform_state(m_from, u, m_to, perm, flip):
     return out
 
 
-@pytest.mark.parametrize("order", [4, 6])
+@pytest.mark.parametrize("order", [2, 4, 6])
 @pytest.mark.parametrize("perm,flip", [((1, 2, 0), (0, 0, 0)), ((0, 2, 1), (0, 0, 0)),
                                        ((0, 1, 2), (1, 0, 0)), ((2, 0, 1), (0, 1, 1))])
 def test_symmetry_of_rhs_under_axis_maps(oracle, order, perm, flip):
@@ -230,11 +232,11 @@ def test_enforcement_invariants(oracle):
 
 
 # --------------------------------------------------------------------------
-@pytest.mark.parametrize("order", [4, 6])
+@pytest.mark.parametrize("order", [2, 4, 6])
 def test_constraints_converge_on_exact_data(oracle, order):
     """Kerr-Schild data (non-zero At and K) satisfies H = M^i = 0."""
     errs = []
-    for n in (8, 16, 32) if order == 4 else (6, 12, 24):
+    for n in (6, 12, 24) if order == 6 else (8, 16, 32):
         m = oracle.uniform_mesh(n=n, order=order, periodic=False, dom_lo=(2.0, 1.8, 1.9),
                                 dom_hi=(3.5, 3.3, 3.4))
         u = an.state_on_mesh(m, "kerr_schild", (1.0,))
@@ -294,14 +296,16 @@ def test_rk4_is_fourth_order_in_time(oracle):
     assert np.all(order_of(errs) > 3.6) and np.all(order_of(errs) < 4.6), errs
 
 
-def test_linear_wave_l1_rms_convergence(oracle):
-    """Sec. 4.1: periodic linear wave, amplitude 1e-8, one period, 6th-order
-    differencing + RK4; L1_RMS of g_ab(T) - g_ab(0) converges (>= 4th order,
-    the RK4 limit; the paper observes 6th where space dominates)."""
+@pytest.mark.parametrize("order", [2, 6])
+def test_linear_wave_l1_rms_convergence(oracle, order):
+    """Sec. 4.1: periodic linear wave, amplitude 1e-8, one period, RK4;
+    L1_RMS of g_ab(T) - g_ab(0) converges at the expected order: >= 4th
+    with 6th-order differencing (the RK4 limit; the paper observes 6th
+    where space dominates), 2nd with 2nd-order differencing (2 ghosts)."""
     res = []
     for n in (8, 16, 32):
         w = 4.0 / n
-        m = oracle.uniform_mesh(n=(n, 4, 4), order=6, periodic=True, lapse=1, shift=1,
+        m = oracle.uniform_mesh(n=(n, 4, 4), order=order, periodic=True, lapse=1, shift=1,
                                 ko_sigma=0.0, eta=2.0,
                                 dom_lo=(-0.5, -w / 2, -w / 2), dom_hi=(0.5, w / 2, w / 2))
         u = m.initial_data(inputs.ID_LINEAR_WAVE, [1e-8, 1.0, 0.0])
@@ -319,7 +323,7 @@ def test_linear_wave_l1_rms_convergence(oracle):
                 tot += np.mean(np.abs(g - g0)) ** 2
         res.append(np.sqrt(tot))
     ords = order_of(res)
-    assert res[0] > 1e-12 and np.all(ords > 4.0), (res, ords)
+    assert res[0] > 1e-12 and np.all(ords > (4.0 if order == 6 else 1.8)), (res, ords)
 
 
 # --------------------------------------------------------------------------

@@ -188,3 +188,52 @@ def test_bl_binary_mesh_fills_exactly_on_quartics(oracle):
     m.fill_ghosts(u)
     assert np.all(np.isfinite(u))
     assert np.abs(u - ref).max() <= 1e-11 * np.abs(ref).max()
+
+
+# --- 2 ghosts (2nd-order differencing): 3-point transfer, reading R19 ---
+# n = N_g + 1 = 3 Lagrange points per axis (Sec. 3.1.1): exact for degree <= 2
+# per axis, not for 3, error O(h^3).
+
+def _max_ghost_error(m, fn, fine_only=False):
+    u = fill_with(m, fn)
+    ref = u.copy()
+    for b, blk in enumerate(m.blocks(u)):
+        blk[:, ghost_masks(m)[b]] = np.nan
+    m.fill_ghosts(u)
+    err, scale = 0.0, 0.0
+    for b in range(m.nblocks):
+        if fine_only and m.level[b] != 1:
+            continue
+        g = ghost_masks(m)[b]
+        got, want = m.blocks(u)[b][:, g], m.blocks(ref)[b][:, g]
+        assert np.all(np.isfinite(got))
+        err = max(err, np.abs(got - want).max())
+        scale = max(scale, np.abs(want).max())
+    return err, scale
+
+
+@pytest.mark.parametrize("centre", [(0.1, 0.2, 0.3), (7.9, 0.1, 0.2)])
+@pytest.mark.parametrize("deg", [(2, 2, 2), (1, 0, 2), (0, 2, 1)])
+def test_two_ghost_transfer_exact_on_quadratics(oracle, centre, deg):
+    """Interior refined region and one touching the x = +8 face (the
+    3-point prolongation stencil shifted by one into the domain)."""
+    m = two_level(oracle, order=2, centre=centre)
+    assert m.ghosts == 2
+    p = lambda X, Y, Z: (0.3 + X) ** deg[0] * (0.2 - Y) ** deg[1] * (0.1 + Z) ** deg[2]
+    err, scale = _max_ghost_error(m, p)
+    assert err <= 1e-12 * scale, (err, scale)
+
+
+def test_two_ghost_transfer_not_exact_on_cubics(oracle):
+    m = two_level(oracle, order=2)
+    err, _ = _max_ghost_error(m, lambda X, Y, Z: (0.3 + X) ** 3)
+    assert err > 1e-6
+
+
+@pytest.mark.parametrize("centre", [(0.1, 0.2, 0.3), (7.9, 0.1, 0.2)])
+def test_two_ghost_transfer_converges_at_third_order(oracle, centre):
+    fn = lambda X, Y, Z: np.sin(0.6 * X + 0.3) * np.cos(0.5 * Y - 0.2) * np.sin(0.4 * Z + 0.7)
+    errs = [_max_ghost_error(two_level(oracle, n=n, order=2, centre=centre, radius=0.5 * 8 / n), fn,
+                             fine_only=True)[0] for n in (8, 16)]
+    rate = np.log2(errs[0] / errs[1])
+    assert 2.5 < rate < 4.0, (errs, rate)
