@@ -121,8 +121,9 @@ int launch_fused_group(z4c_ctx *ctx, int g, const StageArgs &a) {
   }
   if (!G.f32 && pre) {
     for (const Group::ExtRange &e : G.eranges)
-      CK(G.order == 6 ? launch_fused_pre_f64_ext6(e.ext, a, tl + e.first, e.count, ctx->stream)
-                      : launch_fused_pre_f64_ext4(e.ext, a, tl + e.first, e.count, ctx->stream));
+      CK(G.order == 6   ? launch_fused_pre_f64_ext6(e.ext, a, tl + e.first, e.count, ctx->stream)
+         : G.order == 4 ? launch_fused_pre_f64_ext4(e.ext, a, tl + e.first, e.count, ctx->stream)
+                        : launch_fused_pre_f64_ext2(e.ext, a, tl + e.first, e.count, ctx->stream));
   } else if (!G.f32)
     CK(launch_fused_f64(G.order, a, tl, nt, pre, ctx->stream));
   else if (pre && ctx->occ[1] == 4)
@@ -143,7 +144,7 @@ int launch_sommerfeld_p(z4c_ctx *ctx, int p, const StageArgs &a) {
 
 // RHS + stage update of every group, then the Sommerfeld cells
 int launch_stage(z4c_ctx *ctx, const StageArgs &base) {
-  for (int g = 0; g < 4; ++g) {
+  for (int g = 0; g < NGRP; ++g) {
     const StageArgs a = group_args(ctx, base, ctx->grp[g].f32);
     int r = launch_prepass_group(ctx, g, a);
     if (r) return r;
@@ -427,7 +428,7 @@ int z4c_profile_steps(z4c_ctx *ctx, double dt, int nsteps, double *ms) {
       });
       if (r) return r;
       r = timed(3, [&] {
-        for (int g = 0; g < 4; ++g) {
+        for (int g = 0; g < NGRP; ++g) {
           const int rr = launch_prepass_group(ctx, g, group_args(ctx, a, ctx->grp[g].f32));
           if (rr) return rr;
         }
@@ -435,7 +436,7 @@ int z4c_profile_steps(z4c_ctx *ctx, double dt, int nsteps, double *ms) {
       });
       if (r) return r;
       r = timed(1, [&] {
-        for (int g = 0; g < 4; ++g) {
+        for (int g = 0; g < NGRP; ++g) {
           const int rr = launch_fused_group(ctx, g, group_args(ctx, a, ctx->grp[g].f32));
           if (rr) return rr;
         }

@@ -49,7 +49,9 @@ cudaError_t launch_constraint_partials(int order, const double *u0, const DevBlo
                                        double *partials, cudaStream_t st) {
   if (ntiles <= 0) return cudaSuccess;
   dim3 block(TX, TY);
-  if (order == 4)
+  if (order == 2)
+    constraints_kernel<2><<<ntiles, block, 0, st>>>(u0, blocks, tiles, instance, r_mask, per_cell, partials);
+  else if (order == 4)
     constraints_kernel<4><<<ntiles, block, 0, st>>>(u0, blocks, tiles, instance, r_mask, per_cell, partials);
   else
     constraints_kernel<6><<<ntiles, block, 0, st>>>(u0, blocks, tiles, instance, r_mask, per_cell, partials);

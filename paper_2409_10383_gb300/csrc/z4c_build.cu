@@ -24,17 +24,51 @@ size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 long long iround(double v) { return (long long)std::llround(v); }
 long long ifloor(double v) { return (long long)std::floor(v); }
 
-// Lagrange basis polynomial l_i(x) over the points xs[0..4] (Sec. 3.1.1)
-double lagrange5(const double xs[5], int i, double x) {
+// Lagrange basis polynomial l_i(x) over the points xs[0..np-1] (Sec. 3.1.1)
+double lagrange(const double *xs, int np, int i, double x) {
   double w = 1.0;
-  for (int q = 0; q < 5; ++q)
+  for (int q = 0; q < np; ++q)
     if (q != i) w *= (x - xs[q]) / (xs[i] - xs[q]);
   return w;
+}
+double lagrange5(const double xs[5], int i, double x) { return lagrange(xs, 5, i, x); }
+
+// Points per axis of the transfer stencils: N_g + 1 = 3 with 2 ghosts
+// (Sec. 3.1.1, the 3rd-order transfer of 2nd-order differencing), else 5.
+// Every table and kernel works on 5-point windows; a 3-point stencil is
+// stored as the 5-point window that contains it (kept inside the active
+// region or the domain), with zero weights on the two other points.
+int transfer_points(int ghosts) { return ghosts == 2 ? 3 : 5; }
+
+// 5 restriction weights: window start key = s5 - 2c (fine cells, relative to
+// the coarse cell's first child); np == 3 puts the 3-point weights of the
+// cells s5 + off .. s5 + off + 2 at positions off .. off + 2.
+void restriction_row(int key, int np, int off, double w[5]) {
+  for (int q = 0; q < 5; ++q) w[q] = 0.0;
+  double xs[5];
+  const int o = np == 5 ? 0 : off;
+  for (int q = 0; q < np; ++q) xs[q] = key + o + q - 0.5;  // fine centres, relative to the coarse centre
+  for (int q = 0; q < np; ++q) w[o + q] = lagrange(xs, np, q, 0.0);
+}
+
+// Restriction stencil along one axis (Sec. 3.1.1, readings R12 and R19):
+// coarse cell c of a fine block of n cells; returns the 5-point window start
+// s5 and, for np == 3, the offset of the 3-point stencil inside it.
+void restriction_start(int c, int n, int np, int &s5, int &off) {
+  const int nc = n / 2;
+  if (np == 5) {
+    s5 = std::min(std::max(c < nc / 2 ? 2 * c - 1 : 2 * c - 2, 0), n - 5);
+    off = 0;
+    return;
+  }
+  const int s3 = std::min(std::max(c < nc / 2 ? 2 * c : 2 * c - 1, 0), n - 3);
+  s5 = std::min(std::max(s3 - 1, 0), n - 5);
+  off = s3 - s5;
 }
 
 int check_instance(const z4c_instance &I) {
   const z4c_params &p = I.params;
-  if (I.fd_order != 4 && I.fd_order != 6) return Z4C_ERR_UNSUPPORTED;
+  if (I.fd_order != 2 && I.fd_order != 4 && I.fd_order != 6) return Z4C_ERR_UNSUPPORTED;
   if (I.ghosts < I.fd_order / 2 + 1 || I.ghosts > 8) return Z4C_ERR_UNSUPPORTED;
   if (p.rhs_precision != 64 && p.rhs_precision != 32) return Z4C_ERR_UNSUPPORTED;
   if (p.lapse < 0 || p.lapse > 1 || p.shift < 0 || p.shift > 1) return Z4C_ERR_BAD_ARG;
@@ -158,30 +192,31 @@ struct GhostBuilder {
     return storage_index(lb, q);
   }
 
-  int pattern(int key) {
-    auto it = wpat.find(key);
+  int pattern(int key, int np, int off) {
+    const int k = 16 * key + 4 * (np == 3) + off;
+    auto it = wpat.find(k);
     if (it != wpat.end()) return it->second;
-    // fine points at offsets key + q - 1/2 (fine units) from the coarse centre
-    double xs[5];
-    for (int q = 0; q < 5; ++q) xs[q] = key + q - 0.5;
+    double w[5];
+    restriction_row(key, np, off, w);
     const int row = (int)(ctx->wtab.size() / 5);
-    for (int q = 0; q < 5; ++q) ctx->wtab.push_back(lagrange5(xs, q, 0.0));
-    wpat[key] = row;
+    for (int q = 0; q < 5; ++q) ctx->wtab.push_back(w[q]);
+    wpat[k] = row;
     return row;
   }
 
   // restriction of fine block nb at the coarse cell centred at x (Sec. 3.1.1):
   // 5 fine cells per axis, start 2c-1 (lower half of the block) or 2c-2
-  // (upper half), clamped into the active region
+  // (upper half); with 2 ghosts 3 cells from 2c or 2c-1; clamped into the
+  // active region
   RestrictRef restriction(int nb, const double x[3]) {
     RestrictRef r{};
     long long st[3];
+    const int np = transfer_points(I.ghosts);
     for (int d = 0; d < 3; ++d) {
-      const int n = Lo.n[d], nc = n / 2;
       const long long c = ifloor((x[d] - blk(nb).lo[d]) / (2.0 * hb(nb)));
-      long long s = c < nc / 2 ? 2 * c - 1 : 2 * c - 2;
-      s = std::min<long long>(std::max<long long>(s, 0), n - 5);
-      r.wp[d] = pattern((int)(s - 2 * c));
+      int s, off;
+      restriction_start((int)c, Lo.n[d], np, s, off);
+      r.wp[d] = pattern((int)(s - 2 * c), np, off);
       st[d] = s + I.ghosts;
       r.cc |= (int32_t)(c << (8 * d));
     }
@@ -230,7 +265,7 @@ struct GhostBuilder {
       sh = std::max<long long>(std::min<long long>(P - 2, nd - 5), 0) - (P - 2);
     }
     start = P - 2 + sh;
-    row = (int)(10 * (sh + 2) + 5 * (gi - 2 * P));
+    row = (int)(10 * (sh + 2) + 5 * (gi - 2 * P)) + (transfer_points(I.ghosts) == 3 ? 50 : 0);
   }
 
   // Ghost regions of block lb (index r0 + 3 r1 + 9 r2 with r_d = 0 below,
@@ -376,6 +411,7 @@ struct GhostBuilder {
                 if (sh[d] < -2 || sh[d] > 2) err = 1;  // domain narrower than 5 coarse cells
                 else mask |= (int)(sh[d] + 2) << (PROLONG_SHIFT_BIT + 3 * d);
               }
+              if (transfer_points(g) == 3) mask |= 1 << PROLONG_NP3_BIT;
               // the lower child may lie before the storage (odd ghost width): address
               // children relative to an index that can be negative; the kernel only
               // touches the masked ones
@@ -430,13 +466,24 @@ int z4c_create_batch(const z4c_instance *instances, int ninstances, const z4c_bl
   bool sched_set[2] = {false, false};
   // prolongation weights: coarse points at shift-2..shift+2 (coarse
   // spacing) from the parent centre, evaluated at the children's offsets
-  // -1/4 and +1/4, for shift = -2..2
+  // -1/4 and +1/4, for shift = -2..2.  pw[50..99]: the 3-point stencils of
+  // 2 ghosts in the same 5-point windows.  The window shift fixes where the
+  // parent lies in it (2 - shift) and so the 3-point start inside it,
+  // clamp(parent - 1, 0, 2): parent-1..parent+1, moved by at most one cell
+  // into the domain like the window (readings R13, R19).
   for (int sh = -2; sh <= 2; ++sh) {
     double xs[5];
     for (int q = 0; q < 5; ++q) xs[q] = sh + q - 2;
     for (int q = 0; q < 5; ++q) {
       ctx->pw[10 * (sh + 2) + q] = lagrange5(xs, q, -0.25);
       ctx->pw[10 * (sh + 2) + 5 + q] = lagrange5(xs, q, 0.25);
+    }
+    const int s3 = std::min(std::max(2 - sh - 1, 0), 2);
+    double x3[3];
+    for (int a = 0; a < 3; ++a) x3[a] = sh - 2 + s3 + a;
+    for (int a = 0; a < 3; ++a) {
+      ctx->pw[50 + 10 * (sh + 2) + s3 + a] = lagrange(x3, 3, a, -0.25);
+      ctx->pw[50 + 10 * (sh + 2) + 5 + s3 + a] = lagrange(x3, 3, a, 0.25);
     }
   }
   for (int i = 0; i < ninstances; ++i) {
@@ -468,9 +515,11 @@ int z4c_create_batch(const z4c_instance *instances, int ninstances, const z4c_bl
     const long long S = (long long)e[0] * e[1] * e[2];
     if (S * NF >= (1LL << 31)) return bail(Z4C_ERR_UNSUPPORTED);
     ctx->max_S = std::max(ctx->max_S, (int)S);
-    const double den1 = ord == 4 ? 12.0 : 60.0, den2 = ord == 4 ? 12.0 : 180.0;
-    const double kosg = ord == 4 ? 1.0 / 64.0 : -1.0 / 256.0;  // (-1)^(N+1) / 2^(2N)
-    Group &G = ctx->grp[2 * (ord == 6) + (f32 ? 1 : 0)];
+    // stencil denominators: 2h, h^2 (2nd order); 12h, 12h^2 (4th); 60h, 180h^2 (6th)
+    const double den1 = ord == 2 ? 2.0 : ord == 4 ? 12.0 : 60.0, den2 = ord == 2 ? 1.0 : ord == 4 ? 12.0 : 180.0;
+    // KO: (-1)^(N+1) / 2^(2N), N = order/2 + 1
+    const double kosg = ord == 2 ? -1.0 / 16.0 : ord == 4 ? 1.0 / 64.0 : -1.0 / 256.0;
+    Group &G = ctx->grp[group_of(ord, f32)];
     G.order = ord;
     G.f32 = f32;
     const int W = ord / 2;
@@ -539,12 +588,15 @@ int z4c_create_batch(const z4c_instance *instances, int ninstances, const z4c_bl
         for (int d = 0; d < 3; ++d) ok &= ctx->blocks[r.src].n[d] <= RB_NMAX;
     if (ok) {
       ctx->rb_mode = true;
-      for (int key = -4; key < 4; ++key) {  // the same weights as GhostBuilder::pattern
-        double xs[5];
-        for (int q = 0; q < 5; ++q) xs[q] = key + q - 0.5;
-        ctx->krow[key + 4] = (int32_t)(ctx->wtab.size() / 5);
-        for (int q = 0; q < 5; ++q) ctx->wtab.push_back(lagrange5(xs, q, 0.0));
-      }
+      // the same weights as GhostBuilder::pattern: krow[key + 4] for 5
+      // points, krow[8 + 3 (key + 4) + off] for 3 points at offset off
+      for (int key = -4; key < 4; ++key)
+        for (int v = 0; v < 4; ++v) {
+          double w[5];
+          restriction_row(key, v == 0 ? 5 : 3, v == 0 ? 0 : v - 1, w);
+          ctx->krow[v == 0 ? key + 4 : 8 + 3 * (key + 4) + v - 1] = (int32_t)(ctx->wtab.size() / 5);
+          for (int q = 0; q < 5; ++q) ctx->wtab.push_back(w[q]);
+        }
       std::map<int, int> rbi;
       auto add = [&](const RestrictRef &r, int32_t dst, int32_t didx) {
         auto it = rbi.find(r.src);
@@ -608,7 +660,7 @@ int z4c_create_batch(const z4c_instance *instances, int ninstances, const z4c_bl
   ctx->o_rbuf = take(sizeof(RestrictRef) * ctx->rbuf.size());
   ctx->o_rblocks = take(sizeof(int32_t) * ctx->rblocks.size());
   ctx->o_rbcopy = take(sizeof(RbCopy) * ctx->rbcopy.size());
-  ctx->o_krow = take(sizeof(int32_t) * 8);
+  ctx->o_krow = take(sizeof ctx->krow);
   ctx->o_rb = take(sizeof(double) * NF * RB_NC3 * ctx->rblocks.size());
   ctx->o_cbcopy = take(sizeof(CbCopy) * ctx->cbcopy.size());
   ctx->o_prol = take(sizeof(ProlongRef) * ctx->prol.size());
@@ -617,7 +669,7 @@ int z4c_create_batch(const z4c_instance *instances, int ninstances, const z4c_bl
   ctx->o_paxtab = take(sizeof(int32_t) * ctx->paxtab.size());
   ctx->o_pidx = take(sizeof(int32_t) * ctx->pidx.size());
   ctx->o_wtab = take(sizeof(double) * ctx->wtab.size());
-  ctx->o_pw = take(sizeof(double) * 50);
+  ctx->o_pw = take(sizeof ctx->pw);
   ctx->o_cb = take(sizeof(double) * NF * (size_t)ctx->ncb);
   ctx->o_ctiles = take(sizeof(Tile) * ctx->ctiles.size());
   ctx->cfirst.assign(ctx->blocks.size() + 1, 0);
@@ -707,7 +759,7 @@ int z4c_bind(z4c_ctx *ctx, void *u0, void *stage_a, void *stage_b, void *acc, vo
   CK(up(ctx->o_rbuf, ctx->rbuf.data(), sizeof(RestrictRef) * ctx->rbuf.size()));
   CK(up(ctx->o_rblocks, ctx->rblocks.data(), sizeof(int32_t) * ctx->rblocks.size()));
   CK(up(ctx->o_rbcopy, ctx->rbcopy.data(), sizeof(RbCopy) * ctx->rbcopy.size()));
-  CK(up(ctx->o_krow, ctx->krow, sizeof(int32_t) * 8));
+  CK(up(ctx->o_krow, ctx->krow, sizeof ctx->krow));
   CK(up(ctx->o_cbcopy, ctx->cbcopy.data(), sizeof(CbCopy) * ctx->cbcopy.size()));
   CK(up(ctx->o_prol, ctx->prol.data(), sizeof(ProlongRef) * ctx->prol.size()));
   CK(up(ctx->o_pbox, ctx->pbox.data(), sizeof(PBox) * ctx->pbox.size()));
@@ -715,7 +767,7 @@ int z4c_bind(z4c_ctx *ctx, void *u0, void *stage_a, void *stage_b, void *acc, vo
   CK(up(ctx->o_paxtab, ctx->paxtab.data(), sizeof(int32_t) * ctx->paxtab.size()));
   CK(up(ctx->o_pidx, ctx->pidx.data(), sizeof(int32_t) * ctx->pidx.size()));
   CK(up(ctx->o_wtab, ctx->wtab.data(), sizeof(double) * ctx->wtab.size()));
-  CK(up(ctx->o_pw, ctx->pw, sizeof(double) * 50));
+  CK(up(ctx->o_pw, ctx->pw, sizeof ctx->pw));
   CK(up(ctx->o_ctiles, ctx->ctiles.data(), sizeof(Tile) * ctx->ctiles.size()));
   CK(up(ctx->o_cfirst, ctx->cfirst.data(), sizeof(int32_t) * ctx->cfirst.size()));
   CK(cudaMemsetAsync(ctx->d_status(), 0, sizeof(int32_t), st));

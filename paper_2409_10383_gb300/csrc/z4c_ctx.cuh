@@ -42,13 +42,18 @@ struct Group {
   bool empty() const { return tiles.empty(); }
 };
 
+// Work groups: one per (differencing order, precision).  Orders 4 and 6
+// keep groups 0..3; 2nd order (2 ghosts) takes 4 and 5.
+constexpr int NGRP = 6;
+inline int group_of(int order, bool f32) { return 2 * (order == 6 ? 1 : order == 2 ? 2 : 0) + (f32 ? 1 : 0); }
+
 }  // namespace z4c
 
 struct z4c_ctx {
   std::vector<z4c::Instance> inst;
   std::vector<z4c_block> blocks;
   std::vector<z4c::DevBlock> dblocks;
-  z4c::Group grp[4];
+  z4c::Group grp[z4c::NGRP];
   std::vector<z4c::CellRef> somm[2];    // Sommerfeld cells, per precision (0 FP64, 1 FP32)
   std::vector<z4c::GhostCopy> gcopy[2];  // same-level ghost copies, per precision
   std::vector<z4c::Tile> ctiles;         // every interior tile (constraints), in block order
@@ -62,15 +67,16 @@ struct z4c_ctx {
   std::vector<z4c::PBox> pbox;           // ghost regions prolonged as boxes
   std::vector<int32_t> pslots, paxtab;   // their coarse-box slots and per-axis stencil tables
   std::vector<double> wtab;              // restriction weight patterns (5 each)
-  double pw[50] = {0};                   // prolongation weights [shift + 2][child][5]
+  double pw[100] = {0};                  // prolongation weights [3-point][shift + 2][child][5]
   int ncb = 0;                           // coarse-buffer slots
   // block-structured restriction (every fine block with restriction targets
   // has at most RB_NMAX cells per axis): the fine blocks, the scatter list,
-  // wtab rows of the weight pattern keys -4..3
+  // wtab rows of the weight pattern keys -4..3 (5 points: krow[key + 4];
+  // 3 points at offset off in the window: krow[8 + 3 (key + 4) + off])
   bool rb_mode = false;
   std::vector<int32_t> rblocks;
   std::vector<z4c::RbCopy> rbcopy;
-  int32_t krow[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int32_t krow[32] = {0};
   std::vector<double> dt_host;           // time step per block
   size_t reg_elems = 0;
   int max_S = 0;

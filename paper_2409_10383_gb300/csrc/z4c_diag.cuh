@@ -37,7 +37,10 @@ __global__ void __launch_bounds__(TX * TY) indicator_tile_kernel(const double *_
     double sq = 0.0;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      const double q = (b.order == 4 ? FD<4>::d1(s, CHI, st[d]) : FD<6>::d1(s, CHI, st[d])) * b.s1;
+      const double q = (b.order == 2   ? FD<2>::d1(s, CHI, st[d])
+                        : b.order == 4 ? FD<4>::d1(s, CHI, st[d])
+                                       : FD<6>::d1(s, CHI, st[d])) *
+                       b.s1;
       sq = fma(q, q, sq);
     }
     mx = sqrt(sq);

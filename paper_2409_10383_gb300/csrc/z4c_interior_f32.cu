@@ -8,6 +8,7 @@ namespace z4c {
 
 cudaError_t launch_prepass_f32(int order, const StageArgs &a, const Tile *wtiles, int nwtiles, cudaStream_t st) {
   if (nwtiles <= 0) return cudaSuccess;
+  if (order == 2) return launch_prepass_f32_order2(a, wtiles, nwtiles, st);
   dim3 block(TX, TY);
   if (order == 4)
     dydz_kernel<4, true><<<nwtiles, block, 0, st>>>(a, wtiles);
@@ -19,6 +20,7 @@ cudaError_t launch_prepass_f32(int order, const StageArgs &a, const Tile *wtiles
 cudaError_t launch_fused_f32(int order, const StageArgs &a, const Tile *tiles, int ntiles, bool pre,
                              cudaStream_t st) {
   if (ntiles <= 0) return cudaSuccess;
+  if (order == 2) return launch_fused_f32_order2(1, a, tiles, ntiles, pre, st);
   dim3 block(TX, TY);
   if (pre) {
     if (order == 4)

@@ -9,6 +9,7 @@ namespace z4c {
 cudaError_t launch_fused_pre_f32_occ2(int order, const StageArgs &a, const Tile *tiles, int ntiles,
                                        cudaStream_t st) {
   if (ntiles <= 0) return cudaSuccess;
+  if (order == 2) return launch_fused_f32_order2(2, a, tiles, ntiles, true, st);
   dim3 block(TX, TY);
   if (order == 4)
     interior_pre_kernel<4, true, 2><<<ntiles, block, 0, st>>>(a, tiles);

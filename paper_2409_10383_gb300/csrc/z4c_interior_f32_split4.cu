@@ -1,7 +1,7 @@
 // FP32-RHS split schedule (4), order 4: RHS kernels storing k, specialised
 // for the cubic storage extents of common block sizes (n + 6 for n = 24, 48,
 // 64, 96), plus the runtime-stride kernel for any other shape; and the
-// dispatch over both orders.
+// dispatch over the three orders.
 #include <type_traits>
 
 #include "z4c_interior.cuh"
@@ -18,6 +18,7 @@ cudaError_t go4(const StageArgs &a, const Tile *tiles, int ntiles, cudaStream_t 
 cudaError_t launch_split_rhs6(int ext, const StageArgs &a, const Tile *tiles, int ntiles, cudaStream_t st);
 
 bool split_ext_built(int order, int ext) {
+  if (order == 2) return split_ext_built2(ext);
   if (order == 6) return ext == 24 || ext == 32 || ext == 56 || ext == 72 || ext == 104;
   return ext == 30 || ext == 54 || ext == 70 || ext == 102;
 }
@@ -27,6 +28,7 @@ cudaError_t launch_split_rhs_f32(int order, int ext, const StageArgs &a, const T
   if (ntiles <= 0) return cudaSuccess;
   if (!split_ext_built(order, ext)) ext = 0;
   if (order == 6) return launch_split_rhs6(ext, a, tiles, ntiles, st);
+  if (order == 2) return launch_split_rhs2(ext, a, tiles, ntiles, st);
   switch (ext) {
     case 30: return go4<30>(a, tiles, ntiles, st);
     case 54: return go4<54>(a, tiles, ntiles, st);

@@ -102,6 +102,8 @@ struct ProlongRef {
   int32_t dst, cidx0, base, mask;
 };
 constexpr int PROLONG_SHIFT_BIT = 8;
+// set for 2 ghosts: the weights are the 3-point rows pw[50..99]
+constexpr int PROLONG_NP3_BIT = 17;
 // Box prolongation: one ghost region (face, edge or corner) of fine block
 // dst that lies wholly in one coarser block.  Fine cells: storage origin o,
 // extents nf; coarse values from the coarse-buffer slots slots[tab + q] of a
@@ -191,6 +193,15 @@ bool split_ext_built(int order, int ext);
 // extents without a specialised kernel use runtime strides)
 cudaError_t launch_fused_pre_f64_ext6(int ext, const StageArgs &a, const Tile *tiles, int ntiles, cudaStream_t st);
 cudaError_t launch_fused_pre_f64_ext4(int ext, const StageArgs &a, const Tile *tiles, int ntiles, cudaStream_t st);
+// 2nd order with 2 ghosts (z4c_interior_order2_f64.cu, z4c_interior_order2_f32.cu)
+cudaError_t launch_fused_pre_f64_ext2(int ext, const StageArgs &a, const Tile *tiles, int ntiles, cudaStream_t st);
+cudaError_t launch_prepass_f64_order2(const StageArgs &a, const Tile *wtiles, int nwtiles, cudaStream_t st);
+cudaError_t launch_fused_f64_order2(const StageArgs &a, const Tile *tiles, int ntiles, bool pre, cudaStream_t st);
+cudaError_t launch_prepass_f32_order2(const StageArgs &a, const Tile *wtiles, int nwtiles, cudaStream_t st);
+cudaError_t launch_fused_f32_order2(int occ, const StageArgs &a, const Tile *tiles, int ntiles, bool pre,
+                                    cudaStream_t st);
+bool split_ext_built2(int ext);
+cudaError_t launch_split_rhs2(int ext, const StageArgs &a, const Tile *tiles, int ntiles, cudaStream_t st);
 // FP32 fused pre-pass-schedule kernel built for 2 or 4 resident CTAs per SM
 cudaError_t launch_fused_pre_f32_occ2(int order, const StageArgs &a, const Tile *tiles, int ntiles,
                                       cudaStream_t st);

@@ -41,6 +41,27 @@ struct Src {
 template <int ORD>
 struct FD;
 
+// 2nd order (2 ghosts): d1 = (f1 - f-1) / 2h, d2 = (f1 + f-1 - 2 f0) / h^2
+//            (lopsided advection and KO dissipation: KoAdv<2> below)
+template <>
+struct FD<2> {
+  static constexpr int W = 1;
+  template <class S_>
+  __device__ static auto d1(const S_ &s, int f, int st) {
+    return s.at(f, st) - s.at(f, -st);
+  }
+  template <class S_>
+  __device__ static auto d2(const S_ &s, int f, int st) {
+    auto c = s.at(f, 0);
+    auto a = s.at(f, st) + s.at(f, -st);
+    return fma(c, decltype(c)(-2), a);
+  }
+  template <class S_>
+  __device__ static auto mix(const S_ &s, int f, int sa, int sb) {
+    return (s.at(f, sa + sb) - s.at(f, -sa + sb)) - (s.at(f, sa - sb) - s.at(f, -sa - sb));
+  }
+};
+
 // 4th order: d1 = (8 (f1 - f-1) - (f2 - f-2)) / 12h
 //            d2 = (16 (f1 + f-1) - (f2 + f-2) - 30 f0) / 12h^2
 //            (lopsided advection and KO dissipation: KoAdv<4> below)
@@ -124,6 +145,23 @@ struct FD<6> {
 // kcoef()/lcoef() give the same coefficients for KoAdvWeights below.
 template <int ORD>
 struct KoAdv;
+template <>
+struct KoAdv<2> {
+  // lopsided (beta > 0) offsets 0..2: (-3, 4, -1) / 2h;
+  // KO: N = 2, (-1) sigma / (16 h) * (1 -4 6 -4 1) per direction
+  static constexpr int KW = 2;
+  static constexpr int LOFF = 0, LN = 3;
+  template <class R>
+  __device__ static R lop(const R *v) {
+    return fma(v[0], R(-3), fma(v[1], R(4), -v[2]));
+  }
+  template <class R>
+  __device__ static R ko(R c, const R *p) {
+    return fma(c, R(18), fma(p[0], R(-4), p[1]));
+  }
+  __host__ __device__ static constexpr int kcoef(int m) { return m == 0 ? 6 : m == 1 ? -4 : 1; }
+  __host__ __device__ static constexpr int lcoef(int m) { return m == 0 ? -3 : m == 1 ? 4 : m == 2 ? -1 : 0; }
+};
 template <>
 struct KoAdv<4> {
   // lopsided (beta > 0) offsets -1..3: (-3, -10, 18, -6, 1) / 12h;

@@ -65,10 +65,23 @@ __global__ void __launch_bounds__(256) restrict_block_kernel(const double *__res
   const int cx = nx / 2, cy = ny / 2, cz = nz / 2;
   const int g = B.g, e0 = B.e[0], e1 = B.e[1];
   const double *src = reg + B.off + (int64_t)f * B.S;
-  auto start = [](int c, int n) {
+  // 5-point window start s of coarse cell c and its krow index; with 2
+  // ghosts the 3-point stencil from 2c (lower half) or 2c-1 (upper half),
+  // clamped into the block, at offset off inside the window
+  const bool np3 = B.g == 2;
+  auto start = [np3](int c, int n, int &kr) {
     const int nc = n / 2;
-    int s = c < nc / 2 ? 2 * c - 1 : 2 * c - 2;
-    return s < 0 ? 0 : s > n - 5 ? n - 5 : s;
+    if (!np3) {
+      int s = c < nc / 2 ? 2 * c - 1 : 2 * c - 2;
+      s = s < 0 ? 0 : s > n - 5 ? n - 5 : s;
+      kr = s - 2 * c + 4;
+      return s;
+    }
+    int s3 = c < nc / 2 ? 2 * c : 2 * c - 1;
+    s3 = s3 < 0 ? 0 : s3 > n - 3 ? n - 3 : s3;
+    const int s = s3 - 1 < 0 ? 0 : s3 - 1 > n - 5 ? n - 5 : s3 - 1;
+    kr = 8 + 3 * (s - 2 * c + 4) + (s3 - s);
+    return s;
   };
   for (int q = threadIdx.x; q < nx * ny * nz; q += blockDim.x) {
     const int i = q % nx, j = (q / nx) % ny, k = q / (nx * ny);
@@ -77,8 +90,9 @@ __global__ void __launch_bounds__(256) restrict_block_kernel(const double *__res
   __syncthreads();
   for (int q = threadIdx.x; q < cx * ny * nz; q += blockDim.x) {  // (c_x, j, k)
     const int c = q % cx, jk = q / cx;
-    const int s = start(c, nx);
-    const double *w = wtab + 5 * krow[s - 2 * c + 4];
+    int kr;
+    const int s = start(c, nx, kr);
+    const double *w = wtab + 5 * krow[kr];
     const double *row = fine + jk * nx + s;
     double v = 0.0;
 #pragma unroll
@@ -89,8 +103,9 @@ __global__ void __launch_bounds__(256) restrict_block_kernel(const double *__res
   double *ry = fine;
   for (int q = threadIdx.x; q < cx * cy * nz; q += blockDim.x) {  // (c_x, c_y, k)
     const int c0 = q % cx, c = (q / cx) % cy, k = q / (cx * cy);
-    const int s = start(c, ny);
-    const double *w = wtab + 5 * krow[s - 2 * c + 4];
+    int kr;
+    const int s = start(c, ny, kr);
+    const double *w = wtab + 5 * krow[kr];
     double v = 0.0;
 #pragma unroll
     for (int b = 0; b < 5; ++b) v = fma(w[b], rx[(k * ny + s + b) * cx + c0], v);
@@ -100,8 +115,9 @@ __global__ void __launch_bounds__(256) restrict_block_kernel(const double *__res
   double *out = rb + ((int64_t)blockIdx.x * NF + f) * RB_NC3;
   for (int q = threadIdx.x; q < cx * cy * cz; q += blockDim.x) {  // (c_x, c_y, c_z)
     const int cxy = q % (cx * cy), c = q / (cx * cy);
-    const int s = start(c, nz);
-    const double *w = wtab + 5 * krow[s - 2 * c + 4];
+    int kr;
+    const int s = start(c, nz, kr);
+    const double *w = wtab + 5 * krow[kr];
     double v = 0.0;
 #pragma unroll
     for (int cc = 0; cc < 5; ++cc) v = fma(w[cc], ry[(s + cc) * cx * cy + cxy], v);
@@ -139,7 +155,8 @@ __global__ void cb_copy_kernel(const double *__restrict__ reg, const DevBlock *_
 
 // pw[(5 * c + a)]: weight of the a-th of the 5 coarse points for child c
 // (0: offset -1/4, 1: +1/4) with stencil shift code s (shift + 2) at
-// pw + 10 * s
+// pw + 10 * s; the 3-point stencils of 2 ghosts (zero weights on two of the
+// five points) at pw + 50 + 10 * s
 __global__ void prolong_kernel(double *__restrict__ reg, const DevBlock *__restrict__ blocks,
                                const ProlongRef *__restrict__ list, int n, const int32_t *__restrict__ idx,
                                const double *__restrict__ cb, int ncb, const double *__restrict__ pw) {
@@ -151,9 +168,10 @@ __global__ void prolong_kernel(double *__restrict__ reg, const DevBlock *__restr
   const double *cf = cb + (int64_t)f * ncb;
   double wx[2][5], wy[2][5], wz[2][5];
   {
-    const double *px = pw + 10 * ((p.mask >> PROLONG_SHIFT_BIT) & 7);
-    const double *py = pw + 10 * ((p.mask >> (PROLONG_SHIFT_BIT + 3)) & 7);
-    const double *pz = pw + 10 * ((p.mask >> (PROLONG_SHIFT_BIT + 6)) & 7);
+    const double *pb = pw + 50 * ((p.mask >> PROLONG_NP3_BIT) & 1);
+    const double *px = pb + 10 * ((p.mask >> PROLONG_SHIFT_BIT) & 7);
+    const double *py = pb + 10 * ((p.mask >> (PROLONG_SHIFT_BIT + 3)) & 7);
+    const double *pz = pb + 10 * ((p.mask >> (PROLONG_SHIFT_BIT + 6)) & 7);
 #pragma unroll
     for (int q = 0; q < 10; ++q) {
       wx[q / 5][q % 5] = px[q];

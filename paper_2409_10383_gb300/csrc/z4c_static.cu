@@ -149,7 +149,7 @@ extern "C" int z4c_constraints_static(const void *u_device, const int32_t n[3], 
                                       const double lo[3], double h, double chi_floor, double r_mask,
                                       double *norms, void *cuda_stream) {
   if (!u_device || !n || !lo || !norms) return Z4C_ERR_BAD_ARG;
-  if (fd_order != 4 && fd_order != 6) return Z4C_ERR_UNSUPPORTED;
+  if (fd_order != 2 && fd_order != 4 && fd_order != 6) return Z4C_ERR_UNSUPPORTED;
   if (ghosts < fd_order / 2 + 1 || ghosts > 8) return Z4C_ERR_UNSUPPORTED;
   if (!(h > 0.0) || !(chi_floor > 0.0)) return Z4C_ERR_BAD_ARG;
   for (int d = 0; d < 3; ++d)
@@ -157,7 +157,8 @@ extern "C" int z4c_constraints_static(const void *u_device, const int32_t n[3], 
   const long long tiles = (long long)((n[0] + TX - 1) / TX) * ((n[1] + TY - 1) / TY) * n[2];
   if (tiles > Z4C_STATIC_MAX_TILES) return Z4C_ERR_UNSUPPORTED;  // beyond the fixed scratch
   DevBlock b{};
-  const double den1 = fd_order == 4 ? 12.0 : 60.0, den2 = fd_order == 4 ? 12.0 : 180.0;
+  const double den1 = fd_order == 2 ? 2.0 : fd_order == 4 ? 12.0 : 60.0;
+  const double den2 = fd_order == 2 ? 1.0 : fd_order == 4 ? 12.0 : 180.0;
   for (int d = 0; d < 3; ++d) {
     b.n[d] = n[d];
     b.e[d] = n[d] + 2 * ghosts;
@@ -177,7 +178,9 @@ extern "C" int z4c_constraints_static(const void *u_device, const int32_t n[3], 
   double *scratch = nullptr;
   if (static_scratch_address(&scratch) != cudaSuccess) return Z4C_ERR_CUDA;
   const dim3 block(TX, TY);
-  if (fd_order == 4)
+  if (fd_order == 2)
+    constraints_static_kernel<2><<<(unsigned)tiles, block, 0, st>>>((const double *)u_device, b, r_mask, scratch);
+  else if (fd_order == 4)
     constraints_static_kernel<4><<<(unsigned)tiles, block, 0, st>>>((const double *)u_device, b, r_mask, scratch);
   else
     constraints_static_kernel<6><<<(unsigned)tiles, block, 0, st>>>((const double *)u_device, b, r_mask, scratch);

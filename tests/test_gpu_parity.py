@@ -33,6 +33,9 @@ CASES = [
     ("puncture", 6, (2, 2, 2), 16, None),              # config-2 physics, small
     ("puncture", 4, (2, 1, 1), (20, 12, 10), None),    # ragged tiles, Sommerfeld
     ("gauge_wave", 6, (1, 2, 1), (24, 12, 18), None),  # ragged, periodic, two blocks
+    # 2nd-order differencing with 2 ghosts (the paper's default with 2 ghosts)
+    ("puncture", 2, (2, 1, 1), (20, 12, 10), None),
+    ("gauge_wave", 2, (1, 2, 1), (24, 12, 18), None),
 ]
 
 
@@ -92,11 +95,12 @@ def test_rhs_parity_fp64(oracle, kind, order, nb, n, per, schedule):
         assert np.all(m.blocks(got)[b][:, ng] == 0)
 
 
-@pytest.mark.parametrize("precision,schedule", [(64, 1), (64, 2), (32, 1), (32, 2), (32, 3), (32, 4)])
-def test_flat_space_is_exactly_static(oracle, precision, schedule):
+@pytest.mark.parametrize("order,precision,schedule", [(6, 64, 1), (6, 64, 2), (6, 32, 1), (6, 32, 2), (6, 32, 3),
+                                                      (6, 32, 4), (2, 64, 1), (2, 64, 2), (2, 32, 1), (2, 32, 4)])
+def test_flat_space_is_exactly_static(oracle, order, precision, schedule):
     # 16^3 blocks qualify for the staged FP32 kernel (schedule 3)
     n = 16 if schedule == 3 else 12
-    w = H.small_workload("puncture", 6, (2, 1, 1), n, id_kind=inputs.ID_FLAT, id_par=[])
+    w = H.small_workload("puncture", order, (2, 1, 1), n, id_kind=inputs.ID_FLAT, id_par=[])
     g = H.gpu_ctx(w, precision, schedule)
     if schedule == 4:
         g.z4c_set_variant(4, 4)
@@ -128,7 +132,7 @@ def test_gauge_wave_config_ten_steps(oracle):
 
 
 @pytest.mark.parametrize("schedule", [1, 2])
-@pytest.mark.parametrize("order,nb,n", [(6, (2, 2, 2), 16), (4, (1, 2, 1), (12, 10, 16))])
+@pytest.mark.parametrize("order,nb,n", [(6, (2, 2, 2), 16), (4, (1, 2, 1), (12, 10, 16)), (2, (2, 2, 2), 16)])
 def test_puncture_rk4_parity(oracle, order, nb, n, schedule):
     w = H.small_workload("puncture", order, nb, n)
     m = H.oracle_mesh(oracle, w)
@@ -185,15 +189,17 @@ def _round_like_shadow(m, u):
     return v
 
 
-@pytest.mark.parametrize("schedule,occupancy", [(1, 1), (2, 1), (2, 2), (2, 4), (3, 4), (4, 4)])
-def test_fp32_rhs_error_budget(oracle, schedule, occupancy):
+@pytest.mark.parametrize("order,schedule,occupancy", [(6, 1, 1), (6, 2, 1), (6, 2, 2), (6, 2, 4), (6, 3, 4),
+                                                      (6, 4, 4), (2, 1, 1), (2, 2, 2), (2, 4, 4)])
+def test_fp32_rhs_error_budget(oracle, order, schedule, occupancy):
     """FP32 stencils and algebra (FP64 state, RK accumulation, 1/chi,
     enforcement).  Bounds, stated against what FP32 storage alone causes:
       - one RHS call: per-field error <= 8x the error of the FP64 oracle fed
         the FP32-rounded state (the input-rounding floor);
       - 5 RK4 steps of the puncture: per-field |u32 - u64| <= 1e-3 of the
-        change |u64(t) - u64(0)|, and ||H||_2 within 1e-5 (relative) of FP64."""
-    w = H.small_workload("puncture", 6, (2, 2, 2), 16)
+        change |u64(t) - u64(0)|, and ||H||_2 within 1e-5 (relative) of FP64.
+    Orders 6 and 2 (the staged schedule 3 exists for order 6 only)."""
+    w = H.small_workload("puncture", order, (2, 2, 2), 16)
     m = H.oracle_mesh(oracle, w)
     g = H.gpu_ctx(w, precision=32, schedule=schedule)
     g.z4c_set_variant(schedule, occupancy)

@@ -36,10 +36,12 @@ def oracle_of(oracle, w):
 
 @pytest.mark.parametrize("order,periodic,centre", [(6, False, (0.1, 0.2, 0.3)), (4, False, (0.1, 0.2, 0.3)),
                                                    (6, True, (0.1, 0.2, 0.3)), (6, False, (7.9, 0.1, 0.2)),
-                                                   (4, False, (7.9, 0.1, 0.2))])
+                                                   (4, False, (7.9, 0.1, 0.2)), (2, False, (0.1, 0.2, 0.3)),
+                                                   (2, True, (0.1, 0.2, 0.3)), (2, False, (7.9, 0.1, 0.2))])
 def test_smr_ghost_fill_parity(oracle, order, periodic, centre):
     """Centre (7.9, 0.1, 0.2) refines blocks on the x = +8 face next to coarse
-    ones on that face: prolongation stencils shifted into the domain."""
+    ones on that face: prolongation stencils shifted into the domain.  Order
+    2 (2 ghosts) uses the 3-point transfer."""
     from paper_2409_10383_gb300.z4c import Z4c
     w = smr_workload(order=order, periodic=periodic, centre=centre)
     m = oracle_of(oracle, w)
@@ -52,11 +54,13 @@ def test_smr_ghost_fill_parity(oracle, order, periodic, centre):
     assert np.abs(got - u).max() <= 1e-13, np.abs(got - u).max()
 
 
-def test_smr_ghost_fill_parity_wide_blocks(oracle):
-    """Fine blocks of 24^3 (wider than the block-structured restriction
-    handles): the per-entry restriction kernel."""
+@pytest.mark.parametrize("order", [6, 2])
+def test_smr_ghost_fill_parity_wide_blocks(oracle, order):
+    """Fine blocks of 24^3 (wider than the block-structured restriction and
+    the box prolongation handle): the per-entry restriction kernel and the
+    per-parent prolongation kernel."""
     from paper_2409_10383_gb300.z4c import Z4c
-    w = smr_workload(nb=2, n=24, radii=(0.05,))
+    w = smr_workload(nb=2, n=24, radii=(0.05,), order=order)
     m = oracle_of(oracle, w)
     assert (m.level == 1).sum() == 8 and (m.level == 0).sum() == 7
     g = Z4c.from_workload(w)
@@ -68,9 +72,10 @@ def test_smr_ghost_fill_parity_wide_blocks(oracle):
     assert np.abs(got - u).max() <= 1e-13, np.abs(got - u).max()
 
 
-def test_smr_puncture_rk4_parity(oracle):
+@pytest.mark.parametrize("order", [6, 2])
+def test_smr_puncture_rk4_parity(oracle, order):
     from paper_2409_10383_gb300.z4c import Z4c
-    w = smr_workload()
+    w = smr_workload(order=order)
     m = oracle_of(oracle, w)
     assert (m.level == 1).sum() == 64
     g = Z4c.from_workload(w)
@@ -205,10 +210,10 @@ def test_bl_binary_smr_fifty_steps_keep_mirror_symmetry():
 # ---- the paper's SMR accuracy check (Sec. 4.1, Fig. 3): a periodic linear
 # wave through a refined region, against the analytic solution
 
-def _refined_linear_wave(n):
+def _refined_linear_wave(n, order=6):
     half = 0.5
     nn, lo, h, lev = inputs.octree_mesh((2, 2, 2), n, (-half,) * 3, (half,) * 3, [(0.25, 0.25, 0.25)], [0.15], 1)
-    return dict(n=nn, lo=lo, h=h, level=lev, ghosts=4, order=6, periodic=True, dom_lo=(-half,) * 3,
+    return dict(n=nn, lo=lo, h=h, level=lev, ghosts=order // 2 + 1, order=order, periodic=True, dom_lo=(-half,) * 3,
                 dom_hi=(half,) * 3, lapse=1, shift=1, ko_sigma=0.02, kappa1=0.0, kappa2=0.0, eta=2.0,
                 chi_floor=1e-6, cfl=0.25, id_kind=inputs.ID_LINEAR_WAVE, id_par=[1e-6, 1.0, 0.0], precision=64)
 
@@ -230,18 +235,21 @@ def _l1_rms_metric_error(m, w, u, ua):
     return np.sqrt(tot)
 
 
-def test_refined_linear_wave_gpu(oracle):
-    """The linear wave (A = 1e-6) through a refined region, 6th order + RK4
-    to t = 1/8 on the GPU (box prolongation, block restriction, periodic
-    wrap).  Against the oracle: every evolved value within 1e-12 absolute
-    (the fields are O(1) with a 1e-6 wave, so the per-field relative measure
-    with its 1e-3 floor would compare rounding of O(1) values against 1e-3).
-    Against the analytic wave: the L1_RMS error of g_ab converges at >= 4th
-    order from the GPU runs alone."""
+@pytest.mark.parametrize("order,rate", [(6, 3.5), (2, 1.8)])
+def test_refined_linear_wave_gpu(oracle, order, rate):
+    """The linear wave (A = 1e-6) through a refined region, RK4 to t = 1/8 on
+    the GPU (box prolongation, block restriction, periodic wrap), with 6th-
+    order differencing (4 ghosts, 5-point transfer) and 2nd-order (2 ghosts,
+    3-point transfer).  Against the oracle: every evolved value within 1e-12
+    absolute (the fields are O(1) with a 1e-6 wave, so the per-field relative
+    measure with its 1e-3 floor would compare rounding of O(1) values against
+    1e-3).  Against the analytic wave: the L1_RMS error of g_ab converges at
+    the expected order (>= 4th with 6th-order differencing, the RK4 limit;
+    2nd with 2nd-order) from the GPU runs alone."""
     from paper_2409_10383_gb300.z4c import Z4c
     errs = []
     for n in (8, 12):
-        w = _refined_linear_wave(n)
+        w = _refined_linear_wave(n, order)
         m = oracle_of(oracle, w)
         assert (m.level == 1).sum() == 8
         dt = 0.25 * float(np.min(w["h"]))
@@ -258,4 +266,4 @@ def test_refined_linear_wave_gpu(oracle):
             _, absd = H.field_errors(m, u, got)
             assert absd.max() <= 1e-12, absd
         g.close()
-    assert np.log(errs[0] / errs[1]) / np.log(1.5) > 3.5, errs
+    assert np.log(errs[0] / errs[1]) / np.log(1.5) > rate, errs
