@@ -44,9 +44,11 @@ L2_BYTES = 129 * 2 ** 20
 # (dadd, dfma, dmul; exact integers per cell) of a one-block 64^3 order-6
 # capture, stage-1 launch:
 # flops = dadd + dmul + 2 dfma.
-FP64_OPS_PER_CELL_STAGE = {6: dict(dadd=534, dfma=1499, dmul=531)}
+FP64_OPS_PER_CELL_STAGE = {6: dict(dadd=534, dfma=1499, dmul=531),
+                           # 2nd order, 2 ghosts: interior_pre_kernel<2,false,1,false,68>
+                           2: dict(dadd=351, dfma=1037, dmul=518)}
 # DRAM bytes (read + write) per interior cell of that launch
-FP64_DRAM_BYTES_PER_CELL = {6: (121226496 + 93064704) / 262144}
+FP64_DRAM_BYTES_PER_CELL = {6: (121226496 + 93064704) / 262144, 2: (114322688 + 63602432) / 262144}
 # FP32-RHS split schedule (interior_pre_kernel<6,true,4,split,72> storing k
 # + split_epilogue_kernel): executed FP32 operations and the FP64 residue per
 # interior cell per stage, from the same kind of capture
@@ -422,6 +424,8 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=5)
     ap.add_argument("--no-smr", action="store_true")
     ap.add_argument("--smr-steps", type=int, default=50)
+    ap.add_argument("--no-order2", action="store_true",
+                    help="skip the 2nd-order (2 ghosts) variant of the workload")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default kernel variant instead of timing the candidates")
     ap.add_argument("--smr-only", action="store_true",
@@ -469,6 +473,16 @@ def main():
             torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
             smr["value"] = smr["cells"] * ws / (float(t.item()) * 1e-3)
 
+    order2 = None
+    if not args.no_order2 and args.variant == "both" and workload["order"] != 2:
+        w2 = inputs.workload(args.workload + "_o2")
+        q = measure(z4c, torch, w2, 64, args, ws, local)
+        order2 = {"value": q["value"], "unit": UNIT, "ms_per_step": q["ms_per_step"], "dtype": "f64",
+                  "config": {"workload": w2["name"], "fd_order": 2, "ghosts": 2, "cells": q["cells"],
+                             "dt": q["dt"]},
+                  "roofline": q["roofline"], "e2e": q["e2e"], "gpu_launches": q["gpu_launches"],
+                  "clocks": q["clocks"]}
+
     if rank != 0:
         if ws > 1:
             torch.distributed.destroy_process_group()
@@ -501,6 +515,8 @@ def main():
         line["batched"] = batched
     if smr is not None:
         line["smr"] = smr
+    if order2 is not None:
+        line["order2"] = order2
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()

@@ -49,7 +49,13 @@ def uniform_blocks(nb=(1, 1, 1), n=32, dom_lo=(-0.5,) * 3, dom_hi=(0.5,) * 3):
 
 
 def workload(name: str) -> dict:
-    """Named workload: mesh + parameters + initial data (no arithmetic of the method)."""
+    """Named workload: mesh + parameters + initial data (no arithmetic of the method).
+    A name ending in "_o2" is the same problem with 2nd-order differencing
+    and 2 ghosts (the paper's default with 2 ghost cells)."""
+    if name.endswith("_o2"):
+        w = workload(name[:-3])
+        w.update(name=name, order=2, ghosts=2)
+        return w
     if name == "gauge_wave_32":
         n, lo, h = uniform_blocks((1, 1, 1), 32)
         return dict(name=name, n=n, lo=lo, h=h, ghosts=3, order=4, periodic=True,
