@@ -73,6 +73,7 @@ def lib():
             "orc_set_threads": (I, [I]),
             "orc_block_indicators": (None, [mp, P, P, P]),
             "orc_track_punctures": (I, [mp, P, I, P, D, P]),
+            "orc_psi4": (None, [mp, P, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(_lib, name)
@@ -236,6 +237,20 @@ class Mesh:
         cmin, gmax = np.zeros(self.nblocks), np.zeros(self.nblocks)
         lib().orc_block_indicators(ctypes.byref(self._c), _ptr(u), _ptr(cmin), _ptr(gmax))
         return cmin, gmax
+
+    def psi4(self, u: np.ndarray):
+        """Weyl scalar Psi4 (reading R20) at every interior cell: per block a
+        complex (nz+2g, ny+2g, nx+2g) array, zero outside the interior; the
+        ghosts of u must be filled."""
+        out = np.zeros(2 * self.size() // NF)
+        lib().orc_psi4(ctypes.byref(self._c), _ptr(u), _ptr(out))
+        res, off = [], 0
+        for b in range(self.nblocks):
+            ex, ey, ez = self.ext(b)
+            S = ex * ey * ez
+            res.append((out[off:off + S] + 1j * out[off + S:off + 2 * S]).reshape(ez, ey, ex))
+            off += 2 * S
+        return res
 
     def track_punctures(self, u: np.ndarray, xyz, dt: float):
         """One tracker step of each puncture: (new positions, beta at the old

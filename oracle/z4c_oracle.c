@@ -68,6 +68,14 @@
  *   R17 refinement indicators (Sec. 3.2): per block, min chi and max |grad
  *      chi| over interior cells, the gradient by the block's centred
  *      first-derivative stencil.
+ *   R20 Psi4 (Sec. 3.3, computed with a coordinate tetrad; the paper gives no
+ *      formulas): Psi4 = (E_ij - i B_ij) mb^i mb^j with the electric and
+ *      magnetic parts of the Weyl tensor from the 3+1 variables (vacuum,
+ *      K = Khat + 2 Theta) and mb = (e_th - i e_ph)/sqrt(2) from Gram-Schmidt
+ *      on the radial, phi and theta coordinate vectors.  For a linear TT
+ *      wave travelling along +x, on the +x axis, this is
+ *      d_t^2 (h_yy - i h_yz) (h_zz = -h_yy); for one travelling along -x it
+ *      vanishes.  See psi4_point().
  *   R18 puncture tracker (Sec. 3.3): dx/dt = -beta(x), one forward-Euler step
  *      per call, beta by 4-point Lagrange interpolation per axis.
  *
@@ -991,6 +999,150 @@ int orc_rk4_step(const orc_mesh *m, double *u, double dt, int nsteps) {
  * ||X||_2 = sqrt(sum X^2 h^3 / sum h^3) over interior cells.
  * per_cell (nullable): 4 values per storage cell (H, Mx, My, Mz), field
  * major like the state (4 "fields"). */
+/* ------------------------------------------------------------------ */
+/* Weyl scalar Psi4 on the grid (Sec. 3.3: the outgoing Weyl scalar in  */
+/* a coordinate tetrad; reading R20)                                   */
+/* ------------------------------------------------------------------ */
+
+/* Psi4 = (E_ij - i B_ij) mb^i mb^j at one interior cell, with
+ *   gamma_ij = gt_ij / chi_g,  K_ij = (At_ij + gt_ij K / 3) / chi_g,
+ *   K = Khat + 2 Theta,
+ *   E_ij = R_ij + K K_ij - K_ik gamma^kl K_lj      (R_ij: compute_geometry),
+ *   B_ij = symmetric part of gamma_im eps^mkl D_k K_lj,
+ *          eps^mkl = [mkl] / sqrt(det gamma),
+ *   D_k K_lj = d_k K_lj - G^m_kl K_mj - G^m_kj K_lm with the Christoffels of
+ *   gamma, G^m_kl = Gt^m_kl - (delta^m_k d_l chi + delta^m_l d_k chi -
+ *   gt_kl gt^mn d_n chi) / (2 chi_g), and d_k K_lj by the product rule from
+ *   the derivatives of At, gt, Khat, Theta and chi;
+ *   mb = (e_th - i e_ph) / sqrt(2) from Gram-Schmidt in gamma on the
+ *   coordinate vectors x^i (radial), (-y, x, 0) (phi) and
+ *   (x z, y z, -(x^2 + y^2)) (theta), in that order.
+ * x: the cell centre; the tetrad is undefined on the z axis, where the
+ * result is 0. */
+static void psi4_point(const orc_mesh *m, const double *c, long S, const long st[3], double h,
+                       const double x[3], double out[2]) {
+  out[0] = out[1] = 0.0;
+  if (x[0] * x[0] + x[1] * x[1] == 0.0) return;
+  point_data P;
+  geometry G;
+  gather_point(m, c, S, st, h, &P, 1);
+  compute_geometry(m, &P, &G);
+  const double ichi = 1.0 / G.chig, K = G.K;
+  double gam[3][3], gamu[3][3], Kij[3][3], dK[3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      gam[i][j] = P.g[i][j] * ichi;
+      gamu[i][j] = G.gi[i][j] * G.chig;
+      Kij[i][j] = (P.A[i][j] + P.g[i][j] * K / 3.0) * ichi;
+    }
+  for (int k = 0; k < 3; ++k) dK[k] = P.dKhat[k] + 2.0 * P.dTheta[k];
+  double dKij[3][3][3], Gam[3][3][3];
+  for (int k = 0; k < 3; ++k)
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j)
+        dKij[k][i][j] = (P.dA[k][i][j] + (P.dg[k][i][j] * K + P.g[i][j] * dK[k]) / 3.0) * ichi -
+                        Kij[i][j] * P.dchi[k] * ichi;
+  for (int mm = 0; mm < 3; ++mm)
+    for (int k = 0; k < 3; ++k)
+      for (int l = 0; l < 3; ++l) {
+        double gd = 0.0;
+        for (int n = 0; n < 3; ++n) gd += G.gi[mm][n] * P.dchi[n];
+        double dk = (mm == k ? P.dchi[l] : 0.0) + (mm == l ? P.dchi[k] : 0.0) - P.g[k][l] * gd;
+        Gam[mm][k][l] = G.Gu[mm][k][l] - 0.5 * ichi * dk;
+      }
+  double E[3][3], DK[3][3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double kk = 0.0;
+      for (int k = 0; k < 3; ++k)
+        for (int l = 0; l < 3; ++l) kk += Kij[i][k] * gamu[k][l] * Kij[l][j];
+      E[i][j] = G.R[i][j] + K * Kij[i][j] - kk;
+    }
+  for (int k = 0; k < 3; ++k)
+    for (int l = 0; l < 3; ++l)
+      for (int j = 0; j < 3; ++j) {
+        double s = dKij[k][l][j];
+        for (int mm = 0; mm < 3; ++mm) s -= Gam[mm][k][l] * Kij[mm][j] + Gam[mm][k][j] * Kij[l][mm];
+        DK[k][l][j] = s;
+      }
+  const double sqrtg = sqrt(det3(gam));
+  double Bt[3][3], B[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double s = 0.0;
+      for (int mm = 0; mm < 3; ++mm)
+        for (int k = 0; k < 3; ++k)
+          for (int l = 0; l < 3; ++l) {
+            /* Levi-Civita symbol [mkl] */
+            double e = (double)((mm - k) * (k - l) * (l - mm)) / 2.0;
+            if (e != 0.0) s += gam[i][mm] * e / sqrtg * DK[k][l][j];
+          }
+      Bt[i][j] = s;
+    }
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) B[i][j] = 0.5 * (Bt[i][j] + Bt[j][i]);
+  /* tetrad */
+  double u[3][3] = {{x[0], x[1], x[2]},
+                    {-x[1], x[0], 0.0},
+                    {x[0] * x[2], x[1] * x[2], -(x[0] * x[0] + x[1] * x[1])}};
+  double e[3][3]; /* e_r, e_ph, e_th */
+  for (int a = 0; a < 3; ++a) {
+    double v[3] = {u[a][0], u[a][1], u[a][2]};
+    for (int b = 0; b < a; ++b) {
+      double d = 0.0;
+      for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) d += gam[i][j] * e[b][i] * v[j];
+      for (int i = 0; i < 3; ++i) v[i] -= d * e[b][i];
+    }
+    double nn = 0.0;
+    for (int i = 0; i < 3; ++i)
+      for (int j = 0; j < 3; ++j) nn += gam[i][j] * v[i] * v[j];
+    for (int i = 0; i < 3; ++i) e[a][i] = v[i] / sqrt(nn);
+  }
+  const double *ph = e[1], *th = e[2];
+  double Ett = 0, Epp = 0, Etp = 0, Btt = 0, Bpp = 0, Btp = 0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      Ett += E[i][j] * th[i] * th[j];
+      Epp += E[i][j] * ph[i] * ph[j];
+      Etp += E[i][j] * th[i] * ph[j];
+      Btt += B[i][j] * th[i] * th[j];
+      Bpp += B[i][j] * ph[i] * ph[j];
+      Btp += B[i][j] * th[i] * ph[j];
+    }
+  /* mb^i mb^j = (th th - ph ph - i (th ph + ph th)) / 2 */
+  out[0] = 0.5 * (Ett - Epp) - Btp;
+  out[1] = -Etp - 0.5 * (Btt - Bpp);
+}
+
+/* Psi4 at every interior cell: out holds, per block, the real part and then
+ * the imaginary part over the block's storage cells; other cells get 0.
+ * `u` must have its ghosts filled. */
+void orc_psi4(const orc_mesh *m, const double *u, double *out) {
+  long off = 0;
+  for (int b = 0; b < m->nblocks; ++b) {
+    long e0 = ext(m, b, 0), e1 = ext(m, b, 1), e2 = ext(m, b, 2);
+    long S = e0 * e1 * e2;
+    long st[3] = {1, e0, e0 * e1};
+    const double *base = u + blk_offset(m, b);
+#pragma omp parallel for schedule(static)
+    for (long k = 0; k < e2; ++k)
+      for (long j = 0; j < e1; ++j)
+        for (long i = 0; i < e0; ++i) {
+          long cidx = (k * e1 + j) * e0 + i;
+          double v[2] = {0.0, 0.0};
+          if (is_interior(m, b, (int)i, (int)j, (int)k)) {
+            double x[3];
+            cell_centre(m, b, (int)i, (int)j, (int)k, x);
+            psi4_point(m, base + cidx, S, st, m->h[b], x, v);
+          }
+          out[off + cidx] = v[0];
+          out[off + S + cidx] = v[1];
+        }
+    off += 2 * S;
+  }
+}
+
 void orc_constraints(const orc_mesh *m, const double *u, double r_mask, double *per_cell, double norms[6]) {
   double sH = 0, sM = 0, sV = 0, mH = 0, sHm = 0, sMm = 0, sVm = 0, mM = 0;
   long pc_off = 0;

@@ -48,27 +48,80 @@ def _decompose(alpha, beta_u, gamma):
     return fields
 
 
-@lru_cache(maxsize=None)
-def _compiled(kind: str, params: tuple):
+def _spacetime(kind: str, params: tuple):
+    """(alpha, beta^i, gamma_ij) of a named closed-form spacetime."""
     if kind == "gauge_wave":
         A, d = params
         H = 1 - A * sp.sin(2 * sp.pi * (x - t) / d)
-        fields = _decompose(sp.sqrt(H), [0, 0, 0], [[H, 0, 0], [0, 1, 0], [0, 0, 1]])
-    elif kind == "linear_wave":
+        return sp.sqrt(H), [0, 0, 0], [[H, 0, 0], [0, 1, 0], [0, 0, 1]]
+    if kind in ("linear_wave", "linear_wave_in"):
+        # TT wave along +x (linear_wave) or -x (linear_wave_in)
         A, d = params
-        a = A * sp.sin(2 * sp.pi * (x - t) / d)
-        fields = _decompose(sp.Integer(1), [0, 0, 0], [[1, 0, 0], [0, 1 + a, 0], [0, 0, 1 - a]])
-    elif kind == "kerr_schild":
+        a = A * sp.sin(2 * sp.pi * (x - t if kind == "linear_wave" else x + t) / d)
+        return sp.Integer(1), [0, 0, 0], [[1, 0, 0], [0, 1 + a, 0], [0, 0, 1 - a]]
+    if kind == "kerr_schild":
         (M,) = params
         r = sp.sqrt(x * x + y * y + z * z)
         Hs = M / r
         l = [x / r, y / r, z / r]
         gamma = [[sp.KroneckerDelta(i, j) + 2 * Hs * l[i] * l[j] for j in range(3)] for i in range(3)]
-        alpha = 1 / sp.sqrt(1 + 2 * Hs)
-        beta_u = [2 * Hs / (1 + 2 * Hs) * l[i] for i in range(3)]
-        fields = _decompose(alpha, beta_u, gamma)
-    else:
-        raise KeyError(kind)
+        return 1 / sp.sqrt(1 + 2 * Hs), [2 * Hs / (1 + 2 * Hs) * l[i] for i in range(3)], gamma
+    raise KeyError(kind)
+
+
+def _weyl_parts(alpha, beta_u, gamma):
+    """Electric and magnetic parts of the Weyl tensor of a vacuum 3+1 slice,
+    from the ADM variables directly (no conformal decomposition):
+      E_ij = R_ij + K K_ij - K_ik gamma^kl K_lj,
+      B_ij = sym(gamma_im eps^mkl D_k K_lj),  eps^mkl = [mkl] / sqrt(det gamma),
+    with K_ij = -(d_t gamma_ij - D_i beta_j - D_j beta_i) / (2 alpha)."""
+    g = sp.Matrix(3, 3, lambda i, j: gamma[i][j])
+    detg = g.det()
+    gi = g.adjugate() / detg
+    dg = [[[sp.diff(g[i, j], XS[k]) for k in range(3)] for j in range(3)] for i in range(3)]
+    Gam = [[[sum(gi[k, l] * (dg[l][i][j] + dg[l][j][i] - dg[i][j][l]) for l in range(3)) / 2
+             for j in range(3)] for i in range(3)] for k in range(3)]
+    beta_d = [sum(g[i, j] * beta_u[j] for j in range(3)) for i in range(3)]
+    Db = [[sp.diff(beta_d[j], XS[i]) - sum(Gam[k][i][j] * beta_d[k] for k in range(3))
+           for j in range(3)] for i in range(3)]
+    K = [[-(sp.diff(g[i, j], t) - Db[i][j] - Db[j][i]) / (2 * alpha) for j in range(3)]
+         for i in range(3)]
+    trK = sum(gi[i, j] * K[i][j] for i in range(3) for j in range(3))
+    Ric = [[sum(sp.diff(Gam[k][i][j], XS[k]) - sp.diff(Gam[k][i][k], XS[j]) +
+                sum(Gam[k][k][l] * Gam[l][i][j] - Gam[k][j][l] * Gam[l][i][k] for l in range(3))
+                for k in range(3)) for j in range(3)] for i in range(3)]
+    E = [[Ric[i][j] + trK * K[i][j] - sum(K[i][k] * gi[k, l] * K[l][j] for k in range(3) for l in range(3))
+          for j in range(3)] for i in range(3)]
+    DK = [[[sp.diff(K[l][j], XS[k]) - sum(Gam[m][k][l] * K[m][j] + Gam[m][k][j] * K[l][m] for m in range(3))
+            for j in range(3)] for l in range(3)] for k in range(3)]
+    sq = sp.sqrt(detg)
+    Bt = [[sum(g[i, m] * sp.LeviCivita(m, k, l) / sq * DK[k][l][j]
+               for m in range(3) for k in range(3) for l in range(3)) for j in range(3)] for i in range(3)]
+    B = [[(Bt[i][j] + Bt[j][i]) / 2 for j in range(3)] for i in range(3)]
+    return [E[i][j] for i, j in SYM] + [B[i][j] for i, j in SYM] + [g[i, j] for i, j in SYM]
+
+
+@lru_cache(maxsize=None)
+def _compiled_weyl(kind: str, params: tuple):
+    return sp.lambdify((t, x, y, z), _weyl_parts(*_spacetime(kind, params)), modules="numpy", cse=True)
+
+
+def weyl(kind: str, params: tuple, X, Y, Z, time: float = 0.0):
+    """(E, B, gamma) at the points: three (3, 3) + X.shape arrays."""
+    vals = _compiled_weyl(kind, tuple(params))(time, X, Y, Z)
+    v = [np.broadcast_to(np.asarray(q, dtype=float), X.shape) for q in vals]
+    out = []
+    for base in (0, 6, 12):
+        T = np.zeros((3, 3) + X.shape)
+        for q, (i, j) in enumerate(SYM):
+            T[i, j] = T[j, i] = v[base + q]
+        out.append(T)
+    return out
+
+
+@lru_cache(maxsize=None)
+def _compiled(kind: str, params: tuple):
+    fields = _decompose(*_spacetime(kind, params))
     dfields = [sp.diff(f, t) for f in fields]
     fn = sp.lambdify((t, x, y, z), fields, modules="numpy", cse=True)
     dfn = sp.lambdify((t, x, y, z), dfields, modules="numpy", cse=True)
