@@ -311,9 +311,22 @@ def measure(z4c, torch, workload, prec, args, ws, local):
     e2e = {"value": cells * e2e_steps * ws / (t1 - t0), "unit": UNIT, "h2d_bytes_per_step": nbytes,
            "d2h_bytes_per_step": nbytes}
     roof["variant"] = {"schedule": variant[0], "occupancy": variant[1]}
+    # the Weyl scalar Psi4 on the grid (Sec. 3.3 diagnostic, FP64): one
+    # synchronous call = ghost fill + Psi4 at every interior cell
+    psi4 = None
+    if prec == 64:
+        buf = g.z4c_psi4()
+        reps = 3
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            g.z4c_psi4(out=buf)
+        t1 = time.perf_counter()
+        psi4 = {"ms_per_call": (t1 - t0) / reps * 1e3, "value": cells * reps / (t1 - t0), "unit": "cells/s",
+                "note": "z4c_psi4 on the benchmark state: ghost fill + Psi4 (coordinate tetrad) at every interior cell"}
+        del buf
     out = dict(value=value, ms_per_step=ms / args.steps, roofline=roof, e2e=e2e,
                gpu_launches=g.z4c_launches_per_step() * args.steps, clocks=clk.summary(),
-               cells=cells, dt=dt, state_bytes=nbytes)
+               cells=cells, dt=dt, state_bytes=nbytes, psi4=psi4)
     g.close()
     del g
     torch.cuda.empty_cache()
@@ -505,6 +518,8 @@ def main():
                        "parallelism": f"{ws} independent instance(s)"},
             "roofline": r["roofline"], "cpu_baseline": cpu, "e2e": r["e2e"],
             "gpu_launches": r["gpu_launches"], "clocks": r["clocks"]}
+    if r.get("psi4"):
+        line["psi4"] = r["psi4"]
     if prim == 64 and 32 in res:
         q = res[32]
         line["fp32_rhs"] = {"value": q["value"], "unit": UNIT, "ms_per_step": q["ms_per_step"],

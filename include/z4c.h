@@ -5,7 +5,8 @@
  * Bona-Masso lapse and Gamma-driver shift) on a pack of MeshBlocks
  * (Sec. 3: a Mesh of rectangular MeshBlocks, each an active region plus a
  * ghost region; blocks batched into one pack to cut kernel launches) with
- * cell-centred 4th/6th-order finite differences (Sec. 3.2), Kreiss-Oliger
+ * cell-centred 2nd/4th/6th-order finite differences (Sec. 3.2; 2nd order with
+ * 2 ghosts is the paper's default with 2 ghost cells, Sec. 3.1), Kreiss-Oliger
  * dissipation and constraint damping (Sec. 4.3), and classic RK4 whose
  * ghost zones are refilled at every stage (Sec. 3).  Throughput is counted
  * in zone-cycles per second (Sec. 5).
@@ -44,7 +45,7 @@ typedef enum z4c_status {
   Z4C_OK = 0,
   Z4C_ERR_BAD_ARG = -1,      /* null pointer, out-of-range index, bad size */
   Z4C_ERR_BAD_MESH = -2,     /* blocks overlap, leave the mesh, or leave gaps */
-  Z4C_ERR_UNSUPPORTED = -3,  /* order not 4/6, ghosts < order/2 + 1, odd storage extent */
+  Z4C_ERR_UNSUPPORTED = -3,  /* order not 2/4/6, ghosts < order/2 + 1, odd storage extent */
   Z4C_ERR_CUDA = -4,         /* a CUDA runtime call failed */
   Z4C_ERR_TIMEOUT = -5,      /* a bounded device-side wait gave up */
   Z4C_ERR_NAN = -6,          /* a constraint norm came out NaN */
@@ -136,7 +137,7 @@ typedef struct z4c_ctx z4c_ctx;
 
 /* Create a context for one pack of blocks on one mesh (Sec. 3).
  * blocks: nblocks entries (host memory, copied).  ghosts >= fd_order/2 + 1,
- * fd_order 4 or 6, every storage extent n+2*ghosts even.  Blocks must tile
+ * fd_order 2, 4 or 6, every storage extent n+2*ghosts even.  Blocks must tile
  * the mesh exactly with equal n along shared faces.  Makes no CUDA call.
  * On success *out owns the context (release with z4c_destroy). */
 int z4c_create(const z4c_mesh *mesh, const z4c_block *blocks, int nblocks, int ghosts,
@@ -268,7 +269,7 @@ int z4c_autotune(z4c_ctx *ctx, int reps, int *schedule_out, int *occupancy_out);
 /* Refinement indicators of every block (paper Sec. 3.2, the chi-min and
  * d-chi criteria): over the block's interior cells, chi_min[b] = min chi and
  * dchi_max[b] = max |grad chi|, the gradient by the block's centred
- * first-derivative stencil (order 4 or 6), in FP64.  Fills the ghost cells
+ * first-derivative stencil (order 2, 4 or 6), in FP64.  Fills the ghost cells
  * of register reg first.  chi_min, dchi_max: host arrays of nblocks
  * doubles, in block order.  Synchronous. */
 int z4c_block_indicators(z4c_ctx *ctx, int reg, double *chi_min, double *dchi_max);
@@ -286,6 +287,24 @@ int z4c_block_indicators(z4c_ctx *ctx, int reg, double *chi_min, double *dchi_ma
  * Synchronous. */
 #define Z4C_MAX_PUNCTURES 64
 int z4c_track_punctures(z4c_ctx *ctx, int reg, int np, double *xyz, double dt, double *beta_out);
+
+/* Weyl scalar Psi4 on the grid (paper Sec. 3.3: the outgoing Weyl scalar in
+ * a coordinate tetrad; no interpolation onto spheres), in FP64, at every
+ * interior cell of every block:
+ *   Psi4 = (E_ij - i B_ij) mb^i mb^j,
+ *   E_ij = R_ij + K K_ij - K_ik gamma^kl K_lj,
+ *   B_ij = symmetric part of gamma_im eps^mkl D_k K_lj,
+ * from gamma_ij = gt_ij / chi, K_ij = (At_ij + gt_ij K / 3) / chi,
+ * K = Khat + 2 Theta, with the block's centred stencils; the tetrad
+ * mb = (e_theta - i e_phi) / sqrt(2) comes from Gram-Schmidt in gamma_ij on
+ * the coordinate vectors x^i, (-y, x, 0) and (x z, y z, -(x^2 + y^2)) about
+ * the origin.  Cells on the z axis (tetrad undefined) and all non-interior
+ * cells get 0.  Fills the ghost cells of register reg first.
+ * out_device: device, caller-owned, 2 * (register elements / 22) doubles:
+ * for each block in order, the real part over its storage cells
+ * ((n_z+2g) x (n_y+2g) x (n_x+2g), x fastest), then the imaginary part.
+ * Synchronous. */
+int z4c_psi4(z4c_ctx *ctx, int reg, void *out_device);
 
 /* Measurement aid: FP64 (fp64 = 1) or FP32 (fp64 = 0) fused multiply-add
  * throughput of the current device in FLOP/s, from independent FMA chains

@@ -331,11 +331,11 @@ int z4c_constraints_instance(z4c_ctx *ctx, int instance, double r_mask, double *
   if (per_cell_out)
     CK(cudaMemsetAsync(per_cell_out, 0, ctx->reg_elems / NF * 4 * sizeof(double), ctx->stream));
   const int nt = (int)ctx->ctiles.size();
-  for (int q = 0; q < 2; ++q)  // order-4 records first, then order-6 records
-    CK(launch_constraint_partials(q == 0 ? 4 : 6, ctx->reg[0], ctx->d_blocks(), ctx->d_ctiles(), nt, instance,
-                                  r_mask, (double *)per_cell_out, ctx->d_part() + (size_t)q * 8 * nt,
+  for (int q = 0; q < 3; ++q)  // order-4 records first, then order-6, then order-2 records
+    CK(launch_constraint_partials(q == 0 ? 4 : q == 1 ? 6 : 2, ctx->reg[0], ctx->d_blocks(), ctx->d_ctiles(), nt,
+                                  instance, r_mask, (double *)per_cell_out, ctx->d_part() + (size_t)q * 8 * nt,
                                   ctx->stream));
-  CK(launch_constraint_finalize(ctx->d_part(), 2 * nt, ctx->d_res(), ctx->stream));
+  CK(launch_constraint_finalize(ctx->d_part(), 3 * nt, ctx->d_res(), ctx->stream));
   double res[6];
   CK(cudaMemcpyAsync(res, ctx->d_res(), sizeof res, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
@@ -544,6 +544,19 @@ int z4c_block_indicators(z4c_ctx *ctx, int reg, double *chi_min, double *dchi_ma
                        ctx->at<int32_t>(ctx->o_cfirst), nb, ctx->d_part(), out, ctx->stream));
   CK(cudaMemcpyAsync(chi_min, out, sizeof(double) * nb, cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaMemcpyAsync(dchi_max, out + nb, sizeof(double) * nb, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return status_check(ctx);
+}
+
+int z4c_psi4(z4c_ctx *ctx, int reg, void *out_device) {
+  int r = ensure_bound(ctx);
+  if (r) return r;
+  if (reg < 0 || reg > 3 || !out_device) return fail(ctx, Z4C_ERR_BAD_ARG, "bad register or output");
+  r = fill_ghosts(ctx, ctx->reg[reg], nullptr);
+  if (r) return r;
+  CK(cudaMemsetAsync(out_device, 0, ctx->reg_elems / NF * 2 * sizeof(double), ctx->stream));
+  CK(launch_psi4(ctx->reg[reg], ctx->d_blocks(), ctx->d_ctiles(), (int)ctx->ctiles.size(), (double *)out_device,
+                 ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
   return status_check(ctx);
 }

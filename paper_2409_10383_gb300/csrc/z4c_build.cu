@@ -679,7 +679,7 @@ int z4c_create_batch(const z4c_instance *instances, int ninstances, const z4c_bl
   // diagnostics: per-block indicator outputs, tracker inputs and outputs
   ctx->o_diag = take(std::max(sizeof(double) * 2 * ctx->blocks.size(),
                               (sizeof(TrackIn) + sizeof(double) * 6) * Z4C_MAX_PUNCTURES));
-  ctx->o_part = take(sizeof(double) * 8 * 2 * ctx->ctiles.size());  // order-4 and order-6 records
+  ctx->o_part = take(sizeof(double) * 8 * 3 * ctx->ctiles.size());  // order-4, -6 and -2 records
   ctx->o_res = take(sizeof(double) * 8);
   ctx->o_dt = take(sizeof(double) * ctx->dblocks.size());
   if (ctx->has[1]) {

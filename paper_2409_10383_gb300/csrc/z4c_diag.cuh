@@ -1,5 +1,6 @@
 // Diagnostics beside the RK4 step (paper Sec. 3.2: refinement criteria on
-// chi; Sec. 3.3: puncture trackers), FP64.  Launchers in z4c_diag.cu.
+// chi; Sec. 3.3: puncture trackers and the Weyl scalar Psi4), FP64.
+// Launchers in z4c_diag.cu.
 #pragma once
 
 #include "z4c_rhs.cuh"
@@ -119,6 +120,31 @@ __global__ void track_kernel(const double *__restrict__ u, const DevBlock *__res
     out[6 * q + c] = p.x0[c] - dt * v;
     out[6 * q + 3 + c] = v;
   }
+}
+
+// Psi4 (psi4_point) at every interior cell of the blocks of order ORD, one
+// thread per cell over the interior tiles; out holds per block the real part
+// and then the imaginary part over the block's storage cells (offset
+// 2 off / NF), other cells untouched.
+template <int ORD>
+__global__ void __launch_bounds__(TX * TY) psi4_kernel(const double *__restrict__ u,
+                                                       const DevBlock *__restrict__ blocks,
+                                                       const Tile *__restrict__ tiles, double *__restrict__ out) {
+  const Tile t = tiles[blockIdx.x];
+  const DevBlock &b = blocks[t.block];
+  const int i = t.i0 + threadIdx.x, j = t.j0 + threadIdx.y, kk = t.k0;
+  if (b.order != ORD || i >= b.n[0] || j >= b.n[1]) return;
+  const int g = b.g, e0 = b.e[0], e1 = b.e[1];
+  const int32_t cidx = ((kk + g) * e1 + (j + g)) * e0 + (i + g);
+  const int st[3] = {1, e0, e0 * e1};
+  const Src<double, false> s{u + b.off, cidx, b.S};
+  const double ichi = 1.0 / fmax(s.at(CHI, 0), b.chi_floor);
+  const double x[3] = {b.lo[0] + (i + 0.5) * b.h, b.lo[1] + (j + 0.5) * b.h, b.lo[2] + (kk + 0.5) * b.h};
+  double v[2];
+  psi4_point<ORD>(s, st, scales_of(b, 0.0), ichi, x, v);
+  double *o = out + b.off / NF * 2 + cidx;
+  o[0] = v[0];
+  o[b.S] = v[1];
 }
 
 }  // namespace z4c

@@ -761,6 +761,173 @@ __device__ __forceinline__ void constraints_point(const SRC &s, const int st[3],
   }
 }
 
+// Weyl scalar Psi4 at one interior cell (Sec. 3.3: the outgoing Weyl
+// scalar in a coordinate tetrad), in FP64:
+//   Psi4 = (E_ij - i B_ij) mb^i mb^j,
+//   E_ij = R_ij + K K_ij - K_ik gamma^kl K_lj  (R_ij of gamma_ij = gt_ij / chi),
+//   B_ij = sym(gamma_im C^m_j), C^m_j = [mkl] D_k K_lj / sqrt(det gamma),
+//   K_ij = (At_ij + gt_ij K / 3) / chi, K = Khat + 2 Theta, its derivatives by
+//   the product rule, D_k with the Christoffels of gamma,
+//   G^m_kl = Gt^m_kl - (delta^m_k d_l chi + delta^m_l d_k chi
+//            - gt_kl gt^mn d_n chi) / (2 chi);
+//   mb = (e_th - i e_ph) / sqrt(2), Gram-Schmidt in gamma on x^i,
+//   (-y, x, 0) and (x z, y z, -(x^2 + y^2)), in that order.
+// x: the cell centre; 0 on the z axis, where the tetrad is undefined.
+template <int ORD, class SRC>
+__device__ __forceinline__ void psi4_point(const SRC &s, const int st[3], const Scales<double> &sc, double ichi,
+                                           const double x[3], double out[2]) {
+  using F = FD<ORD>;
+  using R = double;
+  out[0] = out[1] = 0.0;
+  if (x[0] * x[0] + x[1] * x[1] == 0.0) return;
+  const R K = s.val(KHAT) + 2.0 * s.val(THETA);
+  R g[6], A[6], gi[6];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    g[q] = s.val(GXX + q);
+    A[q] = s.val(AXX + q);
+  }
+  inverse_metric(g, gi);
+  R dchi[3], dK[3], dGam[3][3], dg[3][6], dA[3][6];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    dchi[d] = F::d1(s, CHI, st[d]) * sc.s1;
+    dK[d] = (F::d1(s, KHAT, st[d]) + 2.0 * F::d1(s, THETA, st[d])) * sc.s1;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) dGam[d][i] = F::d1(s, GAMX + i, st[d]) * sc.s1;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      dg[d][q] = F::d1(s, GXX + q, st[d]) * sc.s1;
+      dA[d][q] = F::d1(s, AXX + q, st[d]) * sc.s1;
+    }
+  }
+  R Gl[3][6], Gu[3][6], Gd[3];
+  christoffel(gi, dg, Gl, Gu, Gd);
+  R DDchi[6];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = i; j < 3; ++j) {
+      const int q = S6(i, j);
+      R ddc = i == j ? F::d2(s, CHI, st[i]) * sc.s2 : F::mix(s, CHI, st[i], st[j]) * sc.smix;
+      DDchi[q] = ddc - (Gu[0][q] * dchi[0] + Gu[1][q] * dchi[1] + Gu[2][q] * dchi[2]);
+    }
+  R Ric[6];
+  const Direct<ORD, double, SRC> dv{s, st, sc};
+  ricci(dv, ichi, g, gi, dchi, dGam, Gl, Gu, Gd, DDchi, Ric);
+
+  // physical metric and extrinsic curvature
+  R gam[6], gamu[6], Kd[6], dKd[3][6];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    gam[q] = g[q] * ichi;
+    gamu[q] = gi[q] / ichi;
+    Kd[q] = fma(g[q], K * (1.0 / 3.0), A[q]) * ichi;
+  }
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+#pragma unroll
+    for (int q = 0; q < 6; ++q)
+      dKd[d][q] = (dA[d][q] + (dg[d][q] * K + g[q] * dK[d]) * (1.0 / 3.0) - Kd[q] * dchi[d]) * ichi;
+  // Christoffels of gamma
+  R gd[3], Gp[3][6];
+#pragma unroll
+  for (int m = 0; m < 3; ++m) gd[m] = gi[S6(m, 0)] * dchi[0] + gi[S6(m, 1)] * dchi[1] + gi[S6(m, 2)] * dchi[2];
+#pragma unroll
+  for (int m = 0; m < 3; ++m)
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int l = k; l < 3; ++l) {
+        const int q = S6(k, l);
+        const R c = (m == k ? dchi[l] : 0.0) + (m == l ? dchi[k] : 0.0) - g[q] * gd[m];
+        Gp[m][q] = Gu[m][q] - 0.5 * ichi * c;
+      }
+  // E_ij
+  R E[6];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = i; j < 3; ++j) {
+      R kk = 0.0;
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int l = 0; l < 3; ++l) kk += Kd[S6(i, k)] * gamu[S6(k, l)] * Kd[S6(l, j)];
+      E[S6(i, j)] = Ric[S6(i, j)] + K * Kd[S6(i, j)] - kk;
+    }
+  // D_k K_lj and its curl C^m_j
+  R DK[3][3][3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int l = 0; l < 3; ++l)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        R v = dKd[k][S6(l, j)];
+#pragma unroll
+        for (int m = 0; m < 3; ++m) v -= Gp[m][S6(k, l)] * Kd[S6(m, j)] + Gp[m][S6(k, j)] * Kd[S6(l, m)];
+        DK[k][l][j] = v;
+      }
+  const R detg = g[0] * (g[3] * g[5] - g[4] * g[4]) - g[1] * (g[1] * g[5] - g[4] * g[2]) +
+                 g[2] * (g[1] * g[4] - g[3] * g[2]);
+  const R isq = 1.0 / (sqrt(detg) * ichi * sqrt(ichi));  // 1 / sqrt(det gamma)
+  R C[3][3];
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    C[0][j] = (DK[1][2][j] - DK[2][1][j]) * isq;
+    C[1][j] = (DK[2][0][j] - DK[0][2][j]) * isq;
+    C[2][j] = (DK[0][1][j] - DK[1][0][j]) * isq;
+  }
+  R Bt[3][3], B[6];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) Bt[i][j] = gam[S6(i, 0)] * C[0][j] + gam[S6(i, 1)] * C[1][j] + gam[S6(i, 2)] * C[2][j];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = i; j < 3; ++j) B[S6(i, j)] = 0.5 * (Bt[i][j] + Bt[j][i]);
+  // tetrad: e[0] radial, e[1] phi, e[2] theta
+  R e[3][3];
+  const R u[3][3] = {{x[0], x[1], x[2]},
+                     {-x[1], x[0], 0.0},
+                     {x[0] * x[2], x[1] * x[2], -(x[0] * x[0] + x[1] * x[1])}};
+  auto dotg = [&](const R *a, const R *b) {
+    R v = 0.0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) v += gam[S6(i, j)] * a[i] * b[j];
+    return v;
+  };
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    R v[3] = {u[a][0], u[a][1], u[a][2]};
+#pragma unroll
+    for (int b = 0; b < a; ++b) {
+      const R d = dotg(e[b], v);
+#pragma unroll
+      for (int i = 0; i < 3; ++i) v[i] -= d * e[b][i];
+    }
+    const R inv = 1.0 / sqrt(dotg(v, v));
+#pragma unroll
+    for (int i = 0; i < 3; ++i) e[a][i] = v[i] * inv;
+  }
+  auto quadf = [&](const R *X, const R *a, const R *b) {
+    R v = 0.0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) v += X[S6(i, j)] * a[i] * b[j];
+    return v;
+  };
+  const R *ph = e[1], *th = e[2];
+  // mb^i mb^j = (th th - ph ph - i (th ph + ph th)) / 2
+  out[0] = 0.5 * (quadf(E, th, th) - quadf(E, ph, ph)) - quadf(B, th, ph);
+  out[1] = -quadf(E, th, ph) - 0.5 * (quadf(B, th, th) - quadf(B, ph, ph));
+}
+
 // ---- FP64 stage epilogue: RK update and algebraic constraint enforcement ----
 
 // Float <-> double conversions on the integer pipe.  On this part FP64-pipe

@@ -27,7 +27,7 @@ EXPORTS = ("z4c_create", "z4c_create_batch", "z4c_set_initial_data_instance", "z
            "z4c_constraints", "z4c_get_state", "z4c_set_state", "z4c_evolve_host",
            "z4c_sync", "z4c_profile_steps", "z4c_set_variant", "z4c_autotune", "z4c_peak_fma", "z4c_constraints_static",
            "z4c_launches_per_step", "z4c_last_error", "z4c_destroy", "z4c_block_indicators",
-           "z4c_track_punctures")
+           "z4c_track_punctures", "z4c_psi4")
 Z4C_MAX_PUNCTURES = 64
 
 
@@ -93,6 +93,7 @@ def lib():
             "z4c_constraints_static": (I, [P, P, I, I, P, D, D, D, P, P]),
             "z4c_block_indicators": (I, [P, I, P, P]),
             "z4c_track_punctures": (I, [P, I, I, P, D, P]),
+            "z4c_psi4": (I, [P, I, P]),
             "z4c_launches_per_step": (I, [P]),
             "z4c_last_error": (ctypes.c_char_p, [P]),
             "z4c_destroy": (None, [P]),
@@ -320,6 +321,19 @@ class Z4c:
         _check(lib().z4c_track_punctures(self.ctx, int(reg), len(x), x.ctypes.data, float(dt), beta.ctypes.data),
                self.ctx, "z4c_track_punctures")
         return x, beta
+
+    def z4c_psi4(self, reg=REG_U0, out=None):
+        """Weyl scalar Psi4 (paper Sec. 3.3, coordinate tetrad) at every
+        interior cell: a device tensor of 2 * (register elements / 22)
+        doubles, per block the real part then the imaginary part over its
+        storage cells; fills reg's ghosts first."""
+        n = 2 * (self.nelem // 22)
+        if out is None:
+            out = self.torch.empty(n, dtype=self.torch.float64, device=self.regs[0].device)
+        self._enter()
+        _check(lib().z4c_psi4(self.ctx, int(reg), out.data_ptr()), self.ctx, "z4c_psi4")
+        self._leave(out)
+        return out
 
     def z4c_profile_steps(self, dt, nsteps):
         ms = np.zeros(4)
