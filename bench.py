@@ -44,17 +44,17 @@ L2_BYTES = 129 * 2 ** 20
 # (dadd, dfma, dmul; exact integers per cell) of a one-block 64^3 order-6
 # capture, stage-1 launch:
 # flops = dadd + dmul + 2 dfma.
-FP64_OPS_PER_CELL_STAGE = {6: dict(dadd=534, dfma=1499, dmul=531),
+FP64_OPS_PER_CELL_STAGE = {6: dict(dadd=533, dfma=1392, dmul=516),
                            # 2nd order, 2 ghosts: interior_pre_kernel<2,false,1,false,68>
-                           2: dict(dadd=351, dfma=1037, dmul=518)}
+                           2: dict(dadd=349, dfma=931, dmul=503)}
 # DRAM bytes (read + write) per interior cell of that launch
-FP64_DRAM_BYTES_PER_CELL = {6: (121226496 + 93064704) / 262144, 2: (114322688 + 63602432) / 262144}
+FP64_DRAM_BYTES_PER_CELL = {6: (121026816 + 85157632) / 262144, 2: (114210560 + 63556864) / 262144}
 # FP32-RHS split schedule (interior_pre_kernel<6,true,4,split,72> storing k
 # + split_epilogue_kernel): executed FP32 operations and the FP64 residue per
 # interior cell per stage, from the same kind of capture
-FP32_OPS_PER_CELL_STAGE = {6: dict(fadd=1086, ffma=1381, fmul=522)}
+FP32_OPS_PER_CELL_STAGE = {6: dict(fadd=1085, ffma=1274, fmul=507)}
 FP32_F64_RESIDUE_PER_CELL_STAGE = {6: dict(dadd=47, dfma=22, dmul=25)}
-FP32_DRAM_BYTES_PER_CELL = {6: (62101504 + 4483840 + 77116416 + 28987392) / 262144}
+FP32_DRAM_BYTES_PER_CELL = {6: (62101760 + 4572416 + 77183744 + 29128448) / 262144}
 # algorithmic HBM bytes per zone-cycle (fused 3-register RK4, 22 FP64 fields;
 # the same for the FP32-RHS path, whose state stays FP64)
 ALG_BYTES_PER_ZONE_CYCLE = 352 * 8

@@ -397,24 +397,26 @@ __device__ __forceinline__ void christoffel(const R gi[6], const R dg[3][6], R G
 //   Rchi_ij = (DDchi_ij + gt_ij gt^lm DDchi_lm) / (2 chi)
 //             - (d_i chi d_j chi + 3 gt_ij gt^lm d_l chi d_m chi) / (4 chi^2)
 // with DDchi_ij = d_i d_j chi - Gt^k_ij d_k chi and 1/chi -> ichi.
+// The quadratic Christoffel terms are summed as
+//   sum_km U[k][m][i] d_m gt_jk + U[k][m][j] Gt_ikm,  U[k][m][i] = gt^lm Gt^k_li:
+// the term gt^lm Gt^k_im Gt_klj equals sum_km U[k][m][i] Gt_kmj, and
+// Gt_jkm + Gt_kmj = d_m gt_jk by the definition of Gt_ijk, so two of the
+// three contractions collapse into one against the metric derivatives.
 template <class R, class DV>
 __device__ __forceinline__ void ricci(const DV &dv, R ichi,
-                                      const R g[6], const R gi[6], const R dchi[3],
+                                      const R g[6], const R gi[6], const R dchi[3], const R dg[3][6],
                                       const R dGam[3][3], const R Gl[3][6], const R Gu[3][6],
                                       const R Gd[3], const R DDchi[6], R Ric[6]) {
-  // U[k][m][i] = gt^lm Gt^k_li ; V[k][m][j] = gt^lm Gt_klj
-  R U[3][3][3], V[3][3][3];
+  // U[k][m][i] = gt^lm Gt^k_li
+  R U[3][3][3];
 #pragma unroll
   for (int k2 = 0; k2 < 3; ++k2)
 #pragma unroll
     for (int m = 0; m < 3; ++m)
 #pragma unroll
-      for (int i = 0; i < 3; ++i) {
+      for (int i = 0; i < 3; ++i)
         U[k2][m][i] = gi[S6(0, m)] * Gu[k2][S6(0, i)] + gi[S6(1, m)] * Gu[k2][S6(1, i)] +
                       gi[S6(2, m)] * Gu[k2][S6(2, i)];
-        V[k2][m][i] = gi[S6(0, m)] * Gl[k2][S6(0, i)] + gi[S6(1, m)] * Gl[k2][S6(1, i)] +
-                      gi[S6(2, m)] * Gl[k2][S6(2, i)];
-      }
   const R trDDchi = trsym(gi, DDchi);
   const R dchi2 = quad(gi, dchi, dchi);
 #pragma unroll
@@ -442,9 +444,7 @@ __device__ __forceinline__ void ricci(const DV &dv, R ichi,
 #pragma unroll
       for (int k2 = 0; k2 < 3; ++k2)
 #pragma unroll
-        for (int m = 0; m < 3; ++m)
-          t += U[k2][m][i] * Gl[j][S6(k2, m)] + U[k2][m][j] * Gl[i][S6(k2, m)] +
-               Gu[k2][S6(i, m)] * V[k2][m][j];
+        for (int m = 0; m < 3; ++m) t += U[k2][m][i] * dg[m][S6(j, k2)] + U[k2][m][j] * Gl[i][S6(k2, m)];
       r += t;
       R rc = R(0.5) * ichi * (DDchi[q] + g[q] * trDDchi) -
              R(0.25) * ichi * ichi * (dchi[i] * dchi[j] + R(3) * g[q] * dchi2);
@@ -515,7 +515,7 @@ __device__ __forceinline__ void rhs_point(const SRC &s, const DV &dv, const int 
   auto quad = [&](const R *a, const R *b) { return z4c::quad(gi, a, b); };
 
   R Ric[6];
-  ricci(dv, ichi, g, gi, dchi, dGam, Gl, Gu, Gd, DDchi, Ric);
+  ricci(dv, ichi, g, gi, dchi, dg, dGam, Gl, Gu, Gd, DDchi, Ric);
   const R Rs = chi * trsym(Ric);
 
   // D_i D_j alpha and its trace
@@ -711,7 +711,7 @@ __device__ __forceinline__ void constraints_point(const SRC &s, const int st[3],
     }
   R Ric[6];
   const Direct<ORD, double, SRC> dv{s, st, sc};
-  ricci(dv, ichi, g, gi, dchi, dGam, Gl, Gu, Gd, DDchi, Ric);
+  ricci(dv, ichi, g, gi, dchi, dg, dGam, Gl, Gu, Gd, DDchi, Ric);
   // At^ij and At_ij At^ij
   R M[3][3];
 #pragma unroll
@@ -814,7 +814,7 @@ __device__ __forceinline__ void psi4_point(const SRC &s, const int st[3], const 
     }
   R Ric[6];
   const Direct<ORD, double, SRC> dv{s, st, sc};
-  ricci(dv, ichi, g, gi, dchi, dGam, Gl, Gu, Gd, DDchi, Ric);
+  ricci(dv, ichi, g, gi, dchi, dg, dGam, Gl, Gu, Gd, DDchi, Ric);
 
   // physical metric and extrinsic curvature
   R gam[6], gamu[6], Kd[6], dKd[3][6];
