@@ -135,15 +135,32 @@ int launch_fused_group(z4c_ctx *ctx, int g, const StageArgs &a) {
   return Z4C_OK;
 }
 
-int launch_sommerfeld_p(z4c_ctx *ctx, int p, const StageArgs &a) {
+int launch_sommerfeld_p(z4c_ctx *ctx, int p, const StageArgs &a, cudaStream_t st) {
   const int n = (int)ctx->somm[p].size();
   if (!n) return Z4C_OK;
-  CK(launch_sommerfeld(p == 1, a, ctx->d_somm(p), n, ctx->stream));
+  CK(launch_sommerfeld(p == 1, a, ctx->d_somm(p), n, st));
   return Z4C_OK;
 }
 
-// RHS + stage update of every group, then the Sommerfeld cells
-int launch_stage(z4c_ctx *ctx, const StageArgs &base) {
+// RHS + stage update of every group, and the Sommerfeld cells.  The
+// Sommerfeld kernel reads the stage state (its cells and their neighbours)
+// and writes the next state, accumulator and shadow at its own cells only;
+// the interior kernels write only interior cells and their own scratch.  So
+// with fork set (a captured step) the Sommerfeld cells run on the side
+// stream beside the interior kernels, joined before the stage ends; else
+// they follow on the context's stream.
+int launch_stage(z4c_ctx *ctx, const StageArgs &base, bool fork = false) {
+  const bool any_somm = !ctx->somm[0].empty() || !ctx->somm[1].empty();
+  fork = fork && any_somm && ctx->stream != nullptr && ctx->side != nullptr;
+  if (fork) {
+    CK(cudaEventRecord(ctx->ev_fork, ctx->stream));
+    CK(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
+    for (int p = 0; p < 2; ++p) {
+      const int r = launch_sommerfeld_p(ctx, p, group_args(ctx, base, p == 1), ctx->side);
+      if (r) return r;
+    }
+    CK(cudaEventRecord(ctx->ev_join, ctx->side));
+  }
   for (int g = 0; g < NGRP; ++g) {
     const StageArgs a = group_args(ctx, base, ctx->grp[g].f32);
     int r = launch_prepass_group(ctx, g, a);
@@ -151,8 +168,12 @@ int launch_stage(z4c_ctx *ctx, const StageArgs &base) {
     r = launch_fused_group(ctx, g, a);
     if (r) return r;
   }
+  if (fork) {
+    CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_join, 0));
+    return Z4C_OK;
+  }
   for (int p = 0; p < 2; ++p) {
-    const int r = launch_sommerfeld_p(ctx, p, group_args(ctx, base, p == 1));
+    const int r = launch_sommerfeld_p(ctx, p, group_args(ctx, base, p == 1), ctx->stream);
     if (r) return r;
   }
   return Z4C_OK;
@@ -184,12 +205,14 @@ StageArgs stage_args(z4c_ctx *ctx, int s) {
   return a;
 }
 
-int enqueue_step(z4c_ctx *ctx) {
+// One RK4 step; fork: run each stage's Sommerfeld cells on the side stream
+// (the captured graph's branch)
+int enqueue_step(z4c_ctx *ctx, bool fork = false) {
   for (int s = 0; s < 4; ++s) {
     const StageArgs a = stage_args(ctx, s);
     int r = fill_ghosts(ctx, const_cast<double *>(a.x64), ctx->has[1] ? ctx->d_sh(s % 2) : nullptr);
     if (r) return r;
-    r = launch_stage(ctx, a);
+    r = launch_stage(ctx, a, fork);
     if (r) return r;
   }
   return Z4C_OK;
@@ -299,8 +322,13 @@ int z4c_rk4_step_batch(z4c_ctx *ctx, const double *dt_per_instance, int nsteps) 
   }
   if (!ctx->graph) {  // the step reads dt from the device table: one graph serves every dt
     cudaGraph_t g = nullptr;
+    if (ctx->fork_somm && !ctx->side) {  // before the capture begins
+      CK(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
+      CK(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
+    }
     CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-    r = enqueue_step(ctx);
+    r = enqueue_step(ctx, ctx->fork_somm);
     cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
     if (r) {
       if (g) cudaGraphDestroy(g);
@@ -445,7 +473,7 @@ int z4c_profile_steps(z4c_ctx *ctx, double dt, int nsteps, double *ms) {
       if (r) return r;
       r = timed(2, [&] {
         for (int p = 0; p < 2; ++p) {
-          const int rr = launch_sommerfeld_p(ctx, p, group_args(ctx, a, p == 1));
+          const int rr = launch_sommerfeld_p(ctx, p, group_args(ctx, a, p == 1), ctx->stream);
           if (rr) return rr;
         }
         return (int)Z4C_OK;
@@ -645,6 +673,7 @@ const char *z4c_last_error(const z4c_ctx *ctx) { return ctx ? ctx->err.c_str() :
 void z4c_destroy(z4c_ctx *ctx) {
   if (!ctx) return;
   ctx->drop_graph();
+  ctx->drop_side();
   delete ctx;
 }
 

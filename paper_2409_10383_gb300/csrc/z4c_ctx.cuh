@@ -130,6 +130,19 @@ struct z4c_ctx {
       graph = nullptr;
     }
   }
+  // side stream and fork/join events of the captured step: the Sommerfeld
+  // cells of a stage run beside its interior kernels (created on first
+  // capture, released with the context)
+  bool fork_somm = true;
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  void drop_side() {
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
+    if (side) cudaStreamDestroy(side);
+    side = nullptr;
+    ev_fork = ev_join = nullptr;
+  }
 };
 
 namespace z4c {
