@@ -166,6 +166,14 @@ def uneven_batch_small(seed: int = SEED):
     return uneven_batch(seed, sizes=(8, 12, 16, 20), n_puncture=6, n_wave=2)
 
 
+def mixed_order_batch_small(seed: int = SEED):
+    """uneven_batch_small plus two 2nd-order (2 ghosts) instances: an FP64
+    puncture of 12^3 and an FP32-RHS gauge wave of 16^3, so that all three
+    differencing orders share one batch."""
+    return uneven_batch_small(seed) + [_instance("puncture", 12, 2, 64, 1.0),
+                                       _instance("gauge_wave", 16, 2, 32, 0.05)]
+
+
 # ---------------------------------------------------------------------------
 # static mesh refinement: oct-tree of equal MeshBlocks (paper Sec. 3, 2:1)
 # ---------------------------------------------------------------------------

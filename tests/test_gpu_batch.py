@@ -1,6 +1,6 @@
 """Batched evolution of independent problems (one graph launch per RK4 step).
 
-A batch mixes block sizes, orders 4/6, FP64 and FP32-RHS, punctures and
+A batch mixes block sizes, orders 2/4/6, FP64 and FP32-RHS, punctures and
 gauge waves, each instance with its own dt.  Packing must not change any
 instance's arithmetic: every instance's state is bit-identical to the same
 instance evolved alone, FP64 instances match the oracle (1e-10), and the
@@ -28,9 +28,11 @@ def _dt(w):
     return w["cfl"] * float(w["h"][0])
 
 
-def test_batch_equals_single_instances(oracle):
+@pytest.mark.parametrize("mix", ["uneven_batch_small", "mixed_order_batch_small"])
+def test_batch_equals_single_instances(oracle, mix):
+    """mixed_order_batch_small adds 2nd-order instances (FP64 and FP32-RHS)."""
     from paper_2409_10383_gb300.z4c import Z4c
-    ws = inputs.uneven_batch_small()
+    ws = getattr(inputs, mix)()
     g = Z4c.batch(ws)
     for i, w in enumerate(ws):
         g.z4c_set_initial_data_instance(i, w["id_kind"], w["id_par"])
