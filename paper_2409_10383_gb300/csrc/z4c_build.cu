@@ -683,9 +683,9 @@ int z4c_create_batch(const z4c_instance *instances, int ninstances, const z4c_bl
   ctx->o_res = take(sizeof(double) * 8);
   ctx->o_dt = take(sizeof(double) * ctx->dblocks.size());
   if (ctx->has[1]) {
-    ctx->o_sh0 = take(sizeof(float) * ctx->reg_elems);
-    ctx->o_sh1 = take(sizeof(float) * ctx->reg_elems);
-    ctx->o_ds32 = take(sizeof(float) * ctx->reg_elems);
+    ctx->o_sh0 = take(sizeof(float) * ctx->reg_elems + z4c_ctx::F32_SHIFT);
+    ctx->o_sh1 = take(sizeof(float) * ctx->reg_elems + z4c_ctx::F32_SHIFT);
+    ctx->o_ds32 = take(sizeof(float) * ctx->reg_elems + z4c_ctx::F32_SHIFT);
   }
   if (ctx->has[0]) ctx->o_ds64 = take(sizeof(double) * ctx->reg_elems);
   ctx->o_status = take(sizeof(int32_t));

@@ -118,8 +118,14 @@ struct z4c_ctx {
   double *d_part() const { return (double *)(scratch + o_part); }
   double *d_res() const { return (double *)(scratch + o_res); }
   double *d_dt() const { return (double *)(scratch + o_dt); }
-  float *d_sh(int q) const { return (float *)(scratch + (q == 0 ? o_sh0 : o_sh1)); }
-  void *d_dstore(bool f32) const { return scratch + (f32 ? o_ds32 : o_ds64); }
+  // FP32 arrays in the state layout start 16 bytes past a 256-byte boundary:
+  // with 4 ghosts and a row length that is a multiple of 8 floats, every
+  // row's interior then starts on a 32-byte sector boundary, so a warp's
+  // 16-float row slice spans 2 sectors instead of 3 (the FP64 layout is
+  // already aligned: 4 ghosts are 32 bytes)
+  static constexpr size_t F32_SHIFT = 16;
+  float *d_sh(int q) const { return (float *)(scratch + (q == 0 ? o_sh0 : o_sh1) + F32_SHIFT); }
+  void *d_dstore(bool f32) const { return f32 ? scratch + o_ds32 + F32_SHIFT : scratch + o_ds64; }
   bool smr() const { return !prol.empty() || !rghost.empty() || !pbox.empty(); }
   template <class T>
   const T *at(size_t o) const { return (const T *)(scratch + o); }
