@@ -650,7 +650,7 @@ __device__ __forceinline__ void rhs_point(const SRC &s, const DV &dv, const int 
       // into a register array costs a compare-and-select per element)
       __shared__ R kko[NF][TX * TY];
       const int tid = threadIdx.y * TX + threadIdx.x;
-#pragma unroll 1
+#pragma unroll 2
       for (int f = 0; f < NF; ++f)
         kko[f][tid] = (!p.shift && f >= BETAX) ? R(0) : kaw.apply_diff(s, f, st);
 #pragma unroll
