@@ -333,6 +333,45 @@ def measure(z4c, torch, workload, prec, args, ws, local):
     return out
 
 
+def fp32_accuracy(z4c, workload, steps=20):
+    """FP32-RHS against FP64 on the benchmark workload, both evolved `steps`
+    RK4 steps from the same initial data: the relative differences of the
+    Hamiltonian-constraint L2 norm and of the puncture lapse (min alpha over
+    the interior cells), and per field the largest |u32 - u64| over the
+    largest change of the FP64 field, max|u64(t) - u64(0)|, over the
+    interior cells."""
+    dt = workload["cfl"] * float(workload["h"][0])
+    nb = len(workload["n"])
+    # interior cells only (uniform blocks): the ghost cells of a register are
+    # not part of the evolved state (an FP32-RHS context refreshes only the
+    # FP32 shadow's ghosts)
+    n, gw = [int(v) for v in workload["n"][0]], int(workload["ghosts"])
+    inter = np.zeros((n[2] + 2 * gw, n[1] + 2 * gw, n[0] + 2 * gw), bool)
+    inter[gw:gw + n[2], gw:gw + n[1], gw:gw + n[0]] = True
+    inter = inter.ravel()
+    res = {}
+    for prec in (64, 32):
+        g = z4c.Z4c.from_workload(workload, precision=prec)
+        g.z4c_set_initial_data(workload["id_kind"], workload["id_par"])
+        if prec == 64:
+            u0 = g.z4c_get_state().reshape(nb, 22, -1)[:, :, inter]
+        g.z4c_rk4_step(dt, steps)
+        u = g.z4c_get_state().reshape(nb, 22, -1)[:, :, inter]
+        norms = g.z4c_constraints(r_mask=1.0)[0]
+        res[prec] = (u, norms[0], float(u[:, 18].min()))
+        g.close()
+    (u64, h64, a64), (u32, h32, a32) = res[64], res[32]
+    change = np.abs(u64 - u0).max(axis=(0, 2))
+    diff = np.abs(u32 - u64).max(axis=(0, 2))
+    moved = change > 0
+    ratio = np.where(moved, diff / np.where(moved, change, 1.0), 0.0)
+    return {"steps": steps, "t": steps * dt,
+            "hamiltonian_l2": [h64, h32], "hamiltonian_l2_rel_diff": abs(h32 - h64) / h64,
+            "puncture_lapse": [a64, a32], "puncture_lapse_rel_diff": abs(a32 - a64) / a64,
+            "max_field_diff_over_change": float(ratio.max()), "worst_field": int(ratio.argmax()),
+            "note": "interior cells; min alpha is the lapse at the puncture; fields that did not change are skipped"}
+
+
 def measure_batch(z4c, torch, steps, warmup):
     """The uneven batch (80 independent single-block problems: punctures and
     gauge waves of 24^3..96^3, orders 4/6, FP64 and FP32-RHS) evolved
@@ -496,6 +535,10 @@ def main():
                   "roofline": q["roofline"], "e2e": q["e2e"], "gpu_launches": q["gpu_launches"],
                   "clocks": q["clocks"]}
 
+    acc32 = None
+    if rank == 0 and 64 in res and 32 in res:
+        acc32 = fp32_accuracy(z4c, workload)
+
     if rank != 0:
         if ws > 1:
             torch.distributed.destroy_process_group()
@@ -525,7 +568,8 @@ def main():
         line["fp32_rhs"] = {"value": q["value"], "unit": UNIT, "ms_per_step": q["ms_per_step"],
                             "dtype": "f32 stencils/algebra + f64 state, RK, 1/chi, enforcement",
                             "speedup_vs_fp64": q["value"] / r["value"], "roofline": q["roofline"],
-                            "e2e": q["e2e"], "gpu_launches": q["gpu_launches"], "clocks": q["clocks"]}
+                            "e2e": q["e2e"], "gpu_launches": q["gpu_launches"], "clocks": q["clocks"],
+                            "accuracy_vs_fp64": acc32}
     if batched is not None:
         line["batched"] = batched
     if smr is not None:

@@ -221,7 +221,10 @@ int z4c_constraints(z4c_ctx *ctx, double r_mask, double *norms, void *per_cell_o
 int z4c_constraints_instance(z4c_ctx *ctx, int instance, double r_mask, double *norms, void *per_cell_out);
 
 /* Copy register reg to / from host memory (bytes = z4c_state_bytes()).
- * Synchronous.  Pinned host memory makes the copy faster. */
+ * Synchronous.  Pinned host memory makes the copy faster.  The evolved
+ * state is the interior and Sommerfeld cells; ghost cells hold the values of
+ * the last fill of that register (call z4c_fill_ghosts first for current
+ * ones; for FP32-RHS blocks the RK4 step fills only the FP32 copy's ghosts). */
 int z4c_get_state(z4c_ctx *ctx, int reg, void *host, size_t bytes);
 int z4c_set_state(z4c_ctx *ctx, int reg, const void *host, size_t bytes);
 

@@ -197,7 +197,8 @@ def test_fp32_rhs_error_budget(oracle, order, schedule, occupancy):
       - one RHS call: per-field error <= 8x the error of the FP64 oracle fed
         the FP32-rounded state (the input-rounding floor);
       - 5 RK4 steps of the puncture: per-field |u32 - u64| <= 1e-3 of the
-        change |u64(t) - u64(0)|, and ||H||_2 within 1e-5 (relative) of FP64.
+        change |u64(t) - u64(0)|, the puncture lapse (min alpha) within 1e-3
+        of its change, and ||H||_2 within 1e-5 (relative) of FP64.
     Orders 6 and 2 (the staged schedule 3 exists for order 6 only)."""
     w = H.small_workload("puncture", order, (2, 2, 2), 16)
     m = H.oracle_mesh(oracle, w)
@@ -222,6 +223,10 @@ def test_fp32_rhs_error_budget(oracle, order, schedule, occupancy):
         d = np.concatenate([(m.blocks(v)[b][f] - m.blocks(u)[b][f])[m.evolved_mask(b)] for b in range(m.nblocks)])
         c = np.concatenate([(m.blocks(u)[b][f] - m.blocks(u0)[b][f])[m.evolved_mask(b)] for b in range(m.nblocks)])
         assert np.abs(d).max() <= 1e-3 * np.abs(c).max(), f
+    def min_lapse(x):
+        return min(m.blocks(x)[b][18][m.interior_mask(b)].min() for b in range(m.nblocks))
+    a0, a64, a32 = min_lapse(u0), min_lapse(u), min_lapse(v)
+    assert abs(a32 - a64) <= 1e-3 * abs(a64 - a0), (a32, a64, a0)
     m.fill_ghosts(u)
     m.fill_ghosts(v)
     n64, _ = m.constraints(u)
