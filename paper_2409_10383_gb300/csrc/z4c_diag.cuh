@@ -125,11 +125,14 @@ __global__ void track_kernel(const double *__restrict__ u, const DevBlock *__res
 // Psi4 (psi4_point) at every interior cell of the blocks of order ORD, one
 // thread per cell over the interior tiles; out holds per block the real part
 // and then the imaginary part over the block's storage cells (offset
-// 2 off / NF), other cells untouched.
-template <int ORD>
+// 2 off / NF), other cells untouched.  PRE: the y/z first derivatives of the
+// eleven fields with mixed second derivatives come from ds (the FP64
+// pre-pass arrays of u, as in the RHS); else every stencil reads u.
+template <int ORD, bool PRE>
 __global__ void __launch_bounds__(TX * TY) psi4_kernel(const double *__restrict__ u,
                                                        const DevBlock *__restrict__ blocks,
-                                                       const Tile *__restrict__ tiles, double *__restrict__ out) {
+                                                       const Tile *__restrict__ tiles, const double *__restrict__ ds,
+                                                       double *__restrict__ out) {
   const Tile t = tiles[blockIdx.x];
   const DevBlock &b = blocks[t.block];
   const int i = t.i0 + threadIdx.x, j = t.j0 + threadIdx.y, kk = t.k0;
@@ -138,10 +141,18 @@ __global__ void __launch_bounds__(TX * TY) psi4_kernel(const double *__restrict_
   const int32_t cidx = ((kk + g) * e1 + (j + g)) * e0 + (i + g);
   const int st[3] = {1, e0, e0 * e1};
   const Src<double, false> s{u + b.off, cidx, b.S};
+  const Scales<double> sc = scales_of(b, 0.0);
   const double ichi = 1.0 / fmax(s.at(CHI, 0), b.chi_floor);
   const double x[3] = {b.lo[0] + (i + 0.5) * b.h, b.lo[1] + (j + 0.5) * b.h, b.lo[2] + (kk + 0.5) * b.h};
   double v[2];
-  psi4_point<ORD>(s, st, scales_of(b, 0.0), ichi, x, v);
+  if constexpr (PRE) {
+    const Src<double, false> d{ds + b.off, cidx, b.S};
+    const Pre<ORD, double, Src<double, false>, Src<double, false>> dv{s, d, st, sc};
+    psi4_point<ORD>(s, dv, ichi, x, v);
+  } else {
+    const Direct<ORD, double, Src<double, false>> dv{s, st, sc};
+    psi4_point<ORD>(s, dv, ichi, x, v);
+  }
   double *o = out + b.off / NF * 2 + cidx;
   o[0] = v[0];
   o[b.S] = v[1];

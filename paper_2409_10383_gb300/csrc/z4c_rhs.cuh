@@ -772,11 +772,12 @@ __device__ __forceinline__ void constraints_point(const SRC &s, const int st[3],
 //            - gt_kl gt^mn d_n chi) / (2 chi);
 //   mb = (e_th - i e_ph) / sqrt(2), Gram-Schmidt in gamma on x^i,
 //   (-y, x, 0) and (x z, y z, -(x^2 + y^2)), in that order.
-// x: the cell centre; 0 on the z axis, where the tetrad is undefined.
-template <int ORD, class SRC>
-__device__ __forceinline__ void psi4_point(const SRC &s, const int st[3], const Scales<double> &sc, double ichi,
-                                           const double x[3], double out[2]) {
-  using F = FD<ORD>;
+// dv: the derivative provider (stencils of the state, or the y/z pre-pass
+// arrays as in the RHS).  x: the cell centre; 0 on the z axis, where the
+// tetrad is undefined.
+template <int ORD, class SRC, class DV>
+__device__ __forceinline__ void psi4_point(const SRC &s, const DV &dv, double ichi, const double x[3],
+                                           double out[2]) {
   using R = double;
   out[0] = out[1] = 0.0;
   if (x[0] * x[0] + x[1] * x[1] == 0.0) return;
@@ -791,14 +792,14 @@ __device__ __forceinline__ void psi4_point(const SRC &s, const int st[3], const 
   R dchi[3], dK[3], dGam[3][3], dg[3][6], dA[3][6];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    dchi[d] = F::d1(s, CHI, st[d]) * sc.s1;
-    dK[d] = (F::d1(s, KHAT, st[d]) + 2.0 * F::d1(s, THETA, st[d])) * sc.s1;
+    dchi[d] = dv.d1(CHI, d);
+    dK[d] = dv.d1(KHAT, d) + 2.0 * dv.d1(THETA, d);
 #pragma unroll
-    for (int i = 0; i < 3; ++i) dGam[d][i] = F::d1(s, GAMX + i, st[d]) * sc.s1;
+    for (int i = 0; i < 3; ++i) dGam[d][i] = dv.d1(GAMX + i, d);
 #pragma unroll
     for (int q = 0; q < 6; ++q) {
-      dg[d][q] = F::d1(s, GXX + q, st[d]) * sc.s1;
-      dA[d][q] = F::d1(s, AXX + q, st[d]) * sc.s1;
+      dg[d][q] = dv.d1(GXX + q, d);
+      dA[d][q] = dv.d1(AXX + q, d);
     }
   }
   R Gl[3][6], Gu[3][6], Gd[3];
@@ -809,11 +810,10 @@ __device__ __forceinline__ void psi4_point(const SRC &s, const int st[3], const 
 #pragma unroll
     for (int j = i; j < 3; ++j) {
       const int q = S6(i, j);
-      R ddc = i == j ? F::d2(s, CHI, st[i]) * sc.s2 : F::mix(s, CHI, st[i], st[j]) * sc.smix;
+      R ddc = i == j ? dv.d2(CHI, i) : dv.mix(CHI, i, j);
       DDchi[q] = ddc - (Gu[0][q] * dchi[0] + Gu[1][q] * dchi[1] + Gu[2][q] * dchi[2]);
     }
   R Ric[6];
-  const Direct<ORD, double, SRC> dv{s, st, sc};
   ricci(dv, ichi, g, gi, dchi, dg, dGam, Gl, Gu, Gd, DDchi, Ric);
 
   // physical metric and extrinsic curvature

@@ -127,3 +127,19 @@ def test_psi4_batch(oracle):
         off += n2
     assert off == got.size
     g.close()
+
+
+def test_psi4_fp32_only_context(oracle):
+    """A context with FP32-RHS blocks only has no FP64 pre-pass store: Psi4
+    then takes every stencil from the FP64 state (the other kernel form)."""
+    from paper_2409_10383_gb300.z4c import Z4c
+    w = H.small_workload("puncture", 6, (2, 1, 1), 12)
+    m = H.oracle_mesh(oracle, w)
+    g = Z4c.from_workload(w, precision=32)
+    g.z4c_set_initial_data(w["id_kind"], w["id_par"])
+    g.z4c_rk4_step(0.25 * float(w["h"][0]), 2)
+    got = g.z4c_psi4().cpu().numpy()
+    u = g.z4c_get_state()
+    m.fill_ghosts(u)
+    _compare(m, u, got)
+    g.close()
