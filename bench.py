@@ -47,6 +47,12 @@ L2_BYTES = 129 * 2 ** 20
 FP64_OPS_PER_CELL_STAGE = {6: dict(dadd=533, dfma=1392, dmul=516),
                            # 2nd order, 2 ghosts: interior_pre_kernel<2,false,1,false,68>
                            2: dict(dadd=349, dfma=931, dmul=503)}
+# The same method as the oracle writes it out (oracle/flopcount.py: the
+# oracle's RK4 step on a counting scalar type, per interior cell and stage):
+# 49-point mixed stencils, separate KO and advection, full index loops.
+# Reported beside the executed count as the cross-check; dividing it by the
+# kernel time would read several times the FP64 peak.
+ORACLE_FLOPS_PER_CELL_STAGE = {6: 21266.0, 4: 14184.6, 2: 9146.7}
 # DRAM bytes (read + write) per interior cell of that launch
 FP64_DRAM_BYTES_PER_CELL = {6: (121026816 + 85157632) / 262144, 2: (114210560 + 63556864) / 262144}
 # FP32-RHS split schedule (interior_pre_kernel<6,true,4,split,72> storing k
@@ -246,7 +252,10 @@ def measure(z4c, torch, workload, prec, args, ws, local):
                 "peak_source": "measured DFMA throughput (z4c_peak_fma), FMA = 2 flops",
                 "peak_nominal": NOMINAL_FP64 / 1e12,
                 "fp64_issue_frac": insts / (interior_ms * 1e-3) / (peak64 / 2),
-                "flops_per_cell_stage": flops / cells}
+                "flops_per_cell_stage": flops / cells,
+                "oracle_flops_per_cell_stage": ORACLE_FLOPS_PER_CELL_STAGE.get(order),
+                "flops_note": "achieved counts the FP64 flops the kernel executes (ncu); the oracle's "
+                              "plain formulation of the same step counts oracle_flops_per_cell_stage"}
     elif prec == 32 and order in FP32_OPS_PER_CELL_STAGE:
         # the slower of: FP32 flops at the FP32 peak, FP64-residue flops at
         # the FP64 peak, algorithmic bytes at the HBM bandwidth
