@@ -237,6 +237,10 @@ def measure(z4c, torch, workload, prec, args, ws, local):
     interior_ms = kms[1] / 4.0  # per launch (4 stages per step)
     peak64 = z4c.z4c_peak_fma(True, st)
     peak32 = z4c.z4c_peak_fma(False, st)
+    conv = None
+    if prec == 32:  # the FP32-RHS path converts every field twice per stage
+        conv = {k: z4c.z4c_peak_convert(m, st) for k, m in
+                (("f2d_hw", 0), ("f2d_int", 1), ("d2f_hw", 2), ("d2f_int", 3))}
     order = workload["order"]
     if prec == 64 and order in FP64_OPS_PER_CELL_STAGE:
         ops = FP64_OPS_PER_CELL_STAGE[order]
@@ -302,6 +306,8 @@ def measure(z4c, torch, workload, prec, args, ws, local):
                           "interior": kms[1] / kms.sum(), "sommerfeld": kms[2] / kms.sum()}
     roof["fp64_fma_peak_tflops"] = peak64 / 1e12
     roof["fp32_fma_peak_tflops"] = peak32 / 1e12
+    if conv:
+        roof["conversions_per_s"] = conv
 
     # end to end through the C ABI with pinned host buffers: every step copies
     # the state host -> device, runs one RK4 step and copies it back

@@ -315,6 +315,15 @@ int z4c_psi4(z4c_ctx *ctx, int reg, void *out_device);
  * cuda_stream and synchronised.  Allocates nothing. */
 int z4c_peak_fma(int fp64, void *cuda_stream, double *flops_per_s);
 
+/* Measurement aid: float <-> double conversions per second of the current
+ * device (the FP32-RHS path's conversion cost).  mode 0: float -> double by
+ * the hardware conversion; 1: the same by the integer-pipe bit manipulation
+ * the FP32-RHS kernels use; 2: double -> float by the hardware (round to
+ * nearest even); 3: the same on the integer pipe.  Independent chains with
+ * no memory traffic; enqueued on cuda_stream and synchronised.  Allocates
+ * nothing.  Z4C_ERR_BAD_ARG for another mode. */
+int z4c_peak_convert(int mode, void *cuda_stream, double *conv_per_s);
+
 /* Constraint norms of one MeshBlock without any device allocation.
  *
  * The paper has no counterpart to this call; it exists for callers that

@@ -658,6 +658,13 @@ int z4c_peak_fma(int fp64, void *cuda_stream, double *flops_per_s) {
   return Z4C_OK;
 }
 
+int z4c_peak_convert(int mode, void *cuda_stream, double *conv_per_s) {
+  if (!conv_per_s || mode < 0 || mode > 3) return Z4C_ERR_BAD_ARG;
+  z4c_ctx *ctx = nullptr;
+  CK(peak_convert(mode, (cudaStream_t)cuda_stream, conv_per_s));
+  return Z4C_OK;
+}
+
 int z4c_launches_per_step(const z4c_ctx *ctx) {
   if (!ctx) return Z4C_ERR_BAD_ARG;
   int per_stage = 0;

@@ -89,4 +89,30 @@ cudaError_t peak_fma(bool f64, cudaStream_t st, double *flops_per_s) {
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
+cudaError_t peak_convert(int mode, cudaStream_t st, double *conv_per_s) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int threads = 256, blocks = sms * 8, iters = 2048;
+  unsigned long long *sink = nullptr;  // kernel never writes (condition never true)
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  for (int rep = 0; rep < 2; ++rep) {  // first launch warms up clocks
+    cudaEventRecord(e0, st);
+    if (mode == 0) convert_peak_kernel<0><<<blocks, threads, 0, st>>>(sink, iters);
+    else if (mode == 1) convert_peak_kernel<1><<<blocks, threads, 0, st>>>(sink, iters);
+    else if (mode == 2) convert_peak_kernel<2><<<blocks, threads, 0, st>>>(sink, iters);
+    else convert_peak_kernel<3><<<blocks, threads, 0, st>>>(sink, iters);
+    cudaEventRecord(e1, st);
+  }
+  cudaError_t e = cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *conv_per_s = 8.0 * iters * (double)threads * blocks / (ms * 1e-3);
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
 }  // namespace z4c

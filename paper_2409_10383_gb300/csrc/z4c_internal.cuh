@@ -237,5 +237,6 @@ cudaError_t launch_constraint_partials(int order, const double *u0, const DevBlo
 cudaError_t launch_constraint_finalize(const double *partials, int n, double *result, cudaStream_t st);
 
 cudaError_t peak_fma(bool f64, cudaStream_t st, double *flops_per_s);
+cudaError_t peak_convert(int mode, cudaStream_t st, double *conv_per_s);
 
 }  // namespace z4c

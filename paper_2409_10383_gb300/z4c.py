@@ -27,7 +27,7 @@ EXPORTS = ("z4c_create", "z4c_create_batch", "z4c_set_initial_data_instance", "z
            "z4c_constraints", "z4c_get_state", "z4c_set_state", "z4c_evolve_host",
            "z4c_sync", "z4c_profile_steps", "z4c_set_variant", "z4c_autotune", "z4c_peak_fma", "z4c_constraints_static",
            "z4c_launches_per_step", "z4c_last_error", "z4c_destroy", "z4c_block_indicators",
-           "z4c_track_punctures", "z4c_psi4")
+           "z4c_track_punctures", "z4c_psi4", "z4c_peak_convert")
 Z4C_MAX_PUNCTURES = 64
 
 
@@ -94,6 +94,7 @@ def lib():
             "z4c_block_indicators": (I, [P, I, P, P]),
             "z4c_track_punctures": (I, [P, I, I, P, D, P]),
             "z4c_psi4": (I, [P, I, P]),
+            "z4c_peak_convert": (I, [I, P, P]),
             "z4c_launches_per_step": (I, [P]),
             "z4c_last_error": (ctypes.c_char_p, [P]),
             "z4c_destroy": (None, [P]),
@@ -371,6 +372,16 @@ def z4c_peak_fma(fp64: bool, stream=None) -> float:
     out = ctypes.c_double()
     st = stream.cuda_stream if stream is not None else None
     _check(lib().z4c_peak_fma(int(bool(fp64)), st, ctypes.byref(out)), None, "z4c_peak_fma")
+    return out.value
+
+
+def z4c_peak_convert(mode: int, stream=None) -> float:
+    """float <-> double conversions per second of the current GPU: mode 0/1
+    float -> double by the hardware / on the integer pipe, 2/3 double ->
+    float likewise."""
+    out = ctypes.c_double()
+    st = stream.cuda_stream if stream is not None else None
+    _check(lib().z4c_peak_convert(int(mode), st, ctypes.byref(out)), None, "z4c_peak_convert")
     return out.value
 
 
