@@ -73,6 +73,21 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(torch, x, ws, device="cuda"):
+    """The largest x over the ranks: the job waits for its slowest rank."""
+    if ws <= 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank, ws, ms):
+    """Whole-job throughput: the units all ranks processed over the slowest
+    rank's time (every rank runs its own instance: weak scaling)."""
+    return units_per_rank * ws / (ms * 1e-3)
+
+
 def host_cores():
     try:
         return len(os.sched_getaffinity(0))
@@ -224,12 +239,8 @@ def measure(z4c, torch, workload, prec, args, ws, local):
         g.z4c_rk4_step(dt, args.steps)
         e1.record(st)
         barrier()
-    ms = e0.elapsed_time(e1)
-    if ws > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = cells * args.steps * ws / (ms * 1e-3)
+    ms = max_over_ranks(torch, e0.elapsed_time(e1), ws)
+    value = job_value(cells * args.steps, ws, ms)
 
     # live per-kernel timing: CUDA events around each launch on the context's
     # stream (plain launches of the same kernels on the same state)
@@ -528,17 +539,13 @@ def main():
     if not args.no_batch and args.variant == "both":
         batched = measure_batch(z4c, torch, args.batch_steps, 2)
         if ws > 1:
-            t = torch.tensor([batched["ms_per_step"]], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            batched["value"] = batched["cells"] * ws / (float(t.item()) * 1e-3)
+            batched["value"] = job_value(batched["cells"], ws, max_over_ranks(torch, batched["ms_per_step"], ws))
 
     smr = None
     if not args.no_smr and args.variant == "both":
         smr = measure_smr(z4c, torch, args.smr_steps, 2)
         if ws > 1:
-            t = torch.tensor([smr["ms_per_step"]], device="cuda")
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            smr["value"] = smr["cells"] * ws / (float(t.item()) * 1e-3)
+            smr["value"] = job_value(smr["cells"], ws, max_over_ranks(torch, smr["ms_per_step"], ws))
 
     order2 = None
     if not args.no_order2 and args.variant == "both" and workload["order"] != 2:
