@@ -61,6 +61,13 @@ def test_create_validates_arguments(L):
     assert z4c.z4c_create(_mesh(), [_block()], 2, 4, _params())[0] == z4c.Z4C_ERR_UNSUPPORTED
     assert z4c.z4c_create(_mesh(), [_block()], 3, 6, _params())[0] == z4c.Z4C_ERR_UNSUPPORTED
     assert z4c.z4c_create(_mesh(), [_block()], 4, 4, _params(16))[0] == z4c.Z4C_ERR_UNSUPPORTED
+    # 2nd-order differencing needs 2 ghosts; orders other than 2, 4, 6 are refused
+    ok, ctx = z4c.z4c_create(_mesh(), [_block()], 2, 2, _params())
+    assert ok == 0 and ctx.value
+    L.z4c_destroy(ctx)
+    assert z4c.z4c_create(_mesh(), [_block()], 1, 2, _params())[0] == z4c.Z4C_ERR_UNSUPPORTED
+    assert z4c.z4c_create(_mesh(), [_block()], 3, 3, _params())[0] == z4c.Z4C_ERR_UNSUPPORTED
+    assert z4c.z4c_create(_mesh(), [_block()], 5, 8, _params())[0] == z4c.Z4C_ERR_UNSUPPORTED
     # block does not tile the mesh
     assert z4c.z4c_create(_mesh(), [_block(n=16)], 3, 4, _params())[0] == z4c.Z4C_ERR_BAD_MESH
     # overlapping blocks
@@ -97,4 +104,15 @@ def test_sizes_and_unbound_calls(L):
     assert L.z4c_set_variant(ctx, 2, 2) == 0 and L.z4c_set_variant(ctx, 1, 4) == z4c.Z4C_ERR_UNSUPPORTED
     assert L.z4c_set_variant(ctx, 3, 4) == 0
     assert L.z4c_set_variant(ctx, 4, 4) == 0 and L.z4c_set_variant(ctx, 4, 1) == z4c.Z4C_ERR_UNSUPPORTED
+    L.z4c_destroy(ctx)
+
+
+def test_diagnostic_calls_check_arguments(L):
+    """Argument checks that come before any CUDA call."""
+    out = ctypes.c_double()
+    assert L.z4c_peak_convert(4, None, ctypes.byref(out)) == z4c.Z4C_ERR_BAD_ARG
+    assert L.z4c_peak_convert(-1, None, ctypes.byref(out)) == z4c.Z4C_ERR_BAD_ARG
+    assert L.z4c_peak_convert(0, None, None) == z4c.Z4C_ERR_BAD_ARG
+    rc, ctx = z4c.z4c_create(_mesh(), [_block()], 3, 4, _params())
+    assert L.z4c_psi4(ctx, 0, None) == z4c.Z4C_ERR_NOT_BOUND  # not bound yet
     L.z4c_destroy(ctx)
