@@ -60,7 +60,7 @@ FP64_DRAM_BYTES_PER_CELL = {6: (121026816 + 85157632) / 262144, 2: (114210560 + 
 # interior cell per stage, from the same kind of capture
 FP32_OPS_PER_CELL_STAGE = {6: dict(fadd=1085, ffma=1274, fmul=507)}
 FP32_F64_RESIDUE_PER_CELL_STAGE = {6: dict(dadd=47, dfma=22, dmul=25)}
-FP32_DRAM_BYTES_PER_CELL = {6: (62101760 + 4572416 + 77183744 + 29128448) / 262144}
+FP32_DRAM_BYTES_PER_CELL = {6: (62186496 + 4548096 + 75075840 + 28735744) / 262144}
 # algorithmic HBM bytes per zone-cycle (fused 3-register RK4, 22 FP64 fields;
 # the same for the FP32-RHS path, whose state stays FP64)
 ALG_BYTES_PER_ZONE_CYCLE = 352 * 8
