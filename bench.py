@@ -504,6 +504,8 @@ def main():
     ap.add_argument("--smr-steps", type=int, default=50)
     ap.add_argument("--no-order2", action="store_true",
                     help="skip the 2nd-order (2 ghosts) variant of the workload")
+    ap.add_argument("--no-table1", action="store_true",
+                    help="skip the paper's Table-1 workload (linear wave on 64^3 blocks)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default kernel variant instead of timing the candidates")
     ap.add_argument("--smr-only", action="store_true",
@@ -561,6 +563,19 @@ def main():
     if rank == 0 and 64 in res and 32 in res:
         acc32 = fp32_accuracy(z4c, workload)
 
+    # the paper's Table-1 throughput workload (context: the paper's numbers
+    # are on other hardware)
+    table1 = None
+    if not args.no_table1 and args.variant == "both" and args.workload == "single_puncture_128":
+        w1 = inputs.workload("linear_wave_256")
+        q = measure(z4c, torch, w1, 64, args, ws, local)
+        table1 = {"value": q["value"], "unit": UNIT, "ms_per_step": q["ms_per_step"], "dtype": "f64",
+                  "config": {"workload": w1["name"], "blocks": int(len(w1["n"])), "block": [64, 64, 64],
+                             "cells": q["cells"], "fd_order": 6, "ghosts": 4},
+                  "paper_zcps_context": {"GH200": 2.46e7, "A100": 1.36e7, "MI250X_die": 5.08e6},
+                  "roofline": {k: q["roofline"][k] for k in ("frac", "fp64_issue_frac", "kernel_ms_per_launch")},
+                  "e2e": q["e2e"], "gpu_launches": q["gpu_launches"], "clocks": q["clocks"]}
+
     if rank != 0:
         if ws > 1:
             torch.distributed.destroy_process_group()
@@ -598,6 +613,8 @@ def main():
         line["smr"] = smr
     if order2 is not None:
         line["order2"] = order2
+    if table1 is not None:
+        line["paper_table1"] = table1
     print(json.dumps(line), flush=True)
     if ws > 1:
         torch.distributed.destroy_process_group()
