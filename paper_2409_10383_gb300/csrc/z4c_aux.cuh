@@ -51,29 +51,41 @@ __global__ void sommerfeld_kernel(StageArgs a, const CellRef *__restrict__ cells
   // w2 (u[o2] - u).  Per cell: a1,2_d = -w1,2_d x^d / (2h r); per field:
   // k = -(u - u_inf) / r + sum_d a1_d (u[o1_d] - u) + a2_d (u[o2_d] - u),
   // which is exactly zero on a constant state equal to u_inf.
-  double xd[3], r2 = 0.0;
+  // Coefficients in the stencils' precision R: the FP32 variant forms them
+  // on the FP32 pipe (its FP64 pipe is the stage update's), FP64 in FP64.
+  R xd[3], r2 = R(0);
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    xd[d] = b.lo[d] + (idx[d] - b.g + 0.5) * b.h;
+    if constexpr (F32)
+      xd[d] = fmaf(float(idx[d] - b.g) + 0.5f, b.hf, float(b.lo[d]));
+    else
+      xd[d] = b.lo[d] + (idx[d] - b.g + 0.5) * b.h;
     r2 += xd[d] * xd[d];
   }
-  const double ir = 1.0 / sqrt(r2);
+  R ir, hh;
+  if constexpr (F32) {
+    ir = rsqrtf(r2);
+    hh = 0.5f / b.hf;
+  } else {
+    ir = 1.0 / sqrt(r2);
+    hh = 0.5 / b.h;
+  }
   R a1[3], a2[3];
   int o1[3], o2[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     const int kind = (c.code >> (2 * d)) & 3;
-    const double q = -ir * xd[d] * (0.5 / b.h);
-    const double w1 = kind == SOMM_FORWARD ? 4.0 : kind == SOMM_BACKWARD ? -4.0 : 1.0;
-    const double w2 = kind == SOMM_FORWARD ? -1.0 : kind == SOMM_BACKWARD ? 1.0 : -1.0;
+    const R q = -ir * xd[d] * hh;
+    const R w1 = kind == SOMM_FORWARD ? R(4) : kind == SOMM_BACKWARD ? R(-4) : R(1);
+    const R w2 = kind == SOMM_FORWARD ? R(-1) : kind == SOMM_BACKWARD ? R(1) : R(-1);
     const int s1 = kind == SOMM_BACKWARD ? -1 : 1;
     const int s2 = kind == SOMM_FORWARD ? 2 : kind == SOMM_BACKWARD ? -2 : -1;
-    a1[d] = R(q * w1);
-    a2[d] = R(q * w2);
+    a1[d] = q * w1;
+    a2[d] = q * w2;
     o1[d] = s1 * st[d];
     o2[d] = s2 * st[d];
   }
-  const R mir = R(-ir);
+  const R mir = -ir;
   R k[NF];
 #pragma unroll
   for (int f = 0; f < NF; ++f) {
