@@ -76,6 +76,14 @@ def test_create_validates_arguments(L):
     # off-lattice block
     assert z4c.z4c_create(_mesh(), [_block(lo=(-0.49, -0.5, -0.5))], 3, 4,
                           _params())[0] == z4c.Z4C_ERR_BAD_MESH
+    # a block thinner than the ghost width (a ghost region would span two
+    # neighbours) is refused; one exactly as wide is accepted
+    assert z4c.z4c_create(_mesh(), [_block(n=2, h=0.5)], 3, 4, _params())[0] == z4c.Z4C_ERR_UNSUPPORTED
+    ok, ctx = z4c.z4c_create(_mesh(), [_block(n=3, h=1 / 3)], 3, 4, _params())
+    assert ok == 0 and ctx.value
+    L.z4c_destroy(ctx)
+    # no blocks
+    assert z4c.z4c_create(_mesh(), [], 3, 4, _params())[0] != 0
 
 
 def test_sizes_and_unbound_calls(L):
