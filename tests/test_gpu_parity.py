@@ -36,6 +36,12 @@ CASES = [
     # 2nd-order differencing with 2 ghosts (the paper's default with 2 ghosts)
     ("puncture", 2, (2, 1, 1), (20, 12, 10), None),
     ("gauge_wave", 2, (1, 2, 1), (24, 12, 18), None),
+    # blocks exactly as wide as their ghost layer: every stencil reaches
+    # through the whole interior into the ghosts on the far side
+    ("gauge_wave", 4, (2, 1, 1), 3, None),             # periodic; y, z wrap onto the block itself
+                                                       # (two blocks in x keep cells off the origin,
+                                                       # where the puncture data are infinite)
+    ("puncture", 6, (2, 1, 1), 4, None),               # neighbour's whole interior, Sommerfeld
 ]
 
 
