@@ -124,3 +124,14 @@ def test_diagnostic_calls_check_arguments(L):
     rc, ctx = z4c.z4c_create(_mesh(), [_block()], 3, 4, _params())
     assert L.z4c_psi4(ctx, 0, None) == z4c.Z4C_ERR_NOT_BOUND  # not bound yet
     L.z4c_destroy(ctx)
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    """Without the built CUDA library every call raises: there is no CPU or
+    other fallback path behind the binding."""
+    monkeypatch.setattr(z4c, "LIB_PATH", str(tmp_path / "absent.so"))
+    monkeypatch.setattr(z4c, "_lib", None)
+    with pytest.raises(RuntimeError, match="no fallback"):
+        z4c.lib()
+    with pytest.raises(RuntimeError, match="no fallback"):
+        z4c.z4c_create(_mesh(), [_block()], 3, 4, _params())
