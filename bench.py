@@ -95,16 +95,17 @@ def host_cores():
         return os.cpu_count() or 1
 
 
-def oracle_sample(workload, steps, warmup):
-    """The FP64 CPU oracle on a bounded sample of the workload: one 64^3
-    block of the same physics (order 6, KO 0.5, Sommerfeld boundary,
-    puncture data), RK4 steps at CFL 0.25, on all host cores."""
+def oracle_sample(workload, steps, warmup, n0=None, threads=None):
+    """The FP64 CPU oracle on a bounded sample of the workload: one block
+    (the workload's block size unless n0 is given) of the same physics
+    (order 6, KO 0.5, Sommerfeld boundary, puncture data), RK4 steps at CFL
+    0.25, on all host cores unless threads is given."""
     from oracle import oracle
     oracle.build()
-    cores = host_cores()
+    cores = threads or host_cores()
     oracle.set_threads(cores)
     w = workload
-    n0 = int(w["n"][0][0])
+    n0 = int(n0 or w["n"][0][0])
     lo = -float(w["h"][0]) * n0 / 2
     m = oracle.Mesh(n=[[n0] * 3], lo=[[lo] * 3], h=[float(w["h"][0])], ghosts=w["ghosts"],
                     order=w["order"], dom_lo=(lo,) * 3, dom_hi=(-lo,) * 3, periodic=w["periodic"],
@@ -584,6 +585,9 @@ def main():
     if ws == 1 and not args.no_cpu_baseline:
         c = oracle_sample(workload, args.cpu_steps, 0)
         cpu = {k: c[k] for k in ("value", "unit", "cores", "kind", "sample")}
+        # the same oracle on one core (a smaller block keeps it to about a second)
+        c1 = oracle_sample(workload, 1, 0, n0=32, threads=1)
+        cpu["single_thread"] = {k: c1[k] for k in ("value", "unit", "cores", "sample")}
     order = workload["order"]
     line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": r["ms_per_step"], "higher_is_better": True,
