@@ -399,16 +399,16 @@ def fp32_accuracy(z4c, workload, steps=20):
             "note": "interior cells; min alpha is the lapse at the puncture; fields that did not change are skipped"}
 
 
-def measure_batch(z4c, torch, steps, warmup):
+def measure_batch(z4c, torch, steps, warmup, autotune=True):
     """The uneven batch (80 independent single-block problems: punctures and
     gauge waves of 24^3..96^3, orders 4/6, FP64 and FP32-RHS) evolved
     together, one CUDA-graph launch per RK4 step, each instance with its
-    own dt; kernel variants autotuned."""
+    own dt; kernel variants autotuned (else the built-in defaults)."""
     ws = inputs.uneven_batch()
     g = z4c.Z4c.batch(ws)
     for i, w in enumerate(ws):
         g.z4c_set_initial_data_instance(i, w["id_kind"], w["id_par"])
-    variant = g.z4c_autotune(2)
+    variant = g.z4c_autotune(2) if autotune else (4, 4)
     dts = [w["cfl"] * float(w["h"][0]) for w in ws]
     cells = sum(int(np.prod(w["n"], axis=1).sum()) for w in ws)
     g.z4c_rk4_step_batch(dts, max(1, warmup))
@@ -540,7 +540,7 @@ def main():
     r = res[prim]
     batched = None
     if not args.no_batch and args.variant == "both":
-        batched = measure_batch(z4c, torch, args.batch_steps, 2)
+        batched = measure_batch(z4c, torch, args.batch_steps, 2, autotune=not args.no_autotune)
         if ws > 1:
             batched["value"] = job_value(batched["cells"], ws, max_over_ranks(torch, batched["ms_per_step"], ws))
 
