@@ -302,7 +302,10 @@ int z4c_track_punctures(z4c_ctx *ctx, int reg, int np, double *xyz, double dt, d
  * mb = (e_theta - i e_phi) / sqrt(2) comes from Gram-Schmidt in gamma_ij on
  * the coordinate vectors x^i, (-y, x, 0) and (x z, y z, -(x^2 + y^2)) about
  * the origin.  Cells on the z axis (tetrad undefined) and all non-interior
- * cells get 0.  Fills the ghost cells of register reg first.
+ * cells get 0.  Fills the ghost cells of register reg first.  A context
+ * with FP32-RHS blocks only keeps its y/z derivative store for this call in
+ * the accumulator register (stage register A when reg is the accumulator),
+ * whose content is undefined between steps anyway.
  * out_device: device, caller-owned, 2 * (register elements / 22) doubles:
  * for each block in order, the real part over its storage cells
  * ((n_z+2g) x (n_y+2g) x (n_x+2g), x fastest), then the imaginary part.

@@ -583,20 +583,23 @@ int z4c_psi4(z4c_ctx *ctx, int reg, void *out_device) {
   r = fill_ghosts(ctx, ctx->reg[reg], nullptr);
   if (r) return r;
   CK(cudaMemsetAsync(out_device, 0, ctx->reg_elems / NF * 2 * sizeof(double), ctx->stream));
-  // with an FP64 pre-pass store: the y/z first derivatives of every block
-  // (FP64 and FP32-RHS alike) from the FP64 register, as the RHS takes them
-  const double *ds = nullptr;
-  if (ctx->has[0]) {
+  // the y/z first derivatives of every block (FP64 and FP32-RHS alike) from
+  // the FP64 register, as the RHS takes them, into the FP64 pre-pass store;
+  // a context without one (FP32-RHS blocks only) uses the accumulator
+  // register, which has the store's layout and is free between steps (or
+  // stage register A when reg is the accumulator)
+  void *store = ctx->has[0] ? ctx->d_dstore(false) : ctx->reg[reg == Z4C_REG_ACC ? Z4C_REG_STAGE_A : Z4C_REG_ACC];
+  {
     StageArgs a{};
     a.blocks = ctx->d_blocks();
     a.x64 = ctx->reg[reg];
-    a.dstore = ctx->d_dstore(false);
+    a.dstore = store;
     for (int g = 0; g < NGRP; ++g) {
       const Group &G = ctx->grp[g];
       if (!G.empty()) CK(launch_prepass_f64(G.order, a, ctx->d_wtiles(g), (int)G.wtiles.size(), ctx->stream));
     }
-    ds = (const double *)ctx->d_dstore(false);
   }
+  const double *ds = (const double *)store;
   CK(launch_psi4(ctx->reg[reg], ctx->d_blocks(), ctx->d_ctiles(), (int)ctx->ctiles.size(), ds,
                  (double *)out_device, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));

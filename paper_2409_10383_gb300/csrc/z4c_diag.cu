@@ -25,16 +25,11 @@ cudaError_t launch_track(const double *u, const DevBlock *blocks, const TrackIn 
 cudaError_t launch_psi4(const double *u, const DevBlock *blocks, const Tile *tiles, int ntiles, const double *ds,
                         double *out, cudaStream_t st) {
   if (ntiles <= 0) return cudaSuccess;
+  if (!ds) return cudaErrorInvalidValue;
   const dim3 block(TX, TY);
-  if (ds) {
-    psi4_kernel<2, true><<<ntiles, block, 0, st>>>(u, blocks, tiles, ds, out);
-    psi4_kernel<4, true><<<ntiles, block, 0, st>>>(u, blocks, tiles, ds, out);
-    psi4_kernel<6, true><<<ntiles, block, 0, st>>>(u, blocks, tiles, ds, out);
-  } else {
-    psi4_kernel<2, false><<<ntiles, block, 0, st>>>(u, blocks, tiles, ds, out);
-    psi4_kernel<4, false><<<ntiles, block, 0, st>>>(u, blocks, tiles, ds, out);
-    psi4_kernel<6, false><<<ntiles, block, 0, st>>>(u, blocks, tiles, ds, out);
-  }
+  psi4_kernel<2><<<ntiles, block, 0, st>>>(u, blocks, tiles, ds, out);
+  psi4_kernel<4><<<ntiles, block, 0, st>>>(u, blocks, tiles, ds, out);
+  psi4_kernel<6><<<ntiles, block, 0, st>>>(u, blocks, tiles, ds, out);
   return cudaGetLastError();
 }
 

@@ -125,10 +125,10 @@ __global__ void track_kernel(const double *__restrict__ u, const DevBlock *__res
 // Psi4 (psi4_point) at every interior cell of the blocks of order ORD, one
 // thread per cell over the interior tiles; out holds per block the real part
 // and then the imaginary part over the block's storage cells (offset
-// 2 off / NF), other cells untouched.  PRE: the y/z first derivatives of the
+// 2 off / NF), other cells untouched.  The y/z first derivatives of the
 // eleven fields with mixed second derivatives come from ds (the FP64
-// pre-pass arrays of u, as in the RHS); else every stencil reads u.
-template <int ORD, bool PRE>
+// pre-pass arrays of u, as in the RHS); every other stencil reads u.
+template <int ORD>
 __global__ void __launch_bounds__(TX * TY) psi4_kernel(const double *__restrict__ u,
                                                        const DevBlock *__restrict__ blocks,
                                                        const Tile *__restrict__ tiles, const double *__restrict__ ds,
@@ -145,14 +145,9 @@ __global__ void __launch_bounds__(TX * TY) psi4_kernel(const double *__restrict_
   const double ichi = 1.0 / fmax(s.at(CHI, 0), b.chi_floor);
   const double x[3] = {b.lo[0] + (i + 0.5) * b.h, b.lo[1] + (j + 0.5) * b.h, b.lo[2] + (kk + 0.5) * b.h};
   double v[2];
-  if constexpr (PRE) {
-    const Src<double, false> d{ds + b.off, cidx, b.S};
-    const Pre<ORD, double, Src<double, false>, Src<double, false>> dv{s, d, st, sc};
-    psi4_point<ORD>(s, dv, ichi, x, v);
-  } else {
-    const Direct<ORD, double, Src<double, false>> dv{s, st, sc};
-    psi4_point<ORD>(s, dv, ichi, x, v);
-  }
+  const Src<double, false> d{ds + b.off, cidx, b.S};
+  const Pre<ORD, double, Src<double, false>, Src<double, false>> dv{s, d, st, sc};
+  psi4_point<ORD>(s, dv, ichi, x, v);
   double *o = out + b.off / NF * 2 + cidx;
   o[0] = v[0];
   o[b.S] = v[1];

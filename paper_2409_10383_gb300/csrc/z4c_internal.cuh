@@ -168,6 +168,7 @@ struct TrackIn {
 };
 cudaError_t launch_indicators(const double *u, const DevBlock *blocks, const Tile *tiles, int ntiles,
                               const int32_t *first, int nb, double *part, double *out, cudaStream_t st);
+// ds: the FP64 y/z pre-pass arrays of u (required)
 cudaError_t launch_psi4(const double *u, const DevBlock *blocks, const Tile *tiles, int ntiles, const double *ds,
                         double *out, cudaStream_t st);
 cudaError_t launch_track(const double *u, const DevBlock *blocks, const TrackIn *in, int np, double dt, double *out,

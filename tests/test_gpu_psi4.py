@@ -131,15 +131,21 @@ def test_psi4_batch(oracle):
 
 def test_psi4_fp32_only_context(oracle):
     """A context with FP32-RHS blocks only has no FP64 pre-pass store: Psi4
-    then takes every stencil from the FP64 state (the other kernel form)."""
+    then keeps the y/z derivatives in the accumulator register, and the
+    state register is left as it was (interior cells; the call fills the
+    ghosts)."""
     from paper_2409_10383_gb300.z4c import Z4c
     w = H.small_workload("puncture", 6, (2, 1, 1), 12)
     m = H.oracle_mesh(oracle, w)
     g = Z4c.from_workload(w, precision=32)
     g.z4c_set_initial_data(w["id_kind"], w["id_par"])
     g.z4c_rk4_step(0.25 * float(w["h"][0]), 2)
+    before = g.z4c_get_state()
     got = g.z4c_psi4().cpu().numpy()
     u = g.z4c_get_state()
+    for b in range(m.nblocks):
+        mk = m.interior_mask(b)
+        assert np.array_equal(m.blocks(u)[b][:, mk], m.blocks(before)[b][:, mk])
     m.fill_ghosts(u)
     _compare(m, u, got)
     g.close()
