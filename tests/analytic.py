@@ -153,41 +153,46 @@ CONST_STATE = dict(kh=0.31, th=-0.12, gam=(0.05, -0.02, 0.03), beta=(0.2, -0.1, 
                    At=((0.04, 0.015, -0.01), (0.015, -0.025, 0.02), (-0.01, 0.02, -0.015)))
 
 
-def constant_z4c_state(mesh, a=0.0, c=0.0):
-    """Every storage cell of every block: gt = delta, chi = alpha = 1,
-    constant Gam, beta and trace-free At, Khat = kh + a x, Theta = th + c x."""
+def constant_z4c_state(mesh, a=0.0, c=0.0, alpha0=1.0, chi0=1.0):
+    """Every storage cell of every block: gt = delta, chi = chi0, alpha =
+    alpha0, constant Gam, beta and trace-free At, Khat = kh + a x,
+    Theta = th + c x."""
     P = CONST_STATE
     At = np.array(P["At"])
     u = mesh.zeros()
     for b, B in enumerate(mesh.blocks(u)):
         X = mesh.centres(b)[0]
-        B[0] = 1.0
+        B[0] = chi0
         for q, (i, j) in enumerate(SYM):
             B[1 + q] = 1.0 if i == j else 0.0
             B[8 + q] = At[i, j]
-        B[7], B[17], B[18] = P["kh"] + a * X, P["th"] + c * X, 1.0
+        B[7], B[17], B[18] = P["kh"] + a * X, P["th"] + c * X, alpha0
         for i in range(3):
             B[14 + i], B[19 + i] = P["gam"][i], P["beta"][i]
     return u
 
 
-def constant_z4c_rhs(x, a, c, kappa1, kappa2, eta, lapse):
+def constant_z4c_rhs(x, a, c, kappa1, kappa2, eta, lapse, alpha0=1.0, chi0=1.0):
     """(22, len(x)) right-hand side of constant_z4c_state at cells with
-    coordinate x (K = Khat + 2 Theta at the cell, indices moved with delta)."""
+    coordinate x (K = Khat + 2 Theta at the cell, indices moved with delta).
+    Every derivative of chi, alpha, gt, Gam and beta vanishes, so R_ij = 0,
+    D_i D_j alpha = 0 and Gam_d = 0; the lapse alpha0 multiplies every term
+    the Z4c equations (Sec. 2) carry it on, and chi0 enters only d_t chi."""
     P = CONST_STATE
     At, gam, beta = np.array(P["At"]), np.array(P["gam"]), np.array(P["beta"])
+    al = alpha0
     kh, th = P["kh"] + a * x, P["th"] + c * x
     K = kh + 2 * th
     AA, A2 = float(np.sum(At * At)), At @ At
     w = np.zeros((22, np.size(x)))
-    w[0] = 2.0 / 3.0 * K
+    w[0] = 2.0 / 3.0 * chi0 * al * K
     for q, (i, j) in enumerate(SYM):
-        w[1 + q] = -2.0 * At[i, j]
-        w[8 + q] = K * At[i, j] - 2.0 * A2[i, j]
-    w[7] = AA + K * K / 3.0 + kappa1 * (1.0 - kappa2) * th + beta[0] * a
-    w[17] = 0.5 * (2.0 / 3.0 * K * K - AA) - kappa1 * (2.0 + kappa2) * th + beta[0] * c
+        w[1 + q] = -2.0 * al * At[i, j]
+        w[8 + q] = al * (K * At[i, j] - 2.0 * A2[i, j])
+    w[7] = al * (AA + K * K / 3.0) + kappa1 * (1.0 - kappa2) * al * th + beta[0] * a
+    w[17] = 0.5 * al * (2.0 / 3.0 * K * K - AA) - al * kappa1 * (2.0 + kappa2) * th + beta[0] * c
     for i in range(3):
-        w[14 + i] = -2.0 * kappa1 * gam[i] - (2.0 / 3.0 * (2 * a + c) if i == 0 else 0.0)
+        w[14 + i] = -2.0 * al * kappa1 * gam[i] - (2.0 / 3.0 * al * (2 * a + c) if i == 0 else 0.0)
         w[19 + i] = gam[i] - eta * beta[i]
-    w[18] = -2.0 * kh if lapse == 1 else -kh
+    w[18] = -2.0 * al * kh if lapse == 1 else -al * al * kh
     return w

@@ -102,25 +102,28 @@ def test_rhs_parity_fp64(oracle, kind, order, nb, n, per, schedule):
 
 
 @pytest.mark.parametrize("schedule", [1, 2])
-@pytest.mark.parametrize("order,lapse,kappa2,slopes", [(6, 1, 0.2, (0.4, -0.25)), (4, 0, 0.1, (0.3, 0.2)),
-                                                       (2, 1, 0.0, (-0.2, 0.1))])
-def test_rhs_closed_form_constant_state(oracle, order, lapse, kappa2, slopes, schedule):
+@pytest.mark.parametrize("order,lapse,kappa2,slopes,alpha0,chi0", [
+    (6, 1, 0.2, (0.4, -0.25), 1.0, 1.0), (4, 0, 0.1, (0.3, 0.2), 1.0, 1.0), (2, 1, 0.0, (-0.2, 0.1), 1.0, 1.0),
+    (6, 1, 0.3, (0.4, -0.25), 0.7, 0.6), (6, 0, 0.1, (-0.3, 0.15), 1.6, 0.45), (4, 1, 0.0, (0.2, 0.3), 0.7, 1.0),
+    (2, 0, 0.2, (0.1, -0.2), 0.7, 0.6)])
+def test_rhs_closed_form_constant_state(oracle, order, lapse, kappa2, slopes, alpha0, chi0, schedule):
     """The GPU RHS against the closed form of a constant state with linear
-    Khat and Theta (the damping coefficients, the Theta inside K and inside
-    the Gam equation's K gradient, both gauges): 1e-13 of each field's
-    scale, directly, not through the oracle."""
+    Khat and Theta and a constant lapse alpha0 and chi0 (the damping
+    coefficients and their lapse factors, the Theta inside K and inside the
+    Gam equation's K gradient, both gauges with their powers of the lapse):
+    1e-13 of each field's scale, directly, not through the oracle."""
     import analytic as an
     a, c = slopes
     w = H.small_workload("puncture", order, (2, 1, 1), 8, lapse=lapse, shift=1, kappa1=0.07, kappa2=kappa2,
                          eta=1.3, dom_lo=(-0.5,) * 3, dom_hi=(0.5,) * 3)
     m = H.oracle_mesh(oracle, w)
-    u = an.constant_z4c_state(m, a, c)
+    u = an.constant_z4c_state(m, a, c, alpha0, chi0)
     g = H.gpu_ctx(w, schedule=schedule)
     g.z4c_set_state(u, reg=1)
     got = g.z4c_rhs(1).cpu().numpy()
     for b in range(m.nblocks):
         mk = m.interior_mask(b)
-        want = an.constant_z4c_rhs(m.centres(b)[0][mk], a, c, 0.07, kappa2, 1.3, lapse)
+        want = an.constant_z4c_rhs(m.centres(b)[0][mk], a, c, 0.07, kappa2, 1.3, lapse, alpha0, chi0)
         k = m.blocks(got)[b][:, mk]
         err = np.abs(k - want).max(axis=1)
         assert np.all(err <= 1e-13 * np.maximum(1.0, np.abs(want).max(axis=1))), (b, err)

@@ -53,33 +53,39 @@ def test_flat_space_rhs_is_exactly_zero(oracle):
 
 
 # --------------------------------------------------------------------------
-@pytest.mark.parametrize("lapse,kappa2,slopes", [(1, 0.0, (0.0, 0.0)), (1, 0.3, (0.0, 0.0)), (0, 0.1, (0.0, 0.0)),
-                                                 (1, 0.2, (0.4, -0.25))])
-def test_constant_state_closed_form(oracle, lapse, kappa2, slopes):
-    """gt = delta, chi = alpha = 1, constant Gam^i, beta^i and a constant
-    trace-free At; Khat = kh + a x and Theta = th + c x (a, c: slopes; the
-    centred and lopsided stencils are exact and KO vanishes on linear data).
-    The standard Z4c equations reduce to algebra (K = Khat + 2 Theta at the
-    cell, indices moved with delta):
-      d_t chi   = 2/3 K
-      d_t gt_ij = -2 At_ij
-      d_t At_ij = K At_ij - 2 At_ik At_kj
-      d_t Khat  = At_kl At_kl + K^2 / 3 + kappa1 (1 - kappa2) Theta + beta^x a
-      d_t Theta = (2/3 K^2 - At_kl At_kl) / 2 - kappa1 (2 + kappa2) Theta + beta^x c
-      d_t Gam^i = -2 kappa1 Gam^i - 2/3 d_i (2 Khat + Theta)     (Gam_d = 0)
-      d_t alpha = -2 Khat (1+log) or -Khat (harmonic)
+@pytest.mark.parametrize("lapse,kappa2,slopes,alpha0,chi0", [
+    (1, 0.0, (0.0, 0.0), 1.0, 1.0), (1, 0.3, (0.0, 0.0), 1.0, 1.0), (0, 0.1, (0.0, 0.0), 1.0, 1.0),
+    (1, 0.2, (0.4, -0.25), 1.0, 1.0),
+    (1, 0.0, (0.0, 0.0), 0.7, 1.0), (0, 0.1, (0.0, 0.0), 0.7, 1.0), (1, 0.3, (0.4, -0.25), 0.7, 0.6),
+    (0, 0.2, (-0.3, 0.15), 1.6, 0.45)])
+def test_constant_state_closed_form(oracle, lapse, kappa2, slopes, alpha0, chi0):
+    """gt = delta, chi = chi0, alpha = alpha0, constant Gam^i, beta^i and a
+    constant trace-free At; Khat = kh + a x and Theta = th + c x (a, c:
+    slopes; the centred and lopsided stencils are exact and KO vanishes on
+    linear data).  The standard Z4c equations reduce to algebra (K = Khat +
+    2 Theta at the cell, indices moved with delta, al = alpha0):
+      d_t chi   = 2/3 chi0 al K
+      d_t gt_ij = -2 al At_ij
+      d_t At_ij = al (K At_ij - 2 At_ik At_kj)
+      d_t Khat  = al (At_kl At_kl + K^2 / 3) + kappa1 (1 - kappa2) al Theta + beta^x a
+      d_t Theta = al (2/3 K^2 - At_kl At_kl) / 2 - al kappa1 (2 + kappa2) Theta + beta^x c
+      d_t Gam^i = -2 al kappa1 Gam^i - 2/3 al d_i (2 Khat + Theta)     (Gam_d = 0)
+      d_t alpha = -2 al Khat (1+log) or -al^2 Khat (harmonic)
       d_t beta^i = Gam^i - eta beta^i
-    This fixes the damping coefficients kappa1, kappa2, the Theta inside K
-    and inside the K-gradient term of the Gam equation, the Gamma damping
-    and both gauge forms, which the exact solutions used elsewhere leave
-    untouched (their Theta and Gam - Gam_d vanish)."""
+    This fixes the damping coefficients kappa1, kappa2 and the lapse factor
+    each damping term carries, the Theta inside K and inside the K-gradient
+    term of the Gam equation, the Gamma damping and both gauge forms with
+    their powers of the lapse, which the exact solutions used elsewhere
+    leave untouched (their Theta and Gam - Gam_d vanish, and their lapse is
+    1 or harmonic).  alpha0 != 1 separates alpha, alpha^2 and no lapse
+    factor at all."""
     k1, eta = 0.07, 1.3
     a, c = slopes
     m = oracle.uniform_mesh(n=8, order=6, periodic=False, lapse=lapse, shift=1, ko_sigma=0.5, kappa1=k1,
                             kappa2=kappa2, eta=eta)
-    u = an.constant_z4c_state(m, a, c)
+    u = an.constant_z4c_state(m, a, c, alpha0, chi0)
     k = interior(m, m.rhs(u))
-    want = an.constant_z4c_rhs(m.centres(0)[0][m.interior_mask(0)], a, c, k1, kappa2, eta, lapse)
+    want = an.constant_z4c_rhs(m.centres(0)[0][m.interior_mask(0)], a, c, k1, kappa2, eta, lapse, alpha0, chi0)
     err = np.abs(k - want).max(axis=1)
     assert np.all(err <= 1e-13 * np.maximum(1.0, np.abs(want).max(axis=1))), (err, want[:, 0])
 
