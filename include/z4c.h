@@ -239,6 +239,15 @@ int z4c_evolve_host(z4c_ctx *ctx, const void *host_in, void *host_out, size_t by
  * z4c_evolve_host, z4c_profile_steps and z4c_autotune report it too. */
 int z4c_sync(z4c_ctx *ctx);
 
+/* Failure-detection test aid (no counterpart in the paper): enqueue on the
+ * context's stream one kernel whose bounded mbarrier wait must run out (it
+ * waits for 16 bytes of bulk copies and issues none), after at most
+ * `rounds` try_wait attempts (1..65536), then z4c_sync().  Returns
+ * Z4C_ERR_TIMEOUT with its z4c_last_error text, exactly as after a staged
+ * kernel whose copies never landed; the context stays usable and the status
+ * word is cleared.  Touches no register. */
+int z4c_test_wait_timeout(z4c_ctx *ctx, int rounds);
+
 /* Measurement aid: run nsteps RK4 steps with plain (not graph) launches,
  * each bracketed by CUDA events on the context's stream, and return the
  * average milliseconds per step spent in each kernel kind (4 doubles):
@@ -349,12 +358,12 @@ int z4c_peak_convert(int mode, void *cuda_stream, double *conv_per_s);
  * One record is used per 16 x 8 tile of one z-plane; a block needing more
  * than Z4C_STATIC_MAX_TILES tiles (e.g. larger than 128^3) is rejected with
  * Z4C_ERR_UNSUPPORTED.  Calls no cudaMalloc/cudaFree and no allocating
- * library routine.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  Every call shares the array and
- * overwrites the records it reads; calls that overlap on the GPU (other
- * streams or threads without ordering) race on it.  Returns Z4C_ERR_NAN if a
- * norm is NaN. */
+ * library routine.  Every call looks up the array's device address
+ * (cudaGetSymbolAddress) on the current device, which must be the device
+ * that holds u_device, and synchronises cuda_stream before it returns.
+ * Every call shares the array and overwrites the records it reads; calls
+ * that overlap on the GPU (other streams or threads without ordering) race
+ * on it.  Returns Z4C_ERR_NAN if a norm is NaN. */
 #define Z4C_STATIC_MAX_TILES 16384
 int z4c_constraints_static(const void *u_device, const int32_t n[3], int ghosts, int fd_order,
                            const double lo[3], double h, double chi_floor, double r_mask,

@@ -74,7 +74,8 @@ int status_check(z4c_ctx *ctx) {
   if (st == 0) return Z4C_OK;
   CK(cudaMemsetAsync(ctx->d_status(), 0, sizeof(int32_t), ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
-  return fail(ctx, Z4C_ERR_TIMEOUT, "a bulk-copy wait in the staged FP32 kernel gave up; results of that launch are invalid");
+  return fail(ctx, Z4C_ERR_TIMEOUT,
+              "a bounded wait on bulk copies (mbarrier) gave up in a kernel; results of that launch are invalid");
 }
 
 StageArgs group_args(const z4c_ctx *ctx, StageArgs a, bool f32) {
@@ -419,6 +420,14 @@ int z4c_sync(z4c_ctx *ctx) {
   CK(cudaStreamSynchronize(ctx->stream));
   CK(cudaGetLastError());
   return status_check(ctx);
+}
+
+int z4c_test_wait_timeout(z4c_ctx *ctx, int rounds) {
+  int r = ensure_bound(ctx);
+  if (r) return r;
+  if (rounds < 1 || rounds > (1 << 16)) return fail(ctx, Z4C_ERR_BAD_ARG, "rounds must be in 1..65536");
+  CK(launch_wait_probe(ctx->d_status(), rounds, ctx->stream));
+  return z4c_sync(ctx);
 }
 
 int z4c_profile_steps(z4c_ctx *ctx, double dt, int nsteps, double *ms) {

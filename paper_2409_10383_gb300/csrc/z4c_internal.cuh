@@ -181,6 +181,8 @@ cudaError_t launch_prolong(double *reg, const DevBlock *blocks, const ProlongRef
 // rows allow 16-byte aligned bulk copies; the tiles of other blocks use the
 // pre-pass schedule
 cudaError_t launch_staged_f32(int order, const StageArgs &a, const Tile *tiles, int ntiles, cudaStream_t st);
+// failure-detection probe: a bounded mbarrier wait that runs out (status |= 1)
+cudaError_t launch_wait_probe(int32_t *status, int rounds, cudaStream_t st);
 // FP32 split schedule (4): the pre-pass-schedule RHS kernel stores k (FP32)
 // per tile in a.kbuf, then an epilogue kernel applies the RK stage update and
 // the FP64 enforcement at high occupancy

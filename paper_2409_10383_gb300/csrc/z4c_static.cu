@@ -10,8 +10,6 @@
 // The array is shared by every call in the process: each call overwrites the
 // records it uses, and calls that overlap on the GPU (different streams or
 // threads without ordering) race on it.
-#include <mutex>
-
 #include "z4c.h"
 #include "z4c_rhs.cuh"
 
@@ -119,24 +117,15 @@ __global__ void constraints_static_finalize(double *scratch, int n) {
   }
 }
 
-// Device address of g_static_scratch on the current device, looked up once
-// per device (the host-side name is only a stand-in for the symbol).
-std::mutex g_mu;
-double *g_addr[256] = {};
-
+// Device address of g_static_scratch on the current device, looked up on
+// every call with that device current (the host-side name is only a
+// stand-in for the symbol; the lookup allocates nothing).  Not cached: a
+// context torn down and created again may place the array elsewhere.
 cudaError_t static_scratch_address(double **out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void *p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= 256) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_addr[dev]) {
-    void *p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_static_scratch);
-    if (e != cudaSuccess) return e;
-    g_addr[dev] = static_cast<double *>(p);
-  }
-  *out = g_addr[dev];
+  *out = static_cast<double *>(p);
   return cudaSuccess;
 }
 

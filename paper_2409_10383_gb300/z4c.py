@@ -27,7 +27,7 @@ EXPORTS = ("z4c_create", "z4c_create_batch", "z4c_set_initial_data_instance", "z
            "z4c_constraints", "z4c_get_state", "z4c_set_state", "z4c_evolve_host",
            "z4c_sync", "z4c_profile_steps", "z4c_set_variant", "z4c_autotune", "z4c_peak_fma", "z4c_constraints_static",
            "z4c_launches_per_step", "z4c_last_error", "z4c_destroy", "z4c_block_indicators",
-           "z4c_track_punctures", "z4c_psi4", "z4c_peak_convert")
+           "z4c_track_punctures", "z4c_psi4", "z4c_peak_convert", "z4c_test_wait_timeout")
 Z4C_MAX_PUNCTURES = 64
 
 
@@ -86,6 +86,7 @@ def lib():
             "z4c_set_state": (I, [P, I, P, S]),
             "z4c_evolve_host": (I, [P, P, P, S, D, I]),
             "z4c_sync": (I, [P]),
+            "z4c_test_wait_timeout": (I, [P, I]),
             "z4c_profile_steps": (I, [P, D, I, P]),
             "z4c_set_variant": (I, [P, I, I]),
             "z4c_autotune": (I, [P, I, P, P]),
@@ -302,6 +303,12 @@ class Z4c:
 
     def z4c_sync(self):
         _check(lib().z4c_sync(self.ctx), self.ctx, "z4c_sync")
+
+    def z4c_test_wait_timeout(self, rounds=64):
+        """Failure-detection aid: a kernel whose bounded mbarrier wait runs
+        out.  Returns (status, z4c_last_error text)."""
+        rc = lib().z4c_test_wait_timeout(self.ctx, int(rounds))
+        return rc, lib().z4c_last_error(self.ctx).decode()
 
     def z4c_block_indicators(self, reg=REG_U0):
         """Per block (min chi, max |grad chi|) over its interior cells
