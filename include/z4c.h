@@ -105,8 +105,16 @@ typedef struct z4c_block {
  *                 n_y % 8 == 0), schedule 2 for the others; 4 (FP32-RHS
  *                 only) as 2, but the RHS kernel stores k in FP32 and a
  *                 second kernel applies the RK stage update and the FP64
- *                 enforcement at high occupancy.  FP64 instances given 3
- *                 or 4 use 2.  Default (0): 2 for FP64, 4 for FP32-RHS */
+ *                 enforcement at high occupancy; 5 (FP32-RHS only) as 4,
+ *                 but on tiles 64 (or 32) cells wide and 2 (or 4) rows
+ *                 high, so that a warp reads along one row, for cubic
+ *                 blocks with a compiled kernel (order 6, n = 32, 64, 96,
+ *                 128), 16 x 8 tiles for the others; 6 (FP32-RHS only) as
+ *                 5, and the RHS kernel computes two neighbouring cells of
+ *                 a row per thread with packed two-lane FP32 arithmetic
+ *                 where the ghost width and n_x are even.  FP64 instances
+ *                 given 3 to 6 use 2.  Default (0): 2 for FP64, 4 for
+ *                 FP32-RHS */
 typedef struct z4c_params {
   double ko_sigma;
   double kappa1;
@@ -256,18 +264,18 @@ int z4c_test_wait_timeout(z4c_ctx *ctx, int rounds);
  * Advances U0 exactly like z4c_rk4_step.  Synchronous. */
 int z4c_profile_steps(z4c_ctx *ctx, double dt, int nsteps, double *ms);
 
-/* Select a kernel variant explicitly: schedule 1 to 4 (see z4c_params;
- * 3 and 4 apply to FP32-RHS blocks, FP64 blocks then use 2) and occupancy,
+/* Select a kernel variant explicitly: schedule 1 to 6 (see z4c_params;
+ * 3 to 6 apply to FP32-RHS blocks, FP64 blocks then use 2) and occupancy,
  * the resident CTAs per SM the pre-pass-schedule fused kernel's registers
  * are budgeted for: 1 always; 2 or 4 for the FP32-RHS kernel (with schedule
- * 3: for the blocks that do not qualify for staging); schedule 4 is built
- * for 4 only.  Other combinations return Z4C_ERR_UNSUPPORTED.  Makes no
- * CUDA call. */
+ * 3: for the blocks that do not qualify for staging); schedules 4 to 6 are
+ * built for 4 only.  Other combinations return Z4C_ERR_UNSUPPORTED.  Makes
+ * no CUDA call. */
 int z4c_set_variant(z4c_ctx *ctx, int schedule, int occupancy);
 
 /* Pick the fastest kernel variant for this context on this GPU: the
- * schedule (1 or 2; for FP32-RHS blocks also 4, and 3 where blocks qualify;
- * see z4c_params)
+ * schedule (1 or 2; for FP32-RHS blocks also 4, and 3, 5 and 6 where
+ * blocks qualify; see z4c_params)
  * and, for the FP32-RHS fused kernel, the number of resident CTAs per SM its
  * registers are budgeted for (1, 2, 4).
  * Each candidate runs reps + 1 times the ghost fill and stage 1 of RK4 (which

@@ -104,11 +104,23 @@ int launch_fused_group(z4c_ctx *ctx, int g, const StageArgs &a) {
   const bool pre = ctx->sched[p] >= 2;
   const Tile *tl = ctx->d_tiles(g);
   int nt = (int)G.tiles.size();
-  if (G.f32 && ctx->sched[1] == 4) {
-    for (const Group::ExtRange &e : G.eranges) {
+  if (G.f32 && ctx->sched[1] >= 4) {
+    // 4: split RHS kernels + one stage-update kernel; 5: the same on the
+    // wide-tile list (one cell per thread); 6: as 5, two cells per thread
+    // where the blocks allow it
+    const int sc = ctx->sched[1];
+    if (sc >= 5) {
+      tl = ctx->at<Tile>(G.o_ptiles);
+      nt = (int)G.ptiles.size();
+    }
+    for (const Group::ExtRange &e : sc >= 5 ? G.peranges : G.eranges) {
       StageArgs ar = a;
       ar.kbuf = a.kbuf + (size_t)e.first * NF * TX * TY;
-      CK(launch_split_rhs_f32(G.order, e.ext, ar, tl + e.first, e.count, ctx->stream));
+      if (e.shape > 0)
+        CK(launch_wide_rhs_f32(G.order, e.ext, e.shape, sc == 6 && e.pair, ar, tl + e.first, e.count,
+                               ctx->stream));
+      else
+        CK(launch_split_rhs_f32(G.order, e.ext, ar, tl + e.first, e.count, ctx->stream));
     }
     CK(launch_split_epilogue(a, tl, nt, ctx->stream));
     return Z4C_OK;
@@ -497,12 +509,12 @@ int z4c_profile_steps(z4c_ctx *ctx, double dt, int nsteps, double *ms) {
 
 int z4c_set_variant(z4c_ctx *ctx, int schedule, int occupancy) {
   if (!ctx) return Z4C_ERR_BAD_ARG;
-  if (schedule < 1 || schedule > 4) return fail(ctx, Z4C_ERR_BAD_ARG, "schedule must be 1 to 4");
+  if (schedule < 1 || schedule > 6) return fail(ctx, Z4C_ERR_BAD_ARG, "schedule must be 1 to 6");
   const bool ok = (schedule >= 3 ? ctx->has[1] : true) &&
-                  (schedule == 4 ? occupancy == 4
+                  (schedule >= 4 ? occupancy == 4
                                  : occupancy == 1 || (ctx->has[1] && schedule >= 2 && (occupancy == 2 || occupancy == 4)));
   if (!ok) return fail(ctx, Z4C_ERR_UNSUPPORTED, "no kernel built for this schedule/occupancy");
-  ctx->sched[0] = schedule >= 3 ? 2 : schedule;  // schedules 3 and 4 are FP32-only
+  ctx->sched[0] = schedule >= 3 ? 2 : schedule;  // schedules 3 to 6 are FP32-only
   ctx->sched[1] = schedule;
   ctx->occ[1] = occupancy;
   ctx->drop_graph();
@@ -533,6 +545,8 @@ int z4c_autotune(z4c_ctx *ctx, int reps, int *schedule_out, int *occupancy_out) 
       cands.push_back({2, 4});
       if (ctx->has_staged()) cands.push_back({3, 4});
       cands.push_back({4, 4});
+      if (ctx->has_wide()) cands.push_back({5, 4});
+      if (ctx->has_pair()) cands.push_back({6, 4});
     }
     float best = 1e30f;
     Cand pick = {ctx->sched[p], p == 1 ? ctx->occ[1] : 1};
@@ -693,6 +707,8 @@ int z4c_launches_per_step(const z4c_ctx *ctx) {
       per_stage += 2 + (G.rtiles.empty() ? 0 : 1);
     else if (sc == 4 && G.f32)
       per_stage += 2 + (int)G.eranges.size();
+    else if (sc >= 5 && G.f32)
+      per_stage += 2 + (int)G.peranges.size();
     else if (sc >= 2 && !G.f32)
       per_stage += 1 + (int)G.eranges.size();
     else

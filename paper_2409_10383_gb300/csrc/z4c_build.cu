@@ -73,7 +73,7 @@ int check_instance(const z4c_instance &I) {
   if (p.rhs_precision != 64 && p.rhs_precision != 32) return Z4C_ERR_UNSUPPORTED;
   if (p.lapse < 0 || p.lapse > 1 || p.shift < 0 || p.shift > 1) return Z4C_ERR_BAD_ARG;
   if (!(p.chi_floor > 0.0)) return Z4C_ERR_BAD_ARG;
-  if (p.schedule < 0 || p.schedule > 4) return Z4C_ERR_BAD_ARG;
+  if (p.schedule < 0 || p.schedule > 6) return Z4C_ERR_BAD_ARG;
   for (int d = 0; d < 3; ++d)
     if (!(I.mesh.hi[d] > I.mesh.lo[d])) return Z4C_ERR_BAD_MESH;
   return Z4C_OK;
@@ -624,8 +624,39 @@ int z4c_create_batch(const z4c_instance *instances, int ninstances, const z4c_bl
                      [&](const Tile &x, const Tile &y) { return ext_of(x) < ext_of(y); });
     for (int q = 0; q < (int)G.tiles.size(); ++q) {
       const int e = ext_of(G.tiles[q]);
-      if (G.eranges.empty() || G.eranges.back().ext != e) G.eranges.push_back({e, q, 0});
+      if (G.eranges.empty() || G.eranges.back().ext != e) G.eranges.push_back({e, q, 0, true});
       ++G.eranges.back().count;
+      // two cells per thread: even ghost width and interior width, even
+      // block offset (8-byte aligned cell pairs in every array)
+      const DevBlock &D = ctx->dblocks[G.tiles[q].block];
+      G.eranges.back().pair = G.eranges.back().pair && G.f32 && D.g % 2 == 0 && D.n[0] % 2 == 0 &&
+                              D.off % 2 == 0 && D.S % 2 == 0;
+    }
+    if (!G.f32) continue;
+    // schedule-5/6 list: wide tiles (a warp along one row) where n_x is a
+    // multiple of 64 (shape 2) or 32 (shape 1) and a kernel is built
+    for (const Group::ExtRange &r : G.eranges) {
+      const int n0 = ctx->dblocks[G.tiles[r.first].block].n[0];
+      const int shape = !wide_ext_built(G.order, r.ext) ? 0 : n0 % 64 == 0 ? 2 : n0 % 32 == 0 ? 1 : 0;
+      Group::ExtRange pr{r.ext, (int)G.ptiles.size(), 0, r.pair && shape > 0, shape};
+      if (shape == 0) {
+        G.ptiles.insert(G.ptiles.end(), G.tiles.begin() + r.first, G.tiles.begin() + r.first + r.count);
+      } else {
+        const int txs = TX << shape, tys = TY >> shape;
+        int last = -1;
+        for (int q = r.first; q < r.first + r.count; ++q) {
+          const int b = G.tiles[q].block;
+          if (b == last) continue;  // a block's tiles are contiguous in the sorted list
+          last = b;
+          const DevBlock &D = ctx->dblocks[b];
+          for (int k = 0; k < D.n[2]; ++k)
+            for (int j0 = 0; j0 < D.n[1]; j0 += tys)
+              for (int i0 = 0; i0 < D.n[0]; i0 += txs)
+                G.ptiles.push_back(Tile{b | (shape << TILE_SHAPE_SHIFT), i0, j0, k});
+        }
+      }
+      pr.count = (int)G.ptiles.size() - pr.first;
+      G.peranges.push_back(pr);
     }
   }
   // prolongation slots transposed to [125][entries] so that the threads of a
@@ -651,6 +682,7 @@ int z4c_create_batch(const z4c_instance *instances, int ninstances, const z4c_bl
     G.o_wtiles = take(sizeof(Tile) * G.wtiles.size());
     G.o_stiles = take(sizeof(Tile) * G.stiles.size());
     G.o_rtiles = take(sizeof(Tile) * G.rtiles.size());
+    G.o_ptiles = take(sizeof(Tile) * G.ptiles.size());
   }
   for (int p = 0; p < 2; ++p) {
     ctx->o_somm[p] = take(sizeof(CellRef) * ctx->somm[p].size());
@@ -692,7 +724,7 @@ int z4c_create_batch(const z4c_instance *instances, int ninstances, const z4c_bl
   {  // schedule 4: the FP32 RHS of the largest FP32 group's tiles
     size_t nt = 0;
     for (const Group &G : ctx->grp)
-      if (G.f32) nt = std::max(nt, G.tiles.size());
+      if (G.f32) nt = std::max(nt, std::max(G.tiles.size(), G.ptiles.size()));
     ctx->o_kbuf = take(sizeof(float) * NF * TX * TY * nt);
   }
   ctx->scratch_total = o;
@@ -750,6 +782,7 @@ int z4c_bind(z4c_ctx *ctx, void *u0, void *stage_a, void *stage_b, void *acc, vo
     CK(up(G.o_wtiles, G.wtiles.data(), sizeof(Tile) * G.wtiles.size()));
     CK(up(G.o_stiles, G.stiles.data(), sizeof(Tile) * G.stiles.size()));
     CK(up(G.o_rtiles, G.rtiles.data(), sizeof(Tile) * G.rtiles.size()));
+    CK(up(G.o_ptiles, G.ptiles.data(), sizeof(Tile) * G.ptiles.size()));
   }
   for (int p = 0; p < 2; ++p) {
     CK(up(ctx->o_somm[p], ctx->somm[p].data(), sizeof(CellRef) * ctx->somm[p].size()));

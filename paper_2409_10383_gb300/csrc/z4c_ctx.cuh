@@ -36,9 +36,16 @@ struct Group {
   // specialised on it (FP64 pre-pass schedule, FP32 split schedule)
   struct ExtRange {
     int ext, first, count;
+    bool pair;      // the two-cells-per-thread RHS kernel applies (FP32)
+    int shape = 0;  // tile shape of the range (schedule-5/6 list)
   };
   std::vector<ExtRange> eranges;
-  size_t o_tiles = 0, o_wtiles = 0, o_stiles = 0, o_rtiles = 0;
+  // FP32 schedule 5: per extent range, tiles of the widest shape whose width
+  // divides n_x (two cells per thread) where the pair kernel applies, the
+  // range's 16 x 8 tiles (split RHS kernel) elsewhere
+  std::vector<Tile> ptiles;
+  std::vector<ExtRange> peranges;
+  size_t o_tiles = 0, o_wtiles = 0, o_stiles = 0, o_rtiles = 0, o_ptiles = 0;
   bool empty() const { return tiles.empty(); }
 };
 
@@ -112,6 +119,18 @@ struct z4c_ctx {
   int32_t *d_status() const { return (int32_t *)(scratch + o_status); }
   float *d_kbuf() const { return (float *)(scratch + o_kbuf); }
   bool has_staged() const { return !grp[3].stiles.empty(); }
+  bool has_wide() const {
+    for (const z4c::Group &G : grp)
+      for (const z4c::Group::ExtRange &e : G.peranges)
+        if (G.f32 && e.shape > 0) return true;
+    return false;
+  }
+  bool has_pair() const {
+    for (const z4c::Group &G : grp)
+      for (const z4c::Group::ExtRange &e : G.peranges)
+        if (G.f32 && e.shape > 0 && e.pair) return true;
+    return false;
+  }
   const z4c::CellRef *d_somm(int p) const { return (const z4c::CellRef *)(scratch + o_somm[p]); }
   const z4c::GhostCopy *d_gcopy(int p) const { return (const z4c::GhostCopy *)(scratch + o_gcopy[p]); }
   const z4c::Tile *d_ctiles() const { return (const z4c::Tile *)(scratch + o_ctiles); }

@@ -97,12 +97,19 @@ __global__ void __launch_bounds__(TX * TY) dydz_kernel(StageArgs a, const Tile *
 // NF TX TY; the launcher offsets kbuf for a sub-range of a tile list).
 // EXT > 0: every block of the launch has cubic storage EXT^3 (n + 2g = EXT
 // along all axes), so all stencil offsets are compile-time constants.
-template <int ORD, bool F32, int OCC, bool SPLIT = false, int EXT = 0>
+// SHAPE (SPLIT only): tiles of (TX << SHAPE) x (TY >> SHAPE) cells; thread
+// tid = y TX + x takes cell (tid % (TX << SHAPE), tid / (TX << SHAPE)), so
+// a warp covers one row of 32 cells (SHAPE >= 1) instead of two of 16.
+template <int ORD, bool F32, int OCC, bool SPLIT = false, int EXT = 0, int SHAPE = 0>
 __global__ void __launch_bounds__(TX * TY, OCC) interior_pre_kernel(StageArgs a, const Tile *__restrict__ tiles) {
   using R = typename std::conditional<F32, float, double>::type;
+  static_assert(SHAPE == 0 || SPLIT, "tile shapes other than 16 x 8 are for the split RHS kernel");
+  constexpr int TXS = TX << SHAPE;
   const Tile t = tiles[blockIdx.x];
-  const DevBlock &b = a.blocks[t.block];
-  const int i = t.i0 + threadIdx.x, j = t.j0 + threadIdx.y, kk = t.k0;
+  const DevBlock &b = a.blocks[t.block & TILE_BLOCK_MASK];
+  const int tid0 = threadIdx.y * TX + threadIdx.x;
+  const int i = t.i0 + (SHAPE ? tid0 % TXS : (int)threadIdx.x), j = t.j0 + (SHAPE ? tid0 / TXS : (int)threadIdx.y);
+  const int kk = t.k0;
   if (i >= b.n[0] || j >= b.n[1]) return;
   const int g = b.g;
   const int e0 = EXT > 0 ? EXT : b.e[0], e1 = EXT > 0 ? EXT : b.e[1];
@@ -125,7 +132,7 @@ __global__ void __launch_bounds__(TX * TY, OCC) interior_pre_kernel(StageArgs a,
     const Pre<ORD, float, Src<float, true>, Src<float, false>> dv{s, ds, st, sc};
     rhs_point<ORD, float>(s, dv, st, sc, p, ichi, k);
     if constexpr (SPLIT) {
-      float *kt = a.kbuf + (int64_t)blockIdx.x * NF * (TX * TY) + threadIdx.y * TX + threadIdx.x;
+      float *kt = a.kbuf + (int64_t)blockIdx.x * NF * (TX * TY) + tid0;
 #pragma unroll
       for (int f = 0; f < NF; ++f) kt[f * (TX * TY)] = k[f];
       return;
@@ -137,6 +144,46 @@ __global__ void __launch_bounds__(TX * TY, OCC) interior_pre_kernel(StageArgs a,
     rhs_point<ORD, double>(s, dv, st, sc, p, ichi, k);
   }
   stage_epilogue<R>(a, t.block, off, S, k);
+}
+
+// FP32-RHS split-schedule RHS kernel computing two neighbouring cells of a
+// row per thread on the packed f32x2 instructions (F2), on tiles of shape
+// SHAPE: (TX << SHAPE) x (TY >> SHAPE) cells (1: 32 x 4, 2: 64 x 2), 64
+// threads; thread (tx, ty) owns cells (i0 + 2 tx, i0 + 2 tx + 1) of row
+// j0 + ty, so a warp covers 32 (SHAPE 1: two rows) or 64 cells of a row.
+// The same stencils, pre-pass derivatives and algebra as
+// interior_pre_kernel<ORD, true, 4, true, EXT>; a warp's loads of a stencil
+// point touch few cache lines, and the pair shares its x stencil loads.
+// Requires an even storage extent, an even ghost width and n_x a multiple
+// of the tile width (the host checks; every cell pair then starts 8-byte
+// aligned).  Stores k in a.kbuf like the split RHS kernel, cell (ii, jj) of
+// the tile at jj * (TX << SHAPE) + ii.
+template <int ORD, int EXT, int SHAPE>
+__global__ void __launch_bounds__(TX * TY / 2, 4) interior_pair_kernel(StageArgs a, const Tile *__restrict__ tiles) {
+  static_assert(EXT > 0 && EXT % 2 == 0, "pair kernel needs an even compile-time extent");
+  constexpr int TXS = TX << SHAPE;
+  const Tile t = tiles[blockIdx.x];
+  const int blk = t.block & TILE_BLOCK_MASK;
+  const DevBlock &b = a.blocks[blk];
+  const int i = t.i0 + 2 * threadIdx.x, j = t.j0 + threadIdx.y, kk = t.k0;
+  if (i >= b.n[0] || j >= b.n[1]) return;
+  const int g = b.g;
+  constexpr int e0 = EXT, e1 = EXT;
+  constexpr int32_t S = EXT * EXT * EXT;
+  const int32_t cidx = ((kk + g) * e1 + (j + g)) * e0 + (i + g);
+  const int st[3] = {1, e0, e0 * e1};
+  const int64_t off = b.off + cidx;
+  const F2 ichi(inv_chi_f32(a.x64[off], b.chi_floor), inv_chi_f32(a.x64[off + 1], b.chi_floor));
+  const Phys<F2> p{F2(b.kappa1), F2(b.kappa2), F2(b.eta), b.lapse, b.shift};
+  const Scales<F2> sc{F2(b.s1f), F2(b.s2f), F2(b.smixf), F2(b.slopf), F2(b.skof)};
+  const SrcPair<true> s{a.x32 + b.off, cidx, S};
+  const SrcPair<false> ds{reinterpret_cast<const float *>(a.dstore) + b.off, cidx, S};
+  const Pre<ORD, F2, SrcPair<true>, SrcPair<false>> dv{s, ds, st, sc};
+  F2 k[NF];
+  rhs_point<ORD, F2>(s, dv, st, sc, p, ichi, k);
+  float *kt = a.kbuf + (int64_t)blockIdx.x * NF * (TX * TY) + threadIdx.y * TXS + 2 * threadIdx.x;
+#pragma unroll
+  for (int f = 0; f < NF; ++f) *reinterpret_cast<float2 *>(kt + f * (TX * TY)) = k[f].v;
 }
 
 }  // namespace z4c

@@ -45,6 +45,10 @@ struct DevBlock {
 struct Tile {
   int32_t block, i0, j0, k0;  // interior-relative origin
 };
+// The FP32 schedule-5 tile list mixes tile shapes of 128 cells: shape s is
+// (TX << s) x (TY >> s), kept in bits 28..29 of Tile::block (0 elsewhere).
+constexpr int TILE_SHAPE_SHIFT = 28;
+constexpr int32_t TILE_BLOCK_MASK = (1 << TILE_SHAPE_SHIFT) - 1;
 
 // One Sommerfeld cell (a ghost cell outside the domain) of one block: its
 // storage index and (i, j, k) storage coordinates, and per axis d the
@@ -192,6 +196,12 @@ cudaError_t launch_wait_probe(int32_t *status, int rounds, cudaStream_t st);
 cudaError_t launch_split_rhs_f32(int order, int ext, const StageArgs &a, const Tile *tiles, int ntiles,
                                  cudaStream_t st);
 cudaError_t launch_split_epilogue(const StageArgs &a, const Tile *tiles, int ntiles, cudaStream_t st);
+// schedules 5 and 6: the split RHS kernel on wide tiles (shape 1: 32 x 4,
+// 2: 64 x 2) for the extents built, one cell per thread or (pair) two cells
+// per thread on packed f32x2 arithmetic
+bool wide_ext_built(int order, int ext);
+cudaError_t launch_wide_rhs_f32(int order, int ext, int shape, bool pair, const StageArgs &a, const Tile *tiles,
+                                int ntiles, cudaStream_t st);
 // cubic storage extents with a specialised split RHS kernel (per order)
 bool split_ext_built(int order, int ext);
 // FP64 fused pre-pass-schedule kernel for one extent range (ext as above;

@@ -13,6 +13,8 @@
 // FP64 operations per derivative on a part whose FP64 pipe is the bound.
 #pragma once
 
+#include <type_traits>
+
 #include "z4c_internal.cuh"
 
 namespace z4c {
@@ -267,6 +269,126 @@ struct KoAdvWeights {
   __device__ __forceinline__ R apply_diff(const S_ &s, int f, const int st[3]) const {
     const R c = s.at(f, 0);
     R a[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      a[d] = w[d][0] * (s.at(f, -W * st[d]) - c);
+#pragma unroll
+      for (int m = -W + 1; m <= W; ++m) {
+        if (m == 0) continue;
+        a[d] = fma(w[d][m < 0 ? m + W : m + W - 1], s.at(f, m * st[d]) - c, a[d]);
+      }
+    }
+    return a[0] + (a[1] + a[2]);
+  }
+};
+
+// ---- two cells per thread: FP32 pairs on the packed f32x2 instructions ----
+//
+// F2 holds the same quantity at two neighbouring cells (x and x + 1).  Its
+// arithmetic issues one packed instruction (add / sub / mul / fma .f32x2)
+// for both cells.  A product is kept unevaluated (F2Mul) until it meets an
+// addition, which then becomes one fused multiply-add, so a * b + c costs
+// one instruction as it does for a scalar float.  Each lane rounds like the
+// scalar FP32 path; where the two fuse differently the results differ by
+// FP32 rounding only.
+using ::fabs;  // the scalar overloads stay visible beside the F2 ones below
+using ::fma;
+struct F2 {
+  float2 v;
+  F2() = default;
+  __device__ __forceinline__ F2(float2 a) : v(a) {}
+  __device__ __forceinline__ F2(float a, float b) : v(make_float2(a, b)) {}
+  template <class T, class = typename std::enable_if<std::is_arithmetic<T>::value>::type>
+  __device__ __forceinline__ explicit F2(T x) : v(make_float2(float(x), float(x))) {}
+};
+__device__ __forceinline__ float2 f2_sub(float2 a, float2 b) {
+  unsigned long long d;
+  asm("sub.rn.f32x2 %0, %1, %2;"
+      : "=l"(d)
+      : "l"(*reinterpret_cast<unsigned long long *>(&a)), "l"(*reinterpret_cast<unsigned long long *>(&b)));
+  return *reinterpret_cast<float2 *>(&d);
+}
+struct F2Mul {
+  F2 a, b;
+  __device__ __forceinline__ operator F2() const { return F2(__fmul2_rn(a.v, b.v)); }
+};
+__device__ __forceinline__ F2 fma(F2 a, F2 b, F2 c) { return F2(__ffma2_rn(a.v, b.v, c.v)); }
+__device__ __forceinline__ F2 operator-(F2 a) { return F2(-a.v.x, -a.v.y); }
+__device__ __forceinline__ F2Mul operator*(F2 a, F2 b) { return F2Mul{a, b}; }
+__device__ __forceinline__ F2Mul operator*(F2Mul m, F2 b) { return F2Mul{F2(m), b}; }
+__device__ __forceinline__ F2Mul operator*(F2 a, F2Mul m) { return F2Mul{a, F2(m)}; }
+__device__ __forceinline__ F2Mul operator*(F2Mul m, F2Mul n) { return F2Mul{F2(m), F2(n)}; }
+__device__ __forceinline__ F2Mul operator-(F2Mul m) { return F2Mul{-m.a, m.b}; }
+__device__ __forceinline__ F2 operator+(F2 a, F2 b) { return F2(__fadd2_rn(a.v, b.v)); }
+__device__ __forceinline__ F2 operator-(F2 a, F2 b) { return F2(f2_sub(a.v, b.v)); }
+__device__ __forceinline__ F2 operator+(F2Mul m, F2 c) { return fma(m.a, m.b, c); }
+__device__ __forceinline__ F2 operator+(F2 c, F2Mul m) { return fma(m.a, m.b, c); }
+__device__ __forceinline__ F2 operator-(F2 c, F2Mul m) { return fma(-m.a, m.b, c); }
+__device__ __forceinline__ F2 operator-(F2Mul m, F2 c) { return fma(m.a, m.b, -c); }
+__device__ __forceinline__ F2 operator+(F2Mul m, F2Mul n) { return fma(m.a, m.b, F2(n)); }
+__device__ __forceinline__ F2 operator-(F2Mul m, F2Mul n) { return fma(m.a, m.b, -F2(n)); }
+__device__ __forceinline__ F2 operator/(F2 a, F2 b) { return F2(a.v.x / b.v.x, a.v.y / b.v.y); }
+__device__ __forceinline__ F2 &operator+=(F2 &a, F2 b) { return a = a + b; }
+__device__ __forceinline__ F2 &operator+=(F2 &a, F2Mul m) { return a = a + m; }
+__device__ __forceinline__ F2 &operator-=(F2 &a, F2 b) { return a = a - b; }
+__device__ __forceinline__ F2 &operator-=(F2 &a, F2Mul m) { return a = a - m; }
+__device__ __forceinline__ F2 fabs(F2 a) { return F2(fabsf(a.v.x), fabsf(a.v.y)); }
+template <class R>
+struct is_pair : std::false_type {};
+template <>
+struct is_pair<F2> : std::true_type {};
+
+// Stencil source for a cell pair: field f of the even cell c (and c + 1) of
+// an FP32 array whose row starts are 8-byte aligned (every storage extent
+// and block offset even).  An even offset is one aligned 8-byte load; an odd
+// offset takes the upper half of the pair below and the lower half of the
+// pair above.  SHIFTED: the FP32 shadow's gt diagonal is stored minus one.
+template <bool SHIFTED>
+struct SrcPair {
+  const float *__restrict__ base;
+  int32_t c;
+  int32_t S;
+  __device__ __forceinline__ F2 at(int f, int off) const {
+    const float *p = base + (c + (f * S + off));
+    if ((off & 1) == 0) return F2(__ldg(reinterpret_cast<const float2 *>(p)));
+    const float2 lo = __ldg(reinterpret_cast<const float2 *>(p - 1));
+    const float2 hi = __ldg(reinterpret_cast<const float2 *>(p + 1));
+    return F2(lo.y, hi.x);
+  }
+  __device__ __forceinline__ F2 val(int f) const {
+    F2 v = at(f, 0);
+    if (SHIFTED && (f == GXX || f == GYY || f == GZZ)) v += F2(1.0f);
+    return v;
+  }
+};
+
+// KO dissipation + lopsided advection for a cell pair: per lane the same
+// per-cell weights as KoAdvWeights (oriented by the sign of beta^d at that
+// cell), applied to the differences f(m st_d) - f(0) as in apply_diff.
+template <int ORD>
+struct KoAdvWeightsPair {
+  static constexpr int W = KoAdv<ORD>::KW;
+  F2 w[3][2 * W];
+  __device__ __forceinline__ KoAdvWeightsPair(const F2 beta[3], float slop, float sko) {
+    using K = KoAdv<ORD>;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const float b0 = beta[d].v.x, b1 = beta[d].v.y;
+      const bool up0 = b0 >= 0.f, up1 = b1 >= 0.f;
+      const float ab0 = fabsf(b0) * slop, ab1 = fabsf(b1) * slop;
+#pragma unroll
+      for (int m = 1; m <= W; ++m) {
+        const float kw = sko * float(K::kcoef(m));
+        const float lp = float(K::lcoef(m)), lm = float(K::lcoef(-m));
+        w[d][W + m - 1] = F2(fmaf(ab0, up0 ? lp : lm, kw), fmaf(ab1, up1 ? lp : lm, kw));
+        w[d][W - m] = F2(fmaf(ab0, up0 ? lm : lp, kw), fmaf(ab1, up1 ? lm : lp, kw));
+      }
+    }
+  }
+  template <class S_>
+  __device__ __forceinline__ F2 apply_diff(const S_ &s, int f, const int st[3]) const {
+    const F2 c = s.at(f, 0);
+    F2 a[3];
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       a[d] = w[d][0] * (s.at(f, -W * st[d]) - c);
@@ -627,7 +749,17 @@ __device__ __forceinline__ void rhs_point(const SRC &s, const DV &dv, const int 
   for (int i = 0; i < 3; ++i) k[BETAX + i] = p.shift ? Gam[i] - p.eta * beta[i] : R(0);
 
   // lopsided advection along the shift and Kreiss-Oliger dissipation
-  if constexpr (DV::kStagedKO) {
+  if constexpr (is_pair<R>::value) {
+    // cell pairs: weights per lane; the result goes through a shared-memory
+    // slot per field and thread as in the FP32 branch below
+    const KoAdvWeightsPair<ORD> kaw(beta, sc.slop.v.x, sc.sko.v.x);
+    __shared__ F2 kko2[NF][TX * TY / 2];
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;  // 64 threads
+#pragma unroll 2
+    for (int f = 0; f < NF; ++f) kko2[f][tid] = (!p.shift && f >= BETAX) ? F2(0.0f) : kaw.apply_diff(s, f, st);
+#pragma unroll
+    for (int f = 0; f < NF; ++f) k[f] += kko2[f][tid];
+  } else if constexpr (DV::kStagedKO) {
     // already evaluated per field by the staging pass
 #pragma unroll
     for (int f = 0; f < NF; ++f) {

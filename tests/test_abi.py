@@ -102,7 +102,7 @@ def test_sizes_and_unbound_calls(L):
     rc, ctx = z4c.z4c_create(_mesh(), [_block()], 3, 4, _params(64, schedule=1))
     assert rc == 0 and L.z4c_launches_per_step(ctx) == 8  # single fused kernel
     L.z4c_destroy(ctx)
-    assert z4c.z4c_create(_mesh(), [_block()], 3, 4, _params(64, schedule=5))[0] == z4c.Z4C_ERR_BAD_ARG
+    assert z4c.z4c_create(_mesh(), [_block()], 3, 4, _params(64, schedule=7))[0] == z4c.Z4C_ERR_BAD_ARG
     rc, ctx = z4c.z4c_create(_mesh(), [_block()], 3, 4, _params(64))
     assert L.z4c_set_variant(ctx, 2, 4) == z4c.Z4C_ERR_UNSUPPORTED  # FP64 has one occupancy
     assert L.z4c_set_variant(ctx, 3, 1) == z4c.Z4C_ERR_UNSUPPORTED  # schedule 3 is FP32-RHS only

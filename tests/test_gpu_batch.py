@@ -28,18 +28,33 @@ def _dt(w):
     return w["cfl"] * float(w["h"][0])
 
 
-@pytest.mark.parametrize("mix", ["uneven_batch_small", "mixed_order_batch_small"])
-def test_batch_equals_single_instances(oracle, mix):
-    """mixed_order_batch_small adds 2nd-order instances (FP64 and FP32-RHS)."""
+def _pair_mix():
+    """FP32-RHS instances of 32^3 (32 x 4 tiles), 64^3 (64 x 2) and 16^3
+    (16 x 8 tiles) in one wide-tile list, beside FP64 instances."""
+    I = inputs._instance
+    return [I("puncture", 32, 6, 32, 1.0), I("puncture", 16, 6, 32, 1.5), I("gauge_wave", 32, 6, 32, 0.01),
+            I("puncture", 16, 6, 64, 1.2), I("puncture", 64, 6, 32, 0.8), I("puncture", 16, 4, 32, 0.9)]
+
+
+@pytest.mark.parametrize("mix,schedule", [("uneven_batch_small", 0), ("mixed_order_batch_small", 0),
+                                          ("pair_mix", 5), ("pair_mix", 6)])
+def test_batch_equals_single_instances(oracle, mix, schedule):
+    """mixed_order_batch_small adds 2nd-order instances (FP64 and FP32-RHS);
+    schedules 5 and 6 run the FP32-RHS instances whose blocks allow it on
+    wide tiles (6: two cells per thread), alone and in the batch alike."""
     from paper_2409_10383_gb300.z4c import Z4c
-    ws = getattr(inputs, mix)()
+    ws = _pair_mix() if mix == "pair_mix" else getattr(inputs, mix)()
     g = Z4c.batch(ws)
+    if schedule:
+        g.z4c_set_variant(schedule, 4)
     for i, w in enumerate(ws):
         g.z4c_set_initial_data_instance(i, w["id_kind"], w["id_par"])
     g.z4c_rk4_step_batch([_dt(w) for w in ws], STEPS)
     got = g.z4c_get_state()
     for i, w in enumerate(ws):
         s = Z4c.from_workload(w, precision=w["precision"])
+        if schedule and w["precision"] == 32:
+            s.z4c_set_variant(schedule, 4)
         s.z4c_set_initial_data(w["id_kind"], w["id_par"])
         s.z4c_rk4_step(_dt(w), STEPS)
         ref = s.z4c_get_state()

@@ -131,14 +131,16 @@ def test_rhs_closed_form_constant_state(oracle, order, lapse, kappa2, slopes, al
 
 
 @pytest.mark.parametrize("order,precision,schedule", [(6, 64, 1), (6, 64, 2), (6, 32, 1), (6, 32, 2), (6, 32, 3),
-                                                      (6, 32, 4), (2, 64, 1), (2, 64, 2), (2, 32, 1), (2, 32, 4)])
+                                                      (6, 32, 4), (6, 32, 5), (6, 32, 6), (2, 64, 1), (2, 64, 2),
+                                                      (2, 32, 1), (2, 32, 4)])
 def test_flat_space_is_exactly_static(oracle, order, precision, schedule):
-    # 16^3 blocks qualify for the staged FP32 kernel (schedule 3)
-    n = 16 if schedule == 3 else 12
+    # 16^3 blocks qualify for the staged FP32 kernel (schedule 3), 32^3 for
+    # the wide tiles (schedules 5 and 6, 32 x 4)
+    n = 16 if schedule == 3 else 32 if schedule >= 5 else 12
     w = H.small_workload("puncture", order, (2, 1, 1), n, id_kind=inputs.ID_FLAT, id_par=[])
     g = H.gpu_ctx(w, precision, schedule)
-    if schedule == 4:
-        g.z4c_set_variant(4, 4)
+    if schedule >= 4:
+        g.z4c_set_variant(schedule, 4)
     g.z4c_set_initial_data(inputs.ID_FLAT, [])
     g.z4c_fill_ghosts(0)
     assert np.all(g.z4c_rhs(0).cpu().numpy() == 0.0)
@@ -229,7 +231,8 @@ def _round_like_shadow(m, u):
 
 
 @pytest.mark.parametrize("order,schedule,occupancy", [(6, 1, 1), (6, 2, 1), (6, 2, 2), (6, 2, 4), (6, 3, 4),
-                                                      (6, 4, 4), (2, 1, 1), (2, 2, 2), (2, 4, 4)])
+                                                      (6, 4, 4), (6, 5, 4), (6, 6, 4), (2, 1, 1), (2, 2, 2),
+                                                      (2, 4, 4)])
 def test_fp32_rhs_error_budget(oracle, order, schedule, occupancy):
     """FP32 stencils and algebra (FP64 state, RK accumulation, 1/chi,
     enforcement).  Bounds, stated against what FP32 storage alone causes:
@@ -239,7 +242,8 @@ def test_fp32_rhs_error_budget(oracle, order, schedule, occupancy):
         change |u64(t) - u64(0)|, the puncture lapse (min alpha) within 1e-3
         of its change, and ||H||_2 within 1e-5 (relative) of FP64.
     Orders 6 and 2 (the staged schedule 3 exists for order 6 only)."""
-    w = H.small_workload("puncture", order, (2, 2, 2), 16)
+    # schedules 5 and 6 take their wide-tile kernels on blocks of 32 or more
+    w = H.small_workload("puncture", order, (2, 2, 2), 32 if schedule >= 5 else 16)
     m = H.oracle_mesh(oracle, w)
     g = H.gpu_ctx(w, precision=32, schedule=schedule)
     g.z4c_set_variant(schedule, occupancy)
@@ -303,6 +307,45 @@ def test_fp32_split_and_occupancy_builds_are_bit_identical(oracle):
         assert np.array_equal(steps[v], steps[(2, 1)]), v
 
 
+@pytest.mark.parametrize("nb,n", [((2, 1, 1), 32), ((1, 1, 1), 64)])
+def test_fp32_wide_tile_and_pair_kernels(oracle, nb, n):
+    """Schedule 5 runs the split RHS kernel on wide tiles (32 x 4 for 32^3
+    blocks, 64 x 2 for 64^3): the same arithmetic per cell as schedule 4 on
+    16 x 8 tiles, so the RHS and the RK4 steps are bit-identical.  Schedule
+    6 evaluates the same FP32 stencils and algebra two cells per thread on
+    packed f32x2 instructions; only where products are fused into
+    multiply-adds may it round differently.  One RHS call and two RK4 steps
+    of a perturbed puncture state: every field of its RHS within 2e-6 of
+    the field's scale (FP32 rounding, amplified by the stencils'
+    cancellation), and after the steps every field within 1e-4 of its
+    change over the steps (the FP32 budget against FP64 allows 1e-3)."""
+    w = H.small_workload("puncture", 6, nb, n)
+    m = H.oracle_mesh(oracle, w)
+    u = m.initial_data(w["id_kind"], w["id_par"])
+    m.fill_ghosts(u)
+    H.perturb(m, u, 78, 1e-3)
+    dt = 0.25 * float(w["h"][0])
+    rhs, steps = {}, {}
+    for sch in (4, 5, 6):
+        g = H.gpu_ctx(w, precision=32, schedule=sch)
+        g.z4c_set_variant(sch, 4)
+        g.z4c_set_state(u, reg=1)
+        rhs[sch] = g.z4c_rhs(1).cpu().numpy().copy()
+        g.z4c_set_state(u)
+        g.z4c_rk4_step(dt, 2)
+        steps[sch] = g.z4c_get_state()
+        g.close()
+    assert np.array_equal(rhs[5], rhs[4])
+    assert np.array_equal(steps[5], steps[4])
+    err, absd = H.field_errors(m, rhs[4], rhs[6], mask_fn="interior")
+    assert err.max() <= 2e-6, (err, absd)
+    for b in range(m.nblocks):
+        mk = m.interior_mask(b)
+        d = np.abs(m.blocks(steps[6])[b][:, mk] - m.blocks(steps[4])[b][:, mk]).max(axis=1)
+        c = np.abs(m.blocks(steps[4])[b][:, mk] - m.blocks(u)[b][:, mk]).max(axis=1)
+        assert np.all(d <= 1e-4 * c + 1e-14), (b, d, c)
+
+
 def test_autotune_keeps_state_and_picks_a_built_variant(oracle):
     """The autotuner runs only stage 1 (U0 unchanged) and leaves a valid
     variant; evolution after tuning still matches the oracle."""
@@ -313,7 +356,10 @@ def test_autotune_keeps_state_and_picks_a_built_variant(oracle):
         g.z4c_set_initial_data(w["id_kind"], w["id_par"])
         before = g.z4c_get_state()
         sch, occ = g.z4c_autotune(2)
-        assert sch in (1, 2) and occ in ((1,) if prec == 64 else (1, 2, 4))
+        if prec == 64:
+            assert sch in (1, 2) and occ == 1
+        else:
+            assert (sch, occ) in ((1, 1), (2, 1), (2, 2), (2, 4), (3, 4), (4, 4), (5, 4), (6, 4))
         after = g.z4c_get_state()
         for b in range(m.nblocks):
             ev = m.evolved_mask(b)
