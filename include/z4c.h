@@ -273,11 +273,22 @@ int z4c_profile_steps(z4c_ctx *ctx, double dt, int nsteps, double *ms);
  * no CUDA call. */
 int z4c_set_variant(z4c_ctx *ctx, int schedule, int occupancy);
 
+/* FP32-RHS split schedules (4 to 6): which kernel applies the RK stage
+ * update and the enforcement.  kind 0 (the default): the plain kernel, one
+ * thread per cell at high occupancy; kind 1: a persistent kernel fed by
+ * bulk asynchronous copies (TMA) of each tile's k record and FP64 rows into
+ * shared memory, for the tiles that allow it (full tiles, even ghost width
+ * and storage extent, 16-byte aligned registers), the plain kernel for the
+ * others.  The same arithmetic either way (bit-identical results).
+ * Z4C_ERR_BAD_ARG for another kind.  Makes no CUDA call. */
+int z4c_set_epilogue(z4c_ctx *ctx, int kind);
+
 /* Pick the fastest kernel variant for this context on this GPU: the
  * schedule (1 or 2; for FP32-RHS blocks also 4, and 3, 5 and 6 where
  * blocks qualify; see z4c_params)
  * and, for the FP32-RHS fused kernel, the number of resident CTAs per SM its
- * registers are budgeted for (1, 2, 4).
+ * registers are budgeted for (1, 2, 4), and for the split schedules the
+ * stage-update kernel (z4c_set_epilogue).
  * Each candidate runs reps + 1 times the ghost fill and stage 1 of RK4 (which
  * reads U0 and overwrites only the accumulator and stage A, so U0 keeps its
  * value); the fastest is kept, FP64 and FP32-RHS kernels tuned separately.

@@ -113,7 +113,8 @@ int launch_fused_group(z4c_ctx *ctx, int g, const StageArgs &a) {
       tl = ctx->at<Tile>(G.o_ptiles);
       nt = (int)G.ptiles.size();
     }
-    for (const Group::ExtRange &e : sc >= 5 ? G.peranges : G.eranges) {
+    const std::vector<Group::ExtRange> &rs = sc >= 5 ? G.peranges : G.eranges;
+    for (const Group::ExtRange &e : rs) {
       StageArgs ar = a;
       ar.kbuf = a.kbuf + (size_t)e.first * NF * TX * TY;
       if (e.shape > 0)
@@ -122,7 +123,21 @@ int launch_fused_group(z4c_ctx *ctx, int g, const StageArgs &a) {
       else
         CK(launch_split_rhs_f32(G.order, e.ext, ar, tl + e.first, e.count, ctx->stream));
     }
-    CK(launch_split_epilogue(a, tl, nt, ctx->stream));
+    // the stage update: fed by bulk copies where the tiles allow it (not for
+    // a plain RHS evaluation), else one plain launch over the rest
+    const bool tma = ctx->epi_tma && a.mode != MODE_RHS && epilogue_tma_ok(a);
+    bool all = tma;
+    for (const Group::ExtRange &e : rs) all = all && e.full;
+    if (!tma || all) {
+      CK(all ? launch_split_epilogue_tma(a, tl, nt, ctx->stream) : launch_split_epilogue(a, tl, nt, ctx->stream));
+      return Z4C_OK;
+    }
+    for (const Group::ExtRange &e : rs) {
+      StageArgs ar = a;
+      ar.kbuf = a.kbuf + (size_t)e.first * NF * TX * TY;
+      CK(e.full ? launch_split_epilogue_tma(ar, tl + e.first, e.count, ctx->stream)
+                : launch_split_epilogue(ar, tl + e.first, e.count, ctx->stream));
+    }
     return Z4C_OK;
   }
   if (G.f32 && ctx->sched[1] == 3 && !G.stiles.empty()) {
@@ -521,6 +536,14 @@ int z4c_set_variant(z4c_ctx *ctx, int schedule, int occupancy) {
   return Z4C_OK;
 }
 
+int z4c_set_epilogue(z4c_ctx *ctx, int kind) {
+  if (!ctx) return Z4C_ERR_BAD_ARG;
+  if (kind != 0 && kind != 1) return fail(ctx, Z4C_ERR_BAD_ARG, "epilogue kind must be 0 or 1");
+  ctx->epi_tma = kind == 1;
+  ctx->drop_graph();
+  return Z4C_OK;
+}
+
 int z4c_autotune(z4c_ctx *ctx, int reps, int *schedule_out, int *occupancy_out) {
   int r = ensure_bound(ctx);
   if (r) return r;
@@ -536,6 +559,7 @@ int z4c_autotune(z4c_ctx *ctx, int reps, int *schedule_out, int *occupancy_out) 
   CK(cudaEventCreate(&e1));
   struct Cand {
     int sched, occ;
+    bool tma = true;
   };
   for (int p = 0; p < 2; ++p) {  // tune each precision with the other fixed
     if (!ctx->has[p]) continue;
@@ -544,15 +568,25 @@ int z4c_autotune(z4c_ctx *ctx, int reps, int *schedule_out, int *occupancy_out) 
       cands.push_back({2, 2});
       cands.push_back({2, 4});
       if (ctx->has_staged()) cands.push_back({3, 4});
-      cands.push_back({4, 4});
-      if (ctx->has_wide()) cands.push_back({5, 4});
-      if (ctx->has_pair()) cands.push_back({6, 4});
+      cands.push_back({4, 4, false});
+      cands.push_back({4, 4, true});
+      if (ctx->has_wide()) {
+        cands.push_back({5, 4, false});
+        cands.push_back({5, 4, true});
+      }
+      if (ctx->has_pair()) {
+        cands.push_back({6, 4, false});
+        cands.push_back({6, 4, true});
+      }
     }
     float best = 1e30f;
-    Cand pick = {ctx->sched[p], p == 1 ? ctx->occ[1] : 1};
+    Cand pick = {ctx->sched[p], p == 1 ? ctx->occ[1] : 1, ctx->epi_tma};
     for (const Cand &c : cands) {
       ctx->sched[p] = c.sched;
-      if (p == 1) ctx->occ[1] = c.occ;
+      if (p == 1) {
+        ctx->occ[1] = c.occ;
+        ctx->epi_tma = c.tma;
+      }
       for (int rep = 0; rep <= reps; ++rep) {  // first pass untimed
         if (rep == 1) CK(cudaEventRecord(e0, ctx->stream));
         r = fill_ghosts(ctx, ctx->reg[0], ctx->has[1] ? ctx->d_sh(0) : nullptr);
@@ -570,7 +604,10 @@ int z4c_autotune(z4c_ctx *ctx, int reps, int *schedule_out, int *occupancy_out) 
       }
     }
     ctx->sched[p] = pick.sched;
-    if (p == 1) ctx->occ[1] = pick.occ;
+    if (p == 1) {
+      ctx->occ[1] = pick.occ;
+      ctx->epi_tma = pick.tma;
+    }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

@@ -658,6 +658,18 @@ int z4c_create_batch(const z4c_instance *instances, int ninstances, const z4c_bl
       pr.count = (int)G.ptiles.size() - pr.first;
       G.peranges.push_back(pr);
     }
+    // full, 16-byte aligned tiles for the bulk-copy stage update
+    auto full_of = [&](const std::vector<Tile> &tl, Group::ExtRange &r) {
+      r.full = true;
+      for (int q = r.first; q < r.first + r.count; ++q) {
+        const int sh = tl[q].block >> TILE_SHAPE_SHIFT;
+        const DevBlock &D = ctx->dblocks[tl[q].block & TILE_BLOCK_MASK];
+        r.full = r.full && D.n[0] % (TX << sh) == 0 && D.n[1] % (TY >> sh) == 0 && D.g % 2 == 0 &&
+                 D.e[0] % 2 == 0 && D.e[1] % 2 == 0 && D.off % 2 == 0 && D.S % 2 == 0;
+      }
+    };
+    for (Group::ExtRange &r : G.eranges) full_of(G.tiles, r);
+    for (Group::ExtRange &r : G.peranges) full_of(G.ptiles, r);
   }
   // prolongation slots transposed to [125][entries] so that the threads of a
   // warp (neighbouring entries) read consecutive words

@@ -38,6 +38,9 @@ struct Group {
     int ext, first, count;
     bool pair;      // the two-cells-per-thread RHS kernel applies (FP32)
     int shape = 0;  // tile shape of the range (schedule-5/6 list)
+    // full tiles with 16-byte aligned rows (even ghost width, storage
+    // extent and block offset): the bulk-copy stage-update kernel applies
+    bool full = false;
   };
   std::vector<ExtRange> eranges;
   // FP32 schedule 5: per extent range, tiles of the widest shape whose width
@@ -107,6 +110,7 @@ struct z4c_ctx {
   // kernel) and occupancy (resident CTAs per SM the pre-pass-schedule FP32
   // kernel is built for)
   int sched[2] = {2, 2}, occ[2] = {1, 4};
+  bool epi_tma = false;  // FP32 split schedules: the bulk-copy stage update where tiles allow
   // graph of one RK4 step
   cudaGraphExec_t graph = nullptr;
   std::string err;

@@ -196,6 +196,10 @@ cudaError_t launch_wait_probe(int32_t *status, int rounds, cudaStream_t st);
 cudaError_t launch_split_rhs_f32(int order, int ext, const StageArgs &a, const Tile *tiles, int ntiles,
                                  cudaStream_t st);
 cudaError_t launch_split_epilogue(const StageArgs &a, const Tile *tiles, int ntiles, cudaStream_t st);
+// the same, persistent, fed by bulk copies into shared memory (full tiles,
+// even ghost width and storage extent, 16-byte aligned registers)
+cudaError_t launch_split_epilogue_tma(const StageArgs &a, const Tile *tiles, int ntiles, cudaStream_t st);
+bool epilogue_tma_ok(const StageArgs &a);
 // schedules 5 and 6: the split RHS kernel on wide tiles (shape 1: 32 x 4,
 // 2: 64 x 2) for the extents built, one cell per thread or (pair) two cells
 // per thread on packed f32x2 arithmetic

@@ -1127,9 +1127,17 @@ __device__ __forceinline__ void enforce(double v[NF]) {
 // FP64 fused multiply-adds of the FP64 RHS.  FP32 mode: the increment c k of
 // the FP32 RHS is formed in FP32 and added to the FP64 state / accumulator
 // in FP64; the next stage also goes to the FP32 shadow (gt diagonal minus 1).
-template <class R>
-__device__ __forceinline__ void stage_epilogue(const StageArgs &a, int32_t block, int64_t off, int32_t S,
-                                               const R k[NF]) {
+// The stage state u0 and the accumulator are read through U0 / ACC:
+// GlobalField (from the registers, the default) or a staged copy.
+struct GlobalField {
+  const double *p;
+  int64_t off;
+  int32_t S;
+  __device__ __forceinline__ double operator()(int f) const { return p[off + (int64_t)f * S]; }
+};
+template <class R, class U0F, class ACCF>
+__device__ __forceinline__ void stage_epilogue_from(const StageArgs &a, int32_t block, int64_t off, int32_t S,
+                                                    const R k[NF], const U0F &u0f, const ACCF &accf) {
   constexpr bool F32 = sizeof(R) == 4;
   const double dt = a.mode == MODE_RHS ? 0.0 : a.dts[block];
   const double ca = a.fa * dt, cb = a.fb * dt;
@@ -1147,26 +1155,26 @@ __device__ __forceinline__ void stage_epilogue(const StageArgs &a, int32_t block
       const double dn = f2d_int(caf * float(k[f]));
       const double da = f2d_int(cbf * float(k[f]));
       if (a.mode == MODE_S1) {
-        const double u = a.u0[o];
+        const double u = u0f(f);
         a.acc[o] = u + da;
         v[f] = u + dn;
       } else if (a.mode == MODE_S23) {
-        a.acc[o] = a.acc[o] + da;
-        v[f] = a.u0[o] + dn;
+        a.acc[o] = accf(f) + da;
+        v[f] = u0f(f) + dn;
       } else {
-        v[f] = a.acc[o] + da;
+        v[f] = accf(f) + da;
       }
     } else {
       const double kd = double(k[f]);
       if (a.mode == MODE_S1) {
-        const double u = a.u0[o];
+        const double u = u0f(f);
         a.acc[o] = fma(cb, kd, u);
         v[f] = fma(ca, kd, u);
       } else if (a.mode == MODE_S23) {
-        a.acc[o] = fma(cb, kd, a.acc[o]);
-        v[f] = fma(ca, kd, a.u0[o]);
+        a.acc[o] = fma(cb, kd, accf(f));
+        v[f] = fma(ca, kd, u0f(f));
       } else {
-        v[f] = fma(cb, kd, a.acc[o]);
+        v[f] = fma(cb, kd, accf(f));
       }
     }
   }
@@ -1187,6 +1195,12 @@ __device__ __forceinline__ void stage_epilogue(const StageArgs &a, int32_t block
       a.next32[off + (int64_t)f * S] = d2f_int(w);
     }
   }
+}
+
+template <class R>
+__device__ __forceinline__ void stage_epilogue(const StageArgs &a, int32_t block, int64_t off, int32_t S,
+                                               const R k[NF]) {
+  stage_epilogue_from<R>(a, block, off, S, k, GlobalField{a.u0, off, S}, GlobalField{a.acc, off, S});
 }
 
 // 1/max(chi, floor) in FP64 for the FP32 algebra: integer compare (both

@@ -311,7 +311,8 @@ def test_fp32_split_and_occupancy_builds_are_bit_identical(oracle):
 def test_fp32_wide_tile_and_pair_kernels(oracle, nb, n):
     """Schedule 5 runs the split RHS kernel on wide tiles (32 x 4 for 32^3
     blocks, 64 x 2 for 64^3): the same arithmetic per cell as schedule 4 on
-    16 x 8 tiles, so the RHS and the RK4 steps are bit-identical.  Schedule
+    16 x 8 tiles, so the RHS and the RK4 steps are bit-identical, with the
+    plain stage-update kernel and with the one fed by bulk copies.  Schedule
     6 evaluates the same FP32 stencils and algebra two cells per thread on
     packed f32x2 instructions; only where products are fused into
     multiply-adds may it round differently.  One RHS call and two RK4 steps
@@ -326,17 +327,22 @@ def test_fp32_wide_tile_and_pair_kernels(oracle, nb, n):
     H.perturb(m, u, 78, 1e-3)
     dt = 0.25 * float(w["h"][0])
     rhs, steps = {}, {}
-    for sch in (4, 5, 6):
+    for sch, epi in ((4, 0), (4, 1), (5, 0), (5, 1), (6, 1)):
         g = H.gpu_ctx(w, precision=32, schedule=sch)
         g.z4c_set_variant(sch, 4)
+        g.z4c_set_epilogue(epi)
         g.z4c_set_state(u, reg=1)
         rhs[sch] = g.z4c_rhs(1).cpu().numpy().copy()
         g.z4c_set_state(u)
         g.z4c_rk4_step(dt, 2)
-        steps[sch] = g.z4c_get_state()
+        steps[(sch, epi)] = g.z4c_get_state()
         g.close()
+    steps[4] = steps[(4, 0)]
+    steps[6] = steps[(6, 1)]
     assert np.array_equal(rhs[5], rhs[4])
-    assert np.array_equal(steps[5], steps[4])
+    # the wide tiles and the bulk-copy stage update change no arithmetic
+    for v in ((4, 1), (5, 0), (5, 1)):
+        assert np.array_equal(steps[v], steps[4]), v
     err, absd = H.field_errors(m, rhs[4], rhs[6], mask_fn="interior")
     assert err.max() <= 2e-6, (err, absd)
     for b in range(m.nblocks):
