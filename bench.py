@@ -61,6 +61,9 @@ FP64_DRAM_BYTES_PER_CELL = {6: (121026816 + 85157632) / 262144, 2: (114210560 + 
 FP32_OPS_PER_CELL_STAGE = {6: dict(fadd=1085, ffma=1274, fmul=507)}
 FP32_F64_RESIDUE_PER_CELL_STAGE = {6: dict(dadd=47, dfma=22, dmul=25)}
 FP32_DRAM_BYTES_PER_CELL = {6: (62186496 + 4548096 + 75075840 + 28735744) / 262144}
+# the same for schedule 6 (interior_pair_kernel<6,72,2> on 64 x 2 tiles +
+# split_epilogue_kernel on the same tiles), one 64^3 block, stage 1
+FP32_DRAM_BYTES_PER_CELL_PAIR = {6: (62200576 + 6005760 + 75092736 + 28943360) / 262144}
 # algorithmic HBM bytes per zone-cycle (fused 3-register RK4, 22 FP64 fields;
 # the same for the FP32-RHS path, whose state stays FP64)
 ALG_BYTES_PER_ZONE_CYCLE = 352 * 8
@@ -231,7 +234,7 @@ def measure(z4c, torch, workload, prec, args, ws, local):
     # --no-autotune keeps the built-in default (FP64 schedule 2; FP32 split
     # schedule 4), e.g. for a profiler run whose serialised timings would
     # mislead the tuner
-    variant = ((2, 1) if prec == 64 else (4, 4)) if args.no_autotune else g.z4c_autotune(3)
+    variant = ((2, 1) if prec == 64 else (args.fp32_schedule, 4)) if args.no_autotune else g.z4c_autotune(3)
     if args.no_autotune:
         g.z4c_set_variant(*variant)
 
@@ -308,12 +311,21 @@ def measure(z4c, torch, workload, prec, args, ws, local):
                     "unit": "T FP64-pipe instructions/s",
                     "peak_source": "measured DFMA instruction rate (z4c_peak_fma FP64 / 2)",
                     "fp64_residue_flops_per_cell_stage": f64 / cells}
+        ext = int(workload["n"][0][0]) + 2 * int(workload["ghosts"])
+        n0 = int(workload["n"][0][0])
+        shape = "64x2" if n0 % 64 == 0 else "32x4" if n0 % 32 == 0 else "16x8"
+        traffic = (FP32_DRAM_BYTES_PER_CELL[order] * cells if variant[0] == 4 else
+                   FP32_DRAM_BYTES_PER_CELL_PAIR[order] * cells if variant[0] == 6 and shape == "64x2" else None)
+        kname = {4: f"interior_pre_kernel<{order},true,4,split,{ext}> (16x8 tiles)",
+                 5: f"interior_pre_kernel<{order},true,4,split,{ext},wide> ({shape} tiles)",
+                 6: f"interior_pair_kernel<{order},{ext},wide> (two cells per thread, f32x2, {shape} tiles)"}
         roof.update({"frac": t[kind] / sec, "limiter": kind,
-                     "traffic": FP32_DRAM_BYTES_PER_CELL[order] * cells if variant[0] == 4 else None,
-                     "traffic_note": "ncu dram bytes of both split-schedule kernels, one 64^3 block, scaled by cells",
-                     "kernel": (f"interior_pre_kernel<{order},true,4,split,ext> + split_epilogue_kernel (FP32 RHS, "
-                                "FP64 state/RK/enforcement)") if variant[0] == 4 else
-                               f"interior_pre_kernel<{order},true,{variant[1]}> (FP32 RHS, FP64 state/RK/enforcement)",
+                     "traffic": traffic,
+                     "traffic_note": "ncu dram bytes of the RHS and stage-update kernels, one 64^3 block, "
+                                     "scaled by cells",
+                     "kernel": (kname[variant[0]] + " + split_epilogue_kernel (FP32 RHS, FP64 state/RK/enforcement)")
+                     if variant[0] in kname else
+                     f"interior_pre_kernel<{order},true,{variant[1]}> (FP32 RHS, FP64 state/RK/enforcement)",
                      "bound_ms_per_launch": {k: v * 1e3 for k, v in t.items()},
                      "fracs": {k: v / sec for k, v in t.items()}})
     else:
@@ -521,6 +533,8 @@ def measure_batch(z4c, torch, steps, warmup, autotune=True):
     for i, w in enumerate(ws):
         g.z4c_set_initial_data_instance(i, w["id_kind"], w["id_par"])
     variant = g.z4c_autotune(2) if autotune else (4, 4)
+    if not autotune:
+        g.z4c_set_variant(*variant)
     dts = [w["cfl"] * float(w["h"][0]) for w in ws]
     cells = sum(int(np.prod(w["n"], axis=1).sum()) for w in ws)
     g.z4c_rk4_step_batch(dts, max(1, warmup))
@@ -621,6 +635,9 @@ def main():
                     help="skip the paper's Table-1 workload (linear wave on 64^3 blocks)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default kernel variant instead of timing the candidates")
+    ap.add_argument("--fp32-schedule", type=int, default=4, choices=[4, 5, 6],
+                    help="with --no-autotune: the FP32-RHS split schedule (4: 16x8 tiles; 5: wide tiles; "
+                         "6: wide tiles, two cells per thread)")
     ap.add_argument("--smr-only", action="store_true",
                     help="time only the refined two-puncture workload (prints its object)")
     args = ap.parse_args()
