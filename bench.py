@@ -237,6 +237,8 @@ def measure(z4c, torch, workload, prec, args, ws, local):
     variant = ((2, 1) if prec == 64 else (args.fp32_schedule, 4)) if args.no_autotune else g.z4c_autotune(3)
     if args.no_autotune:
         g.z4c_set_variant(*variant)
+        if prec == 32:
+            g.z4c_set_epilogue(args.fp32_epilogue)
 
     def barrier():
         torch.cuda.synchronize()
@@ -638,6 +640,8 @@ def main():
     ap.add_argument("--fp32-schedule", type=int, default=4, choices=[4, 5, 6],
                     help="with --no-autotune: the FP32-RHS split schedule (4: 16x8 tiles; 5: wide tiles; "
                          "6: wide tiles, two cells per thread)")
+    ap.add_argument("--fp32-epilogue", type=int, default=0, choices=[0, 1],
+                    help="with --no-autotune: the FP32-RHS stage-update kernel (0 plain, 1 fed by bulk copies)")
     ap.add_argument("--smr-only", action="store_true",
                     help="time only the refined two-puncture workload (prints its object)")
     args = ap.parse_args()
