@@ -754,8 +754,9 @@ def main():
         line["paper_table1"] = table1
     if batched is not None:
         line["batched"] = batched
-    head = {"fp64": {"value": r["value"], "ms_per_step": r["ms_per_step"],
-                     "roofline_frac": r["roofline"]["frac"], "bound": "FP64 pipe"}}
+    head = {("fp64" if prim == 64 else "fp32_rhs"): {
+        "value": r["value"], "ms_per_step": r["ms_per_step"], "roofline_frac": r["roofline"]["frac"],
+        "bound": "FP64 pipe" if prim == 64 else r["roofline"].get("limiter")}}
     if prim == 64 and 32 in res:
         q = res[32]
         qr = q["roofline"]
