@@ -36,7 +36,7 @@ __device__ __forceinline__ double uinf_of(int f) {
 }
 
 template <bool F32>
-__global__ void __launch_bounds__(128, F32 ? 6 : 4) sommerfeld_kernel(StageArgs a, const CellRef *__restrict__ cells, int n) {
+__global__ void __launch_bounds__(128, F32 ? 8 : 4) sommerfeld_kernel(StageArgs a, const CellRef *__restrict__ cells, int n) {
   using R = typename std::conditional<F32, float, double>::type;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
