@@ -136,8 +136,9 @@ def oracle_sample(workload, steps, warmup, n0=None, threads=None):
         times.append(time.perf_counter() - t0)
     cells = n0 ** 3
     return dict(value=cells * steps / sum(times), unit=UNIT, cores=cores, kind="oracle",
-                sample=f"{steps} RK4 step(s) of one {n0}^3 block (order {w['order']}, "
-                       f"KO {w['ko_sigma']}, Sommerfeld, puncture data) after {warmup} warm-up",
+                sample=f"{steps} RK4 step(s) of one {n0}^3 block on [{lo:g},{-lo:g}]^3 at h = {float(w['h'][0]):g} "
+                       f"(order {w['order']}, KO {w['ko_sigma']}, Sommerfeld on all faces, puncture data at its "
+                       f"centre; the per-cell work of the workload's blocks) after {warmup} warm-up",
                 ms_per_step=1e3 * sum(times) / steps)
 
 
@@ -723,7 +724,7 @@ def main():
         return
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
-        c = oracle_sample(workload, args.cpu_steps, 0)
+        c = oracle_sample(workload, args.cpu_steps, 1)
         cpu = {k: c[k] for k in ("value", "unit", "cores", "kind", "sample")}
         # the same oracle on one core (a smaller block keeps it to about a second)
         c1 = oracle_sample(workload, 1, 0, n0=32, threads=1)

@@ -120,3 +120,33 @@ def test_config5_uneven_batch_full_size_rhs_sampled(oracle):
             bad.append((i, w["name"], w["order"], w["precision"], int(f), float(err[f]), float(bar[f])))
     g.close()
     assert not bad, bad
+
+
+def test_config5_fp64_instances_one_rk4_step_whole_mesh(oracle):
+    """The same batch, autotuned, one RK4 step (each instance at its own
+    dt, one graph launch): every FP64 instance against the oracle's RK4
+    step of that instance over every evolved cell, 1e-10 per field relative
+    to the field's largest value on the instance (the bar of the whole-mesh
+    step tests), from the GPU's own initial state."""
+    from paper_2409_10383_gb300.z4c import Z4c
+    ws = inputs.uneven_batch()
+    g = Z4c.batch(ws)
+    for i, w in enumerate(ws):
+        g.z4c_set_initial_data_instance(i, w["id_kind"], w["id_par"])
+    g.z4c_autotune(2)
+    u0 = g.z4c_get_state(0)
+    dts = [w["cfl"] * float(w["h"][0]) for w in ws]
+    g.z4c_rk4_step_batch(dts, 1)
+    got = g.z4c_get_state(0)
+    g.close()
+    bad = []
+    for i, w in enumerate(ws):
+        if w["precision"] != 64:
+            continue
+        m = H.oracle_mesh(oracle, w)
+        u = u0[g.instance_slice(i)].copy()
+        m.rk4(u, dts[i], 1)
+        rel, _ = H.field_errors(m, u, got[g.instance_slice(i)])
+        if rel.max() > 1e-10:
+            bad.append((i, w["name"], w["order"], float(rel.max()), int(rel.argmax())))
+    assert not bad, bad
