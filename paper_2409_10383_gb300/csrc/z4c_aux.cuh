@@ -35,8 +35,15 @@ __device__ __forceinline__ double uinf_of(int f) {
   return (f == CHI || f == GXX || f == GYY || f == GZZ || f == ALPHA) ? 1.0 : 0.0;
 }
 
+// SOMM_PRELOAD: the stage's FP64 operands (u0 and / or the accumulator) are
+// loaded after the RHS, all at once, before the update (registers to hold
+// them at SOMM_OCC CTAs per SM).
 template <bool F32>
-__global__ void __launch_bounds__(128, F32 ? 8 : 4) sommerfeld_kernel(StageArgs a, const CellRef *__restrict__ cells, int n) {
+constexpr bool SOMM_PRELOAD = F32;
+template <bool F32>
+constexpr int SOMM_OCC = F32 ? 3 : 4;
+template <bool F32>
+__global__ void __launch_bounds__(128, SOMM_OCC<F32>) sommerfeld_kernel(StageArgs a, const CellRef *__restrict__ cells, int n) {
   using R = typename std::conditional<F32, float, double>::type;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
@@ -105,7 +112,13 @@ __global__ void __launch_bounds__(128, F32 ? 8 : 4) sommerfeld_kernel(StageArgs 
     for (int d = 0; d < 3; ++d) v = fma(a1[d], p[o1[d]] - u, fma(a2[d], p[o2[d]] - u, v));
     k[f] = v;
   }
-  stage_epilogue<R>(a, c.block, off, b.S, k);
+  if constexpr (SOMM_PRELOAD<F32>) {
+    StageOperands op;
+    op.load(a, off, b.S);
+    stage_epilogue_preloaded<R>(a, c.block, off, b.S, k, op);
+  } else {
+    stage_epilogue<R>(a, c.block, off, b.S, k);
+  }
 }
 
 

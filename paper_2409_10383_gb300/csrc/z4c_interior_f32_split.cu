@@ -9,12 +9,14 @@ namespace z4c {
 
 // Schedule 4, second kernel: the RK stage update and the FP64 enforcement of
 // the FP32 RHS stored by interior_pre_kernel<..., SPLIT = true> (same tile
-// list, same tile order).  Few registers, so many warps hide the latency of
-// the FP64 state loads.
+// list, same tile order).  Every FP64 operand of the stage (u0 and / or the
+// accumulator, 22 values each) and the 22 k values are loaded first, all at
+// once, into registers (126 per thread, 4 CTAs per SM): one round trip to
+// HBM per cell instead of several.
 // The tile's shape s (bits 28..29 of Tile::block; 0 = 16 x 8) sets which
 // cell of the (TX << s) x (TY >> s) tile thread tid = y TX + x updates: the
 // one the RHS kernel stored at index tid of the tile's k record.
-__global__ void __launch_bounds__(TX * TY, 8) split_epilogue_kernel(StageArgs a, const Tile *__restrict__ tiles) {
+__global__ void __launch_bounds__(TX * TY, 4) split_epilogue_kernel(StageArgs a, const Tile *__restrict__ tiles) {
   const Tile t = tiles[blockIdx.x];
   const int shape = t.block >> TILE_SHAPE_SHIFT, blk = t.block & TILE_BLOCK_MASK;
   const DevBlock &b = a.blocks[blk];
@@ -27,7 +29,9 @@ __global__ void __launch_bounds__(TX * TY, 8) split_epilogue_kernel(StageArgs a,
   float k[NF];
 #pragma unroll
   for (int f = 0; f < NF; ++f) k[f] = kt[f * (TX * TY)];
-  stage_epilogue<float>(a, blk, b.off + cidx, b.S, k);
+  StageOperands op;
+  op.load(a, b.off + cidx, b.S);
+  stage_epilogue_preloaded<float>(a, blk, b.off + cidx, b.S, k, op);
 }
 
 // The same stage update, persistent and fed by bulk asynchronous copies.

@@ -1203,6 +1203,31 @@ __device__ __forceinline__ void stage_epilogue(const StageArgs &a, int32_t block
   stage_epilogue_from<R>(a, block, off, S, k, GlobalField{a.u0, off, S}, GlobalField{a.acc, off, S});
 }
 
+// The stage update with every u0 / accumulator value the stage reads loaded
+// first, all at once (44 independent FP64 loads in flight per thread instead
+// of a few at a time): for kernels with the registers to hold them.
+struct ArrayField {
+  const double *v;
+  __device__ __forceinline__ double operator()(int f) const { return v[f]; }
+};
+struct StageOperands {
+  double u0[NF], acc[NF];
+  __device__ __forceinline__ void load(const StageArgs &a, int64_t off, int32_t S) {
+    const bool need_u0 = a.mode == MODE_S1 || a.mode == MODE_S23;
+    const bool need_acc = a.mode == MODE_S23 || a.mode == MODE_S4;
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      u0[f] = need_u0 ? a.u0[off + (int64_t)f * S] : 0.0;
+      acc[f] = need_acc ? a.acc[off + (int64_t)f * S] : 0.0;
+    }
+  }
+};
+template <class R>
+__device__ __forceinline__ void stage_epilogue_preloaded(const StageArgs &a, int32_t block, int64_t off, int32_t S,
+                                                         const R k[NF], const StageOperands &op) {
+  stage_epilogue_from<R>(a, block, off, S, k, ArrayField{op.u0}, ArrayField{op.acc});
+}
+
 // 1/max(chi, floor) in FP64 for the FP32 algebra: integer compare (both
 // operands positive or chi negative, so the bit patterns order like the
 // values), FP32 reciprocal seed, one FP64 Newton step, rounded to FP32.
