@@ -12,6 +12,8 @@ namespace z4c {
 // ---------------------------------------------------------------------------
 // ghost fill: dst cell <- src cell for every field (one thread per copy)
 // ---------------------------------------------------------------------------
+// A ghost cell is never a source cell, so all 22 loads go first (in flight
+// together) and the stores after them.
 template <class T>
 __global__ void ghost_kernel(T *__restrict__ reg, const DevBlock *__restrict__ blocks,
                              const GhostCopy *__restrict__ list, int n) {
@@ -21,8 +23,11 @@ __global__ void ghost_kernel(T *__restrict__ reg, const DevBlock *__restrict__ b
   const int64_t dS = blocks[c.dst_block].S, sS = blocks[c.src_block].S;
   T *dst = reg + blocks[c.dst_block].off + c.dst_cidx;
   const T *src = reg + blocks[c.src_block].off + c.src_cidx;
+  T v[NF];
 #pragma unroll
-  for (int f = 0; f < NF; ++f) dst[f * dS] = src[f * sS];
+  for (int f = 0; f < NF; ++f) v[f] = src[f * sS];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) dst[f * dS] = v[f];
 }
 
 
