@@ -1123,18 +1123,21 @@ __device__ __forceinline__ void enforce(double v[NF]) {
   v[GYY] = g3 * s; v[GYZ] = g4 * s; v[GZZ] = g5 * s;
 }
 
-// RK4 stage update of one cell and enforcement, then the stores.  FP64 mode:
-// FP64 fused multiply-adds of the FP64 RHS.  FP32 mode: the increment c k of
-// the FP32 RHS is formed in FP32 and added to the FP64 state / accumulator
-// in FP64; the next stage also goes to the FP32 shadow (gt diagonal minus 1).
-// The stage state u0 and the accumulator are read through U0 / ACC:
-// GlobalField (from the registers, the default) or a staged copy.
+// Field f of a register at one cell (u0 or the accumulator), read where it
+// is used.
 struct GlobalField {
   const double *p;
   int64_t off;
   int32_t S;
   __device__ __forceinline__ double operator()(int f) const { return p[off + (int64_t)f * S]; }
 };
+
+// RK4 stage update of one cell and enforcement, then the stores.  FP64 mode:
+// FP64 fused multiply-adds of the FP64 RHS.  FP32 mode: the increment c k of
+// the FP32 RHS is formed in FP32 and added to the FP64 state / accumulator
+// in FP64; the next stage also goes to the FP32 shadow (gt diagonal minus 1).
+// u0f / accf give field f of u0 and of the accumulator: GlobalField (read
+// where used), ArrayField (loaded beforehand, below) or a staged copy.
 template <class R, class U0F, class ACCF>
 __device__ __forceinline__ void stage_epilogue_from(const StageArgs &a, int32_t block, int64_t off, int32_t S,
                                                     const R k[NF], const U0F &u0f, const ACCF &accf) {
