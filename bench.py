@@ -62,8 +62,9 @@ FP32_OPS_PER_CELL_STAGE = {6: dict(fadd=1085, ffma=1274, fmul=507)}
 FP32_F64_RESIDUE_PER_CELL_STAGE = {6: dict(dadd=47, dfma=22, dmul=25)}
 FP32_DRAM_BYTES_PER_CELL = {6: (62186496 + 4548096 + 75075840 + 28735744) / 262144}
 # the same for schedule 6 (interior_pair_kernel<6,72,2> on 64 x 2 tiles +
-# split_epilogue_kernel on the same tiles), one 64^3 block, stage 1
-FP32_DRAM_BYTES_PER_CELL_PAIR = {6: (62200576 + 6005760 + 75092736 + 28943360) / 262144}
+# split_epilogue_kernel on the same tiles, its FP64 operands loaded at once),
+# one 64^3 block, RK stage 2 (which reads both u0 and the accumulator)
+FP32_DRAM_BYTES_PER_CELL_PAIR = {6: (62202624 + 5601280 + 126977536 + 29047552) / 262144}
 # algorithmic HBM bytes per zone-cycle (fused 3-register RK4, 22 FP64 fields;
 # the same for the FP32-RHS path, whose state stays FP64)
 ALG_BYTES_PER_ZONE_CYCLE = 352 * 8
@@ -325,7 +326,8 @@ def measure(z4c, torch, workload, prec, args, ws, local):
         roof.update({"frac": t[kind] / sec, "limiter": kind,
                      "traffic": traffic,
                      "traffic_note": "ncu dram bytes of the RHS and stage-update kernels, one 64^3 block, "
-                                     "scaled by cells",
+                                     "scaled by cells" + (" (RK stage 2: u0 and accumulator read)"
+                                                          if variant[0] == 6 else ""),
                      "kernel": (kname[variant[0]] + " + split_epilogue_kernel (FP32 RHS, FP64 state/RK/enforcement)")
                      if variant[0] in kname else
                      f"interior_pre_kernel<{order},true,{variant[1]}> (FP32 RHS, FP64 state/RK/enforcement)",
