@@ -437,6 +437,11 @@ struct Direct {
   __device__ __forceinline__ R mix(int f, int a, int b) const {
     return FD<ORD>::mix(s, f, st[a], st[b]) * sc.smix;
   }
+  // the same before the scale, and the scales (d2 = d2raw * d2scale, ...)
+  __device__ __forceinline__ R d2raw(int f, int d) const { return FD<ORD>::d2(s, f, st[d]); }
+  __device__ __forceinline__ R mixraw(int f, int a, int b) const { return FD<ORD>::mix(s, f, st[a], st[b]); }
+  __device__ __forceinline__ R d2scale() const { return sc.s2; }
+  __device__ __forceinline__ R mixscale() const { return sc.smix; }
 };
 
 // slot of a field in the stored-derivative arrays (-1: not stored);
@@ -465,6 +470,15 @@ struct Pre {
     if (a == 0 && b == 2) return FD<ORD>::d1(ds, q + NDS, st[0]) * sc.s1;   // D_x (D_z f)
     return FD<ORD>::d1(ds, q + NDS, st[1]) * sc.s1;                         // D_y (D_z f)
   }
+  __device__ __forceinline__ R d2raw(int f, int d) const { return FD<ORD>::d2(s, f, st[d]); }
+  __device__ __forceinline__ R mixraw(int f, int a, int b) const {
+    const int q = dslot(f);
+    if (a == 0 && b == 1) return FD<ORD>::d1(ds, q, st[0]);
+    if (a == 0 && b == 2) return FD<ORD>::d1(ds, q + NDS, st[0]);
+    return FD<ORD>::d1(ds, q + NDS, st[1]);
+  }
+  __device__ __forceinline__ R d2scale() const { return sc.s2; }
+  __device__ __forceinline__ R mixscale() const { return sc.s1; }
 };
 
 template <class R>
@@ -541,19 +555,37 @@ __device__ __forceinline__ void ricci(const DV &dv, R ichi,
                       gi[S6(2, m)] * Gu[k2][S6(2, i)];
   const R trDDchi = trsym(gi, DDchi);
   const R dchi2 = quad(gi, dchi, dchi);
+  // -1/2 gt^lm d_l d_m gt_ij.  Scalar types: the stencils' scales and the
+  // factors -1/2 (diagonal) and -1 (off-diagonal pairs) are folded into
+  // gt^lm once per cell, so the 36 second derivatives of gt are taken
+  // unscaled (42 fewer multiplies per cell).  Cell pairs keep the scaled
+  // form: the six folded weights would cost them registers they lack.
+  constexpr bool fold = !is_pair<R>::value;
+  R gs[6];
+  if constexpr (fold) {
+    const R cd = R(-0.5) * dv.d2scale(), cm = -dv.mixscale();
+    gs[0] = cd * gi[0]; gs[1] = cm * gi[1]; gs[2] = cm * gi[2];
+    gs[3] = cd * gi[3]; gs[4] = cm * gi[4]; gs[5] = cd * gi[5];
+  }
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int j = i; j < 3; ++j) {
       const int q = S6(i, j);
-      R dd[6];
-      dd[0] = dv.d2(GXX + q, 0);
-      dd[3] = dv.d2(GXX + q, 1);
-      dd[5] = dv.d2(GXX + q, 2);
-      dd[1] = dv.mix(GXX + q, 0, 1);
-      dd[2] = dv.mix(GXX + q, 0, 2);
-      dd[4] = dv.mix(GXX + q, 1, 2);
-      R r = R(-0.5) * trsym(gi, dd);
+      R r;
+      if constexpr (fold) {
+        r = gs[0] * dv.d2raw(GXX + q, 0) + gs[3] * dv.d2raw(GXX + q, 1) + gs[5] * dv.d2raw(GXX + q, 2);
+        r += gs[1] * dv.mixraw(GXX + q, 0, 1) + gs[2] * dv.mixraw(GXX + q, 0, 2) + gs[4] * dv.mixraw(GXX + q, 1, 2);
+      } else {
+        R dd[6];
+        dd[0] = dv.d2(GXX + q, 0);
+        dd[3] = dv.d2(GXX + q, 1);
+        dd[5] = dv.d2(GXX + q, 2);
+        dd[1] = dv.mix(GXX + q, 0, 1);
+        dd[2] = dv.mix(GXX + q, 0, 2);
+        dd[4] = dv.mix(GXX + q, 1, 2);
+        r = R(-0.5) * trsym(gi, dd);
+      }
       R t = R(0);
 #pragma unroll
       for (int k2 = 0; k2 < 3; ++k2) t += g[S6(k2, i)] * dGam[j][k2] + g[S6(k2, j)] * dGam[i][k2];

@@ -79,6 +79,11 @@ struct StagedDV {
     return ds[(SL_MIX + 3 * dslot(f) + m) * STAGE_NT + tid];
   }
   __device__ __forceinline__ float ko(int f) const { return ds[(SL_KO + f) * STAGE_NT + tid]; }
+  // the staged values are already scaled
+  __device__ __forceinline__ float d2raw(int f, int d) const { return d2(f, d); }
+  __device__ __forceinline__ float mixraw(int f, int a, int b) const { return mix(f, a, b); }
+  __device__ __forceinline__ float d2scale() const { return 1.f; }
+  __device__ __forceinline__ float mixscale() const { return 1.f; }
 };
 
 // centred first / second differences on values p[m-1] = f(+m), q[m-1] = f(-m)
