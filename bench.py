@@ -365,7 +365,9 @@ def measure(z4c, torch, workload, prec, args, ws, local):
     barrier()
     e2e = {"value": cells * e2e_steps * ws / (t1 - t0), "unit": UNIT, "h2d_bytes_per_step": nbytes,
            "d2h_bytes_per_step": nbytes}
-    roof["variant"] = {"schedule": variant[0], "occupancy": variant[1]}
+    tx, ty, cpt = g.z4c_tile_shape(0)
+    roof["variant"] = {"schedule": variant[0], "occupancy": variant[1],
+                       "tile": f"{tx}x{ty}", "cells_per_thread": cpt}
     # the Weyl scalar Psi4 on the grid (Sec. 3.3 diagnostic, FP64): one
     # synchronous call = ghost fill + Psi4 at every interior cell
     psi4 = None

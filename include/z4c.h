@@ -388,6 +388,13 @@ int z4c_constraints_static(const void *u_device, const int32_t n[3], int ghosts,
                            const double lo[3], double h, double chi_floor, double r_mask,
                            double *norms, void *cuda_stream);
 
+/* The interior tile of block `block` under the context's current kernel
+ * variant (after z4c_autotune: the one it kept): tx x ty cells of one
+ * z-plane per CTA, and the cells each thread computes (2 for the FP32-RHS
+ * schedule 6 on qualifying blocks, else 1).  Z4C_ERR_BAD_ARG for a bad
+ * block index or a NULL output.  Makes no CUDA call. */
+int z4c_tile_shape(const z4c_ctx *ctx, int block, int *tx, int *ty, int *cells_per_thread);
+
 /* Number of kernel launches one RK4 step enqueues. */
 int z4c_launches_per_step(const z4c_ctx *ctx);
 

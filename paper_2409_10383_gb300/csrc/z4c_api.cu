@@ -728,6 +728,22 @@ int z4c_peak_convert(int mode, void *cuda_stream, double *conv_per_s) {
   return Z4C_OK;
 }
 
+int z4c_tile_shape(const z4c_ctx *ctx, int block, int *tx, int *ty, int *cells_per_thread) {
+  if (!ctx || !tx || !ty || !cells_per_thread || block < 0 || block >= (int)ctx->dblocks.size())
+    return Z4C_ERR_BAD_ARG;
+  const bool f32 = ctx->dblocks[block].f32 != 0;
+  const int sc = ctx->sched[f32 ? 1 : 0];
+  int shape = 0, pair = 0;
+  if (f32 && sc >= 5 && block < (int)ctx->wide_shape.size()) {
+    shape = ctx->wide_shape[block];
+    pair = sc == 6 && shape > 0 ? ctx->wide_pair[block] : 0;
+  }
+  *tx = TX << shape;
+  *ty = TY >> shape;
+  *cells_per_thread = pair ? 2 : 1;
+  return Z4C_OK;
+}
+
 int z4c_launches_per_step(const z4c_ctx *ctx) {
   if (!ctx) return Z4C_ERR_BAD_ARG;
   int per_stage = 0;

@@ -633,6 +633,8 @@ int z4c_create_batch(const z4c_instance *instances, int ninstances, const z4c_bl
                               D.off % 2 == 0 && D.S % 2 == 0;
     }
     if (!G.f32) continue;
+    ctx->wide_shape.resize(ctx->dblocks.size(), 0);
+    ctx->wide_pair.resize(ctx->dblocks.size(), 0);
     // schedule-5/6 list: wide tiles (a warp along one row) where n_x is a
     // multiple of 64 (shape 2) or 32 (shape 1) and a kernel is built
     for (const Group::ExtRange &r : G.eranges) {
@@ -648,6 +650,8 @@ int z4c_create_batch(const z4c_instance *instances, int ninstances, const z4c_bl
           const int b = G.tiles[q].block;
           if (b == last) continue;  // a block's tiles are contiguous in the sorted list
           last = b;
+          ctx->wide_shape[b] = (int8_t)shape;
+          ctx->wide_pair[b] = (int8_t)(r.pair ? 1 : 0);
           const DevBlock &D = ctx->dblocks[b];
           for (int k = 0; k < D.n[2]; ++k)
             for (int j0 = 0; j0 < D.n[1]; j0 += tys)

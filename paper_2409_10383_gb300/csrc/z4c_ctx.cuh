@@ -67,6 +67,8 @@ struct z4c_ctx {
   std::vector<z4c::CellRef> somm[2];    // Sommerfeld cells, per precision (0 FP64, 1 FP32)
   std::vector<z4c::GhostCopy> gcopy[2];  // same-level ghost copies, per precision
   std::vector<z4c::Tile> ctiles;         // every interior tile (constraints), in block order
+  std::vector<int8_t> wide_shape;        // per block: tile shape on the schedule-5/6 list (0: 16 x 8)
+  std::vector<int8_t> wide_pair;         // per block: 1 if schedule 6 runs it two cells per thread
   std::vector<int32_t> cfirst;           // first ctile of each block, and the total
   // mesh refinement transfer (FP64 instances with more than one level)
   std::vector<z4c::RestrictRef> rghost;  // coarse ghost cells <- restriction of a finer block

@@ -28,7 +28,7 @@ EXPORTS = ("z4c_create", "z4c_create_batch", "z4c_set_initial_data_instance", "z
            "z4c_sync", "z4c_profile_steps", "z4c_set_variant", "z4c_autotune", "z4c_peak_fma", "z4c_constraints_static",
            "z4c_launches_per_step", "z4c_last_error", "z4c_destroy", "z4c_block_indicators",
            "z4c_track_punctures", "z4c_psi4", "z4c_peak_convert", "z4c_test_wait_timeout",
-           "z4c_set_epilogue")
+           "z4c_set_epilogue", "z4c_tile_shape")
 Z4C_MAX_PUNCTURES = 64
 
 
@@ -89,6 +89,7 @@ def lib():
             "z4c_sync": (I, [P]),
             "z4c_test_wait_timeout": (I, [P, I]),
             "z4c_set_epilogue": (I, [P, I]),
+            "z4c_tile_shape": (I, [P, I, P, P, P]),
             "z4c_profile_steps": (I, [P, D, I, P]),
             "z4c_set_variant": (I, [P, I, I]),
             "z4c_autotune": (I, [P, I, P, P]),
@@ -353,6 +354,14 @@ class Z4c:
 
     def z4c_set_variant(self, schedule, occupancy=1):
         _check(lib().z4c_set_variant(self.ctx, int(schedule), int(occupancy)), self.ctx, "z4c_set_variant")
+
+    def z4c_tile_shape(self, block=0):
+        """(tx, ty, cells per thread) of the block's interior tiles under the
+        current kernel variant."""
+        tx, ty, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().z4c_tile_shape(self.ctx, int(block), ctypes.byref(tx), ctypes.byref(ty), ctypes.byref(c)),
+               self.ctx, "z4c_tile_shape")
+        return tx.value, ty.value, c.value
 
     def z4c_set_epilogue(self, kind):
         """FP32-RHS split schedules: 1 bulk-copy stage-update kernel, 0 plain."""

@@ -135,3 +135,33 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
         z4c.lib()
     with pytest.raises(RuntimeError, match="no fallback"):
         z4c.z4c_create(_mesh(), [_block()], 3, 4, _params())
+
+
+def test_tile_shape_reports_the_variant(L):
+    """z4c_tile_shape (no CUDA call): FP32-RHS blocks of 64^3 take 64 x 2
+    tiles under schedules 5 and 6 (two cells per thread under 6), 32^3
+    blocks 32 x 4, 16^3 blocks stay on 16 x 8; schedule 4 and FP64 blocks
+    use 16 x 8 with one cell per thread."""
+    def ctx(n, prec):
+        ok, c = z4c.z4c_create(_mesh(), [_block(n=n, h=1.0 / n)], 4, 6, _params(prec))
+        assert ok == 0
+        return c
+
+    def shape(c):
+        tx, ty, k = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        assert L.z4c_tile_shape(c, 0, ctypes.byref(tx), ctypes.byref(ty), ctypes.byref(k)) == 0
+        return tx.value, ty.value, k.value
+
+    for n, wide in ((64, (64, 2)), (32, (32, 4)), (16, (16, 8))):
+        c = ctx(n, 32)
+        assert shape(c) == (16, 8, 1)  # default schedule 4
+        assert L.z4c_set_variant(c, 5, 4) == 0
+        assert shape(c) == wide + (1,)
+        assert L.z4c_set_variant(c, 6, 4) == 0
+        assert shape(c) == wide + (2 if wide != (16, 8) else 1,)
+        tx = ctypes.c_int()
+        assert L.z4c_tile_shape(c, 1, ctypes.byref(tx), ctypes.byref(tx), ctypes.byref(tx)) == z4c.Z4C_ERR_BAD_ARG
+        L.z4c_destroy(c)
+    c = ctx(64, 64)
+    assert shape(c) == (16, 8, 1)
+    L.z4c_destroy(c)
