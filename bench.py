@@ -60,11 +60,12 @@ FP64_DRAM_BYTES_PER_CELL = {6: (121649920 + 97539328) / 262144, 2: (114212608 + 
 # interior cell per stage, from the same kind of capture
 FP32_OPS_PER_CELL_STAGE = {6: dict(fadd=1085, ffma=1274, fmul=507)}
 FP32_F64_RESIDUE_PER_CELL_STAGE = {6: dict(dadd=47, dfma=22, dmul=25)}
-FP32_DRAM_BYTES_PER_CELL = {6: (62186496 + 4548096 + 75075840 + 28735744) / 262144}
-# the same for schedule 6 (interior_pair_kernel<6,72,2> on 64 x 2 tiles +
-# split_epilogue_kernel on the same tiles, its FP64 operands loaded at once),
-# one 64^3 block, RK stage 2 (which reads both u0 and the accumulator)
-FP32_DRAM_BYTES_PER_CELL_PAIR = {6: (62202624 + 5601280 + 126977536 + 29047552) / 262144}
+# keyed by (order, schedule, tile): the RHS kernel as it stands (with its L2
+# prefetch of the rows 4 planes ahead) + split_epilogue_kernel on the same
+# tiles, one 64^3 block, RK stage 2 (which reads both u0 and the
+# accumulator).  Schedules 4 and 6 changed after their last capture, so
+# they report no traffic.
+FP32_DRAM_BYTES_PER_CELL = {(6, 5, "64x2"): (65959680 + 4796672 + 126971904 + 28759040) / 262144}
 # algorithmic HBM bytes per zone-cycle (fused 3-register RK4, 22 FP64 fields;
 # the same for the FP32-RHS path, whose state stays FP64)
 ALG_BYTES_PER_ZONE_CYCLE = 352 * 8
@@ -318,16 +319,15 @@ def measure(z4c, torch, workload, prec, args, ws, local):
         ext = int(workload["n"][0][0]) + 2 * int(workload["ghosts"])
         n0 = int(workload["n"][0][0])
         shape = "64x2" if n0 % 64 == 0 else "32x4" if n0 % 32 == 0 else "16x8"
-        traffic = (FP32_DRAM_BYTES_PER_CELL[order] * cells if variant[0] == 4 else
-                   FP32_DRAM_BYTES_PER_CELL_PAIR[order] * cells if variant[0] == 6 and shape == "64x2" else None)
+        per_cell = FP32_DRAM_BYTES_PER_CELL.get((order, variant[0], shape if variant[0] >= 5 else "16x8"))
+        traffic = per_cell * cells if per_cell is not None else None
         kname = {4: f"interior_pre_kernel<{order},true,4,split,{ext}> (16x8 tiles)",
                  5: f"interior_pre_kernel<{order},true,4,split,{ext},wide> ({shape} tiles)",
                  6: f"interior_pair_kernel<{order},{ext},wide> (two cells per thread, f32x2, {shape} tiles)"}
         roof.update({"frac": t[kind] / sec, "limiter": kind,
                      "traffic": traffic,
                      "traffic_note": "ncu dram bytes of the RHS and stage-update kernels, one 64^3 block, "
-                                     "scaled by cells" + (" (RK stage 2: u0 and accumulator read)"
-                                                          if variant[0] == 6 else ""),
+                                     "scaled by cells (RK stage 2: u0 and accumulator read)",
                      "kernel": (kname[variant[0]] + " + split_epilogue_kernel (FP32 RHS, FP64 state/RK/enforcement)")
                      if variant[0] in kname else
                      f"interior_pre_kernel<{order},true,{variant[1]}> (FP32 RHS, FP64 state/RK/enforcement)",

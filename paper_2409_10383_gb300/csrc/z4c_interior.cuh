@@ -7,6 +7,7 @@
 #pragma once
 
 #include "z4c_rhs.cuh"
+#include "z4c_tma.cuh"
 
 namespace z4c {
 
@@ -58,6 +59,14 @@ __global__ void __launch_bounds__(TX * TY) dydz_kernel(StageArgs a, const Tile *
   const Tile t = tiles[blockIdx.x];
   const DevBlock &b = a.blocks[t.block];
   const int i = t.i0 + threadIdx.x, j = t.j0 + threadIdx.y, kk = t.k0;
+  if constexpr (F32) {
+    // into L2: the whole storage rows of this tile's rows of the eleven
+    // fields PF_PRE planes ahead, from the first tile of the row band
+    const int tid = threadIdx.y * TX + threadIdx.x;
+    if (t.i0 == -W && tid < NF && dslot(tid) >= 0)
+      prefetch_rows<float>(a.x32, tid, b.S, kk + b.g + PF_PRE, t.j0 + b.g, t.j0 + b.g + TY, b.e[0], b.e[1], b.e[2],
+                           b.off);
+  }
   const bool in_x = i >= 0 && i < b.n[0], in_y = j >= 0 && j < b.n[1];
   const bool wide_x = i >= -W && i < b.n[0] + W, wide_y = j >= -W && j < b.n[1] + W;
   const bool need_dy = in_y && wide_x;
@@ -110,10 +119,19 @@ __global__ void __launch_bounds__(TX * TY, OCC) interior_pre_kernel(StageArgs a,
   const int tid0 = threadIdx.y * TX + threadIdx.x;
   const int i = t.i0 + (SHAPE ? tid0 % TXS : (int)threadIdx.x), j = t.j0 + (SHAPE ? tid0 / TXS : (int)threadIdx.y);
   const int kk = t.k0;
-  if (i >= b.n[0] || j >= b.n[1]) return;
-  const int g = b.g;
   const int e0 = EXT > 0 ? EXT : b.e[0], e1 = EXT > 0 ? EXT : b.e[1];
   const int32_t S = EXT > 0 ? EXT * EXT * EXT : b.S;
+  if constexpr (F32 && SPLIT) {
+    // into L2: the shadow fields and stored derivatives of this tile's rows
+    // PF_RHS planes ahead (with the ghost rows at the y edges)
+    constexpr int ROWS = TY >> SHAPE;
+    if (tid0 < 2 * NF)
+      prefetch_rows<float>(tid0 < NF ? a.x32 : reinterpret_cast<const float *>(a.dstore), tid0 % NF, S,
+                           kk + b.g + PF_RHS, t.j0 == 0 ? 0 : t.j0 + b.g,
+                           t.j0 + ROWS >= b.n[1] ? e1 : t.j0 + b.g + ROWS, e0, e1, EXT > 0 ? EXT : b.e[2], b.off);
+  }
+  if (i >= b.n[0] || j >= b.n[1]) return;
+  const int g = b.g;
   const int32_t cidx = ((kk + g) * e1 + (j + g)) * e0 + (i + g);
   const int st[3] = {1, e0, e0 * e1};
   const int64_t off = b.off + cidx;
@@ -166,10 +184,19 @@ __global__ void __launch_bounds__(TX * TY / 2, 4) interior_pair_kernel(StageArgs
   const int blk = t.block & TILE_BLOCK_MASK;
   const DevBlock &b = a.blocks[blk];
   const int i = t.i0 + 2 * threadIdx.x, j = t.j0 + threadIdx.y, kk = t.k0;
-  if (i >= b.n[0] || j >= b.n[1]) return;
-  const int g = b.g;
   constexpr int e0 = EXT, e1 = EXT;
   constexpr int32_t S = EXT * EXT * EXT;
+  {
+    // into L2: the shadow fields and stored derivatives of this tile's rows
+    // PF_RHS planes ahead (with the ghost rows at the y edges)
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    if (tid < 2 * NF)
+      prefetch_rows<float>(tid < NF ? a.x32 : reinterpret_cast<const float *>(a.dstore), tid % NF, S,
+                           kk + b.g + PF_RHS, t.j0 == 0 ? 0 : t.j0 + b.g,
+                           t.j0 + (TY >> SHAPE) >= b.n[1] ? e1 : t.j0 + b.g + (TY >> SHAPE), e0, e1, EXT, b.off);
+  }
+  if (i >= b.n[0] || j >= b.n[1]) return;
+  const int g = b.g;
   const int32_t cidx = ((kk + g) * e1 + (j + g)) * e0 + (i + g);
   const int st[3] = {1, e0, e0 * e1};
   const int64_t off = b.off + cidx;

@@ -79,4 +79,36 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, uint32
 
 #endif  // Z4C_TMA_PROVIDED
 
+// Ask the TMA unit to bring `bytes` (a multiple of 16) from a 16-byte
+// aligned global address into L2 ahead of use.  No completion to wait for,
+// no registers held: the loads that follow simply find the lines in L2.
+__device__ __forceinline__ void l2_prefetch(const void *src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
+}
+
+// L2 prefetch of storage rows [r0, r1) of storage plane `plane` of array f
+// (S elements per array) of a block whose field 0 starts at base + boff:
+// one bulk request for the whole run of rows, ghosts along x included.
+// Skipped past the last storage plane (e2) or where the run is not 16-byte
+// aligned (block offset, row length or array size not a multiple of 16
+// bytes).
+template <class T>
+__device__ __forceinline__ void prefetch_rows(const T *base, int f, int32_t S, int plane, int r0, int r1, int e0,
+                                              int e1, int e2, int64_t boff) {
+  constexpr int A = 16 / sizeof(T);
+  if (plane >= e2 || r1 <= r0 || (boff % A) != 0 || (e0 % A) != 0 || (S % A) != 0) return;
+  r0 = r0 < 0 ? 0 : r0;
+  r1 = r1 > e1 ? e1 : r1;
+  const int64_t first = boff + (int64_t)f * S + ((int64_t)plane * e1 + r0) * e0;
+  l2_prefetch(base + first, (uint32_t)((r1 - r0) * e0 * (int)sizeof(T)));
+}
+
+// How many interior planes ahead of its own tile the FP32 stencil kernels
+// prefetch: the split RHS kernels (shadow fields and stored derivatives)
+// and the y/z pre-pass (shadow fields).  Tiles run plane after plane, so
+// plane k + 4 (the stencil's reach) is first touched in HBM by the tiles at
+// plane k; the bulk request brings its rows whole instead of line by line
+// as the stencil loads reach them.
+constexpr int PF_RHS = 4, PF_PRE = 4;
+
 }  // namespace z4c
