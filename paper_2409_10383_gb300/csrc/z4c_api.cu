@@ -166,7 +166,9 @@ int launch_fused_group(z4c_ctx *ctx, int g, const StageArgs &a) {
 int launch_sommerfeld_p(z4c_ctx *ctx, int p, const StageArgs &a, cudaStream_t st) {
   const int n = (int)ctx->somm[p].size();
   if (!n) return Z4C_OK;
-  CK(launch_sommerfeld(p == 1, a, ctx->d_somm(p), n, st));
+  StageArgs as = a;
+  as.kbuf = ctx->d_kbuf_somm();
+  CK(launch_sommerfeld(p == 1, as, ctx->d_somm(p), n, st));
   return Z4C_OK;
 }
 
@@ -747,7 +749,8 @@ int z4c_tile_shape(const z4c_ctx *ctx, int block, int *tx, int *ty, int *cells_p
 int z4c_launches_per_step(const z4c_ctx *ctx) {
   if (!ctx) return Z4C_ERR_BAD_ARG;
   int per_stage = 0;
-  for (int p = 0; p < 2; ++p) per_stage += (ctx->gcopy[p].empty() ? 0 : 1) + (ctx->somm[p].empty() ? 0 : 1);
+  // FP32-RHS Sommerfeld cells take two kernels (RHS, then the stage update)
+  for (int p = 0; p < 2; ++p) per_stage += (ctx->gcopy[p].empty() ? 0 : 1) + (ctx->somm[p].empty() ? 0 : p + 1);
   if (ctx->rb_mode)
     per_stage += 2;  // block restriction + scatter
   else

@@ -20,13 +20,19 @@ cudaError_t launch_ghosts_f32(float *reg, const DevBlock *blocks, const GhostCop
 cudaError_t launch_sommerfeld(bool f32, const StageArgs &a, const CellRef *cells, int ncells,
                               cudaStream_t st) {
   if (ncells <= 0) return cudaSuccess;
-  const int nt = 128;
-  if (f32)
-    sommerfeld_kernel<true><<<(ncells + nt - 1) / nt, nt, 0, st>>>(a, cells, ncells);
-  else
-    sommerfeld_kernel<false><<<(ncells + nt - 1) / nt, nt, 0, st>>>(a, cells, ncells);
+  const int nb = (ncells + SOMM_CTA - 1) / SOMM_CTA;
+  if (f32) {
+    sommerfeld_rhs_f32_kernel<<<nb, SOMM_CTA, 0, st>>>(a, cells, ncells);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    sommerfeld_update_f32_kernel<<<nb, SOMM_CTA, 0, st>>>(a, cells, ncells);
+  } else {
+    sommerfeld_kernel<<<nb, SOMM_CTA, 0, st>>>(a, cells, ncells);
+  }
   return cudaGetLastError();
 }
+
+size_t somm_kbuf_floats(int ncells) { return (size_t)NF * SOMM_CTA * (size_t)((ncells + SOMM_CTA - 1) / SOMM_CTA); }
 
 cudaError_t launch_initial_data(double *u0, const DevBlock *blocks, int nblocks, int max_S, int instance,
                                 int kind, const double *par, int npar, cudaStream_t st) {

@@ -40,31 +40,21 @@ __device__ __forceinline__ double uinf_of(int f) {
   return (f == CHI || f == GXX || f == GYY || f == GZZ || f == ALPHA) ? 1.0 : 0.0;
 }
 
-// SOMM_PRELOAD: the stage's FP64 operands (u0 and / or the accumulator) are
-// loaded after the RHS, all at once, before the update (registers to hold
-// them at SOMM_OCC CTAs per SM).
-template <bool F32>
-constexpr bool SOMM_PRELOAD = F32;
-template <bool F32>
-constexpr int SOMM_OCC = F32 ? 3 : 4;
-template <bool F32>
-__global__ void __launch_bounds__(128, SOMM_OCC<F32>) sommerfeld_kernel(StageArgs a, const CellRef *__restrict__ cells, int n) {
-  using R = typename std::conditional<F32, float, double>::type;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n) return;
-  const CellRef c = cells[t];
-  const DevBlock &b = a.blocks[c.block];
+// The Sommerfeld RHS of one cell into k.
+//   du/dt = -(x^d d_d u + u - u_inf) / r.  The one-sided (w0, w1, w2) =
+//   (-+3, +-4, -+1) at offsets (0, +-1, +-2) and centred (0, 1, -1) at
+//   (0, +1, -1) differences sum to zero, so 2h d_d u = w1 (u[o1] - u) +
+//   w2 (u[o2] - u).  Per cell: a1,2_d = -w1,2_d x^d / (2h r); per field:
+//   k = -(u - u_inf) / r + sum_d a1_d (u[o1_d] - u) + a2_d (u[o2_d] - u),
+//   which is exactly zero on a constant state equal to u_inf.
+// Coefficients in the stencils' precision R: the FP32 variant forms them on
+// the FP32 pipe (its FP64 pipe is the stage update's), FP64 in FP64.
+template <class R>
+__device__ __forceinline__ void somm_rhs(const StageArgs &a, const CellRef &c, const DevBlock &b, R k[NF]) {
+  constexpr bool F32 = sizeof(R) == 4;
   const int st[3] = {1, b.e[0], b.e[0] * b.e[1]};
   const int idx[3] = {c.i, c.j, c.k};
   const int64_t off = b.off + c.cidx;
-  // du/dt = -(x^d d_d u + u - u_inf) / r.  The one-sided (w0, w1, w2) =
-  // (-+3, +-4, -+1) at offsets (0, +-1, +-2) and centred (0, 1, -1) at
-  // (0, +1, -1) differences sum to zero, so 2h d_d u = w1 (u[o1] - u) +
-  // w2 (u[o2] - u).  Per cell: a1,2_d = -w1,2_d x^d / (2h r); per field:
-  // k = -(u - u_inf) / r + sum_d a1_d (u[o1_d] - u) + a2_d (u[o2_d] - u),
-  // which is exactly zero on a constant state equal to u_inf.
-  // Coefficients in the stencils' precision R: the FP32 variant forms them
-  // on the FP32 pipe (its FP64 pipe is the stage update's), FP64 in FP64.
   R xd[3], r2 = R(0);
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
@@ -98,7 +88,6 @@ __global__ void __launch_bounds__(128, SOMM_OCC<F32>) sommerfeld_kernel(StageArg
     o2[d] = s2 * st[d];
   }
   const R mir = -ir;
-  R k[NF];
 #pragma unroll
   for (int f = 0; f < NF; ++f) {
     // the FP32 shadow stores the gt diagonal minus one, i.e. u - u_inf there
@@ -117,13 +106,53 @@ __global__ void __launch_bounds__(128, SOMM_OCC<F32>) sommerfeld_kernel(StageArg
     for (int d = 0; d < 3; ++d) v = fma(a1[d], p[o1[d]] - u, fma(a2[d], p[o2[d]] - u, v));
     k[f] = v;
   }
-  if constexpr (SOMM_PRELOAD<F32>) {
-    StageOperands op;
-    op.load(a, off, b.S);
-    stage_epilogue_preloaded<R>(a, c.block, off, b.S, k, op);
-  } else {
-    stage_epilogue<R>(a, c.block, off, b.S, k);
-  }
+}
+
+// FP64 Sommerfeld cells: the RHS and the stage update in one kernel, one
+// thread per cell.
+__global__ void __launch_bounds__(128, 4) sommerfeld_kernel(StageArgs a, const CellRef *__restrict__ cells, int n) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const CellRef c = cells[t];
+  const DevBlock &b = a.blocks[c.block];
+  double k[NF];
+  somm_rhs<double>(a, c, b, k);
+  stage_epilogue<double>(a, c.block, b.off + c.cidx, b.S, k);
+}
+
+// FP32-RHS Sommerfeld cells, split like the interior cells.  First the FP32
+// RHS, one thread per cell at high occupancy (its work is the 7 loads per
+// field), into a k record per CTA of SOMM_CTA cells ([cta][field][lane] from
+// a.kbuf); then the FP64 stage update of the same cells with every FP64
+// operand loaded at once (u0 and / or the accumulator, 22 each).
+constexpr int SOMM_CTA = 128;
+
+__global__ void __launch_bounds__(SOMM_CTA, 8) sommerfeld_rhs_f32_kernel(StageArgs a,
+                                                                          const CellRef *__restrict__ cells, int n) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const CellRef c = cells[t];
+  float k[NF];
+  somm_rhs<float>(a, c, a.blocks[c.block], k);
+  float *kt = a.kbuf + (int64_t)blockIdx.x * NF * SOMM_CTA + threadIdx.x;
+#pragma unroll
+  for (int f = 0; f < NF; ++f) kt[f * SOMM_CTA] = k[f];
+}
+
+__global__ void __launch_bounds__(SOMM_CTA, 4) sommerfeld_update_f32_kernel(StageArgs a,
+                                                                             const CellRef *__restrict__ cells, int n) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const CellRef c = cells[t];
+  const DevBlock &b = a.blocks[c.block];
+  const int64_t off = b.off + c.cidx;
+  const float *kt = a.kbuf + (int64_t)blockIdx.x * NF * SOMM_CTA + threadIdx.x;
+  float k[NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) k[f] = kt[f * SOMM_CTA];
+  StageOperands op;
+  op.load(a, off, b.S);
+  stage_epilogue_preloaded<float>(a, c.block, off, b.S, k, op);
 }
 
 

@@ -743,6 +743,9 @@ int z4c_create_batch(const z4c_instance *instances, int ninstances, const z4c_bl
       if (G.f32) nt = std::max(nt, std::max(G.tiles.size(), G.ptiles.size()));
     ctx->o_kbuf = take(sizeof(float) * NF * TX * TY * nt);
   }
+  // the FP32-RHS Sommerfeld cells' k records (their own: the Sommerfeld
+  // kernels may run beside the interior ones)
+  ctx->o_kbuf_somm = take(sizeof(float) * somm_kbuf_floats((int)ctx->somm[1].size()));
   ctx->scratch_total = o;
   *out = ctx;
   return Z4C_OK;

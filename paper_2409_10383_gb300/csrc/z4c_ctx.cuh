@@ -96,7 +96,7 @@ struct z4c_ctx {
   // scratch layout (byte offsets)
   size_t o_blocks = 0, o_somm[2] = {0, 0}, o_gcopy[2] = {0, 0}, o_ctiles = 0, o_part = 0, o_res = 0,
          o_dt = 0, o_sh0 = 0, o_sh1 = 0, o_ds64 = 0, o_ds32 = 0, o_rghost = 0, o_rbuf = 0, o_cbcopy = 0,
-         o_prol = 0, o_pidx = 0, o_wtab = 0, o_pw = 0, o_cb = 0, o_status = 0, o_kbuf = 0, o_rblocks = 0,
+         o_prol = 0, o_pidx = 0, o_wtab = 0, o_pw = 0, o_cb = 0, o_status = 0, o_kbuf = 0, o_kbuf_somm = 0, o_rblocks = 0,
          o_rbcopy = 0, o_krow = 0, o_rb = 0, o_pbox = 0, o_pslots = 0,
          o_paxtab = 0, o_cfirst = 0, o_diag = 0, scratch_total = 0;
   // bound buffers
@@ -124,6 +124,7 @@ struct z4c_ctx {
   const z4c::Tile *d_rtiles(int g) const { return (const z4c::Tile *)(scratch + grp[g].o_rtiles); }
   int32_t *d_status() const { return (int32_t *)(scratch + o_status); }
   float *d_kbuf() const { return (float *)(scratch + o_kbuf); }
+  float *d_kbuf_somm() const { return (float *)(scratch + o_kbuf_somm); }
   bool has_staged() const { return !grp[3].stiles.empty(); }
   bool has_wide() const {
     for (const z4c::Group &G : grp)

@@ -234,8 +234,12 @@ cudaError_t launch_fused_f64(int order, const StageArgs &a, const Tile *tiles, i
                              cudaStream_t st);
 cudaError_t launch_fused_f32(int order, const StageArgs &a, const Tile *tiles, int ntiles, bool pre,
                              cudaStream_t st);
+// FP64 cells: one kernel (RHS + stage update).  FP32-RHS cells: the FP32
+// RHS into k records at a.kbuf (somm_kbuf_floats(ncells) floats), then the
+// FP64 stage update.
 cudaError_t launch_sommerfeld(bool f32, const StageArgs &a, const CellRef *cells, int ncells,
                               cudaStream_t st);
+size_t somm_kbuf_floats(int ncells);
 cudaError_t launch_ghosts_f64(double *reg, const DevBlock *blocks, const GhostCopy *list, int n,
                               cudaStream_t st);
 cudaError_t launch_ghosts_f32(float *reg, const DevBlock *blocks, const GhostCopy *list, int n,
