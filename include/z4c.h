@@ -283,6 +283,25 @@ int z4c_set_variant(z4c_ctx *ctx, int schedule, int occupancy);
  * Z4C_ERR_BAD_ARG for another kind.  Makes no CUDA call. */
 int z4c_set_epilogue(z4c_ctx *ctx, int kind);
 
+/* FP32-RHS blocks: which kernel computes the y/z first derivatives of the
+ * eleven fields with mixed second derivatives (the pre-pass of schedules 2
+ * to 6; paper Sec. 2, the second derivatives of the Z4c RHS).  kind 1 (the
+ * default): a kernel whose CTAs each walk a column of 16 planes, fed by TMA
+ * tensor copies of every plane's rows (with the y halo) into a shared-memory
+ * ring, for order-4 and order-6 groups whose blocks have rows, fields and
+ * block offsets that are multiples of 4 floats; the plane-tiled kernel for
+ * the others.  kind 0: the plane-tiled kernel everywhere.  Identical results
+ * either way (bit for bit).  Z4C_ERR_BAD_ARG for another kind.  Makes no
+ * CUDA call. */
+int z4c_set_prepass(z4c_ctx *ctx, int kind);
+
+/* How many blocks have their y/z pre-pass computed by the TMA-fed kernel
+ * under the current z4c_set_prepass kind (0 with kind 0, for FP64 blocks, or
+ * where the blocks do not qualify; a group whose tensor maps could not be
+ * encoded at z4c_bind drops out).  Z4C_ERR_BAD_ARG for a null context.
+ * Makes no CUDA call. */
+int z4c_prepass_tma_blocks(const z4c_ctx *ctx);
+
 /* Pick the fastest kernel variant for this context on this GPU: the
  * schedule (1 or 2; for FP32-RHS blocks also 4, and 3, 5 and 6 where
  * blocks qualify; see z4c_params)

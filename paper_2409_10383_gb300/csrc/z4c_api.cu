@@ -91,6 +91,16 @@ int launch_prepass_group(z4c_ctx *ctx, int g, const StageArgs &a) {
   const Group &G = ctx->grp[g];
   const int p = G.f32 ? 1 : 0;
   if (G.empty() || ctx->sched[p] < 2) return Z4C_OK;
+  if (G.f32 && G.tma_pre && ctx->pre_tma) {
+    // the TMA-fed kernel, with the tensor maps of the shadow being read
+    const int q = a.x32 == ctx->d_sh(0) ? 0 : a.x32 == ctx->d_sh(1) ? 1 : -1;
+    if (q >= 0) {
+      StageArgs at = a;
+      at.tmap32 = ctx->d_tmap(q);
+      CK(launch_prepass_tma_f32(G.order, at, ctx->at<Tile>(G.o_ztiles), (int)G.ztiles.size(), ctx->stream));
+      return Z4C_OK;
+    }
+  }
   const int nw = (int)G.wtiles.size();
   CK(G.f32 ? launch_prepass_f32(G.order, a, ctx->d_wtiles(g), nw, ctx->stream)
            : launch_prepass_f64(G.order, a, ctx->d_wtiles(g), nw, ctx->stream));
@@ -177,11 +187,16 @@ int launch_sommerfeld_p(z4c_ctx *ctx, int p, const StageArgs &a, cudaStream_t st
 // and writes the next state, accumulator and shadow at its own cells only;
 // the interior kernels write only interior cells and their own scratch.  So
 // with fork set (a captured step) the Sommerfeld cells run on the side
-// stream beside the interior kernels, joined before the stage ends; else
-// they follow on the context's stream.
+// stream beside the interior RHS and stage-update kernels, from the end of
+// the y/z pre-passes (which write only their derivative arrays) to the end
+// of the stage; else they follow on the context's stream.
 int launch_stage(z4c_ctx *ctx, const StageArgs &base, bool fork = false) {
   const bool any_somm = !ctx->somm[0].empty() || !ctx->somm[1].empty();
   fork = fork && any_somm && ctx->stream != nullptr && ctx->side != nullptr;
+  for (int g = 0; g < NGRP; ++g) {
+    const int r = launch_prepass_group(ctx, g, group_args(ctx, base, ctx->grp[g].f32));
+    if (r) return r;
+  }
   if (fork) {
     CK(cudaEventRecord(ctx->ev_fork, ctx->stream));
     CK(cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0));
@@ -192,10 +207,7 @@ int launch_stage(z4c_ctx *ctx, const StageArgs &base, bool fork = false) {
     CK(cudaEventRecord(ctx->ev_join, ctx->side));
   }
   for (int g = 0; g < NGRP; ++g) {
-    const StageArgs a = group_args(ctx, base, ctx->grp[g].f32);
-    int r = launch_prepass_group(ctx, g, a);
-    if (r) return r;
-    r = launch_fused_group(ctx, g, a);
+    const int r = launch_fused_group(ctx, g, group_args(ctx, base, ctx->grp[g].f32));
     if (r) return r;
   }
   if (fork) {
@@ -544,6 +556,30 @@ int z4c_set_epilogue(z4c_ctx *ctx, int kind) {
   ctx->epi_tma = kind == 1;
   ctx->drop_graph();
   return Z4C_OK;
+}
+
+int z4c_set_prepass(z4c_ctx *ctx, int kind) {
+  if (!ctx) return Z4C_ERR_BAD_ARG;
+  if (kind != 0 && kind != 1) return fail(ctx, Z4C_ERR_BAD_ARG, "pre-pass kind must be 0 or 1");
+  ctx->pre_tma = kind == 1;
+  ctx->drop_graph();
+  return Z4C_OK;
+}
+
+int z4c_prepass_tma_blocks(const z4c_ctx *ctx) {
+  if (!ctx) return Z4C_ERR_BAD_ARG;
+  if (!ctx->pre_tma) return 0;
+  int n = 0;
+  for (const Group &G : ctx->grp) {
+    if (!G.f32 || !G.tma_pre) continue;
+    int last = -1;
+    for (const Tile &t : G.ztiles) {
+      const int b = t.block & TILE_BLOCK_MASK;
+      if (b != last) ++n;  // a block's tiles are contiguous
+      last = b;
+    }
+  }
+  return n;
 }
 
 int z4c_autotune(z4c_ctx *ctx, int reps, int *schedule_out, int *occupancy_out) {

@@ -14,6 +14,9 @@
 #include <map>
 #include <unordered_map>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "z4c_ctx.cuh"
 
 using namespace z4c;
@@ -21,6 +24,36 @@ using namespace z4c;
 namespace {
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// cuTensorMapEncodeTiled, looked up once through the runtime (no link
+// against the driver library)
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      p = nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }();
+  return fn;
+}
+
+// The block's FP32 shadow as a 4-D tensor (x, y, z, field) with boxes of one
+// field's PRE_TMA_PX x (PRE_TMA_PY + order) rows of one plane; out-of-range
+// box parts read as zero.  False if the encoder is missing or refuses.
+bool encode_shadow_map(CUtensorMap *m, const float *base, const DevBlock &D, int order) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  const cuuint64_t dim[4] = {(cuuint64_t)D.e[0], (cuuint64_t)D.e[1], (cuuint64_t)D.e[2], (cuuint64_t)NF};
+  const cuuint64_t stride[3] = {(cuuint64_t)D.e[0] * 4, (cuuint64_t)D.e[0] * D.e[1] * 4, (cuuint64_t)D.S * 4};
+  const cuuint32_t box[4] = {(cuuint32_t)PRE_TMA_PX, (cuuint32_t)(PRE_TMA_PY + order), 1, 1};
+  const cuuint32_t es[4] = {1, 1, 1, 1};
+  return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, const_cast<float *>(base), dim, stride, box, es,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 long long iround(double v) { return (long long)std::llround(v); }
 long long ifloor(double v) { return (long long)std::floor(v); }
 
@@ -674,6 +707,35 @@ int z4c_create_batch(const z4c_instance *instances, int ninstances, const z4c_bl
     };
     for (Group::ExtRange &r : G.eranges) full_of(G.tiles, r);
     for (Group::ExtRange &r : G.peranges) full_of(G.ptiles, r);
+    // the z-walking pre-pass fed by TMA: 16-byte aligned rows and fields in
+    // every block of the group; tiles whose storage x is a multiple of
+    // PRE_TMA_PX, covering the interior widened by W in x and y, each
+    // walking PRE_TMA_NZ planes (z chunks outermost)
+    if (prepass_tma_built(G.order)) {
+      const int W = G.order / 2;
+      std::vector<int> gb;
+      for (const Tile &t : G.tiles)
+        if (gb.empty() || gb.back() != t.block) gb.push_back(t.block);
+      std::sort(gb.begin(), gb.end());
+      gb.erase(std::unique(gb.begin(), gb.end()), gb.end());
+      bool ok = !gb.empty();
+      for (int b : gb) {
+        const DevBlock &D = ctx->dblocks[b];
+        ok = ok && D.e[0] % 4 == 0 && D.S % 4 == 0 && D.off % 4 == 0 && D.g >= W;
+      }
+      if (ok) {
+        G.tma_pre = true;
+        for (int b : gb) {
+          const DevBlock &D = ctx->dblocks[b];
+          for (int k0 = 0; k0 < D.n[2]; k0 += PRE_TMA_NZ)
+            for (int j0 = -W; j0 < D.n[1] + W; j0 += PRE_TMA_PY)
+              for (int xs = 0; xs < D.g + D.n[0] + W; xs += PRE_TMA_PX)
+                if (xs + PRE_TMA_PX > D.g - W)
+                  for (int fg = 0; fg * PRE_TMA_NQ < NDS; ++fg)
+                    G.ztiles.push_back(Tile{b | (fg << TILE_SHAPE_SHIFT), xs - D.g, j0, k0});
+        }
+      }
+    }
   }
   // prolongation slots transposed to [125][entries] so that the threads of a
   // warp (neighbouring entries) read consecutive words
@@ -699,6 +761,7 @@ int z4c_create_batch(const z4c_instance *instances, int ninstances, const z4c_bl
     G.o_stiles = take(sizeof(Tile) * G.stiles.size());
     G.o_rtiles = take(sizeof(Tile) * G.rtiles.size());
     G.o_ptiles = take(sizeof(Tile) * G.ptiles.size());
+    G.o_ztiles = take(sizeof(Tile) * G.ztiles.size());
   }
   for (int p = 0; p < 2; ++p) {
     ctx->o_somm[p] = take(sizeof(CellRef) * ctx->somm[p].size());
@@ -746,6 +809,8 @@ int z4c_create_batch(const z4c_instance *instances, int ninstances, const z4c_bl
   // the FP32-RHS Sommerfeld cells' k records (their own: the Sommerfeld
   // kernels may run beside the interior ones)
   ctx->o_kbuf_somm = take(sizeof(float) * somm_kbuf_floats((int)ctx->somm[1].size()));
+  // tensor maps of the two FP32 shadows, per block (written at bind)
+  if (ctx->has[1]) ctx->o_tmap = take(2 * 128 * ctx->dblocks.size());
   ctx->scratch_total = o;
   *out = ctx;
   return Z4C_OK;
@@ -802,6 +867,28 @@ int z4c_bind(z4c_ctx *ctx, void *u0, void *stage_a, void *stage_b, void *acc, vo
     CK(up(G.o_stiles, G.stiles.data(), sizeof(Tile) * G.stiles.size()));
     CK(up(G.o_rtiles, G.rtiles.data(), sizeof(Tile) * G.rtiles.size()));
     CK(up(G.o_ptiles, G.ptiles.data(), sizeof(Tile) * G.ptiles.size()));
+    CK(up(G.o_ztiles, G.ztiles.data(), sizeof(Tile) * G.ztiles.size()));
+  }
+  // tensor maps for the TMA-fed pre-pass: per block of a qualifying group
+  // and shadow q, the 4-D tensor (x, y, z, field) of the block's FP32
+  // shadow with boxes of PRE_TMA_PX x (PRE_TMA_PY + order) x 1 x 1
+  if (ctx->has[1]) {
+    const size_t nb = ctx->dblocks.size();
+    std::vector<CUtensorMap> maps(2 * nb);
+    std::memset(maps.data(), 0, sizeof(CUtensorMap) * maps.size());
+    std::vector<char> done(nb, 0);
+    for (Group &G : ctx->grp) {
+      if (!G.tma_pre) continue;
+      for (const Tile &t : G.ztiles) {
+        const int blk = t.block & TILE_BLOCK_MASK;
+        if (done[blk]) continue;
+        done[blk] = 1;
+        const DevBlock &D = ctx->dblocks[blk];
+        for (int q = 0; q < 2; ++q)
+          if (!encode_shadow_map(&maps[q * nb + blk], ctx->d_sh(q) + D.off, D, G.order)) G.tma_pre = false;
+      }
+    }
+    CK(up(ctx->o_tmap, maps.data(), sizeof(CUtensorMap) * maps.size()));
   }
   for (int p = 0; p < 2; ++p) {
     CK(up(ctx->o_somm[p], ctx->somm[p].data(), sizeof(CellRef) * ctx->somm[p].size()));

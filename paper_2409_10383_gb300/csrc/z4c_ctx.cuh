@@ -48,7 +48,12 @@ struct Group {
   // range's 16 x 8 tiles (split RHS kernel) elsewhere
   std::vector<Tile> ptiles;
   std::vector<ExtRange> peranges;
-  size_t o_tiles = 0, o_wtiles = 0, o_stiles = 0, o_rtiles = 0, o_ptiles = 0;
+  // FP32 y/z pre-pass fed by TMA (every block of the group qualifies: row
+  // length, cells per field and block offset multiples of 4 floats): column
+  // tiles walking z; tma_pre is cleared if a tensor map cannot be encoded
+  std::vector<Tile> ztiles;
+  bool tma_pre = false;
+  size_t o_tiles = 0, o_wtiles = 0, o_stiles = 0, o_rtiles = 0, o_ptiles = 0, o_ztiles = 0;
   bool empty() const { return tiles.empty(); }
 };
 
@@ -96,7 +101,7 @@ struct z4c_ctx {
   // scratch layout (byte offsets)
   size_t o_blocks = 0, o_somm[2] = {0, 0}, o_gcopy[2] = {0, 0}, o_ctiles = 0, o_part = 0, o_res = 0,
          o_dt = 0, o_sh0 = 0, o_sh1 = 0, o_ds64 = 0, o_ds32 = 0, o_rghost = 0, o_rbuf = 0, o_cbcopy = 0,
-         o_prol = 0, o_pidx = 0, o_wtab = 0, o_pw = 0, o_cb = 0, o_status = 0, o_kbuf = 0, o_kbuf_somm = 0, o_rblocks = 0,
+         o_prol = 0, o_pidx = 0, o_wtab = 0, o_pw = 0, o_cb = 0, o_status = 0, o_kbuf = 0, o_kbuf_somm = 0, o_tmap = 0, o_rblocks = 0,
          o_rbcopy = 0, o_krow = 0, o_rb = 0, o_pbox = 0, o_pslots = 0,
          o_paxtab = 0, o_cfirst = 0, o_diag = 0, scratch_total = 0;
   // bound buffers
@@ -113,6 +118,7 @@ struct z4c_ctx {
   // kernel is built for)
   int sched[2] = {2, 2}, occ[2] = {1, 4};
   bool epi_tma = false;  // FP32 split schedules: the bulk-copy stage update where tiles allow
+  bool pre_tma = true;   // FP32 y/z pre-pass: the TMA-fed kernel where the group allows
   // graph of one RK4 step
   cudaGraphExec_t graph = nullptr;
   std::string err;
@@ -125,6 +131,8 @@ struct z4c_ctx {
   int32_t *d_status() const { return (int32_t *)(scratch + o_status); }
   float *d_kbuf() const { return (float *)(scratch + o_kbuf); }
   float *d_kbuf_somm() const { return (float *)(scratch + o_kbuf_somm); }
+  // tensor maps (128 bytes each) of FP32 shadow q for every block
+  const void *d_tmap(int q) const { return scratch + o_tmap + (size_t)q * 128 * dblocks.size(); }
   bool has_staged() const { return !grp[3].stiles.empty(); }
   bool has_wide() const {
     for (const z4c::Group &G : grp)

@@ -144,7 +144,21 @@ struct StageArgs {
   int32_t next_full;  // FP32 mode: 1 = write every field of next in FP64, 0 = chi only
   int32_t *status;    // device word; a kernel whose bounded wait gave up ORs in 1
   float *kbuf;        // schedule 4: the FP32 RHS per tile, [tile][field][TX * TY]
+  const void *tmap32; // FP32 y/z pre-pass fed by TMA: the tensor maps of x32, one per block (or null)
 };
+
+// fields with stored y/z first derivatives (their mixed second derivatives
+// are taken from them): chi, gt_ij, alpha, beta^i
+constexpr int NDS = 11;
+
+// Tiles of the FP32 y/z pre-pass fed by TMA: PRE_TMA_PX x PRE_TMA_PY columns
+// (one thread each) walking PRE_TMA_NZ planes; the tile's storage x is a
+// multiple of PRE_TMA_PX.
+constexpr int PRE_TMA_PX = 16;
+constexpr int PRE_TMA_PY = 8;
+constexpr int PRE_TMA_NZ = 16;
+constexpr int PRE_TMA_NQ = 4;   // fields per CTA: a column takes ceil(11 / NQ) = 3 CTAs (field groups)
+constexpr int PRE_TMA_LA = 2;   // planes in flight beyond the 2W + 1 of the stencil
 
 // Interior tile shape of the RHS kernels.
 constexpr int TX = 16;
@@ -230,6 +244,10 @@ cudaError_t launch_fused_pre_f32_occ4(int order, const StageArgs &a, const Tile 
 // pre-pass output, else the single-kernel schedule)
 cudaError_t launch_prepass_f64(int order, const StageArgs &a, const Tile *wtiles, int nwtiles, cudaStream_t st);
 cudaError_t launch_prepass_f32(int order, const StageArgs &a, const Tile *wtiles, int nwtiles, cudaStream_t st);
+// the same derivatives from the z-walking kernel fed by TMA tensor copies
+// (a.tmap32 set; orders with prepass_tma_built): bit-identical results
+bool prepass_tma_built(int order);
+cudaError_t launch_prepass_tma_f32(int order, const StageArgs &a, const Tile *ztiles, int n, cudaStream_t st);
 cudaError_t launch_fused_f64(int order, const StageArgs &a, const Tile *tiles, int ntiles, bool pre,
                              cudaStream_t st);
 cudaError_t launch_fused_f32(int order, const StageArgs &a, const Tile *tiles, int ntiles, bool pre,

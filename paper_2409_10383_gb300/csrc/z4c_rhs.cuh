@@ -449,7 +449,6 @@ struct Direct {
 __host__ __device__ constexpr int dslot(int f) {
   return f == CHI ? 0 : (f >= GXX && f <= GZZ) ? f - GXX + 1 : f == ALPHA ? 7 : (f >= BETAX) ? f - BETAX + 8 : -1;
 }
-constexpr int NDS = 11;
 
 template <int ORD, class R, class SRC, class DS>
 struct Pre {

@@ -28,7 +28,7 @@ EXPORTS = ("z4c_create", "z4c_create_batch", "z4c_set_initial_data_instance", "z
            "z4c_sync", "z4c_profile_steps", "z4c_set_variant", "z4c_autotune", "z4c_peak_fma", "z4c_constraints_static",
            "z4c_launches_per_step", "z4c_last_error", "z4c_destroy", "z4c_block_indicators",
            "z4c_track_punctures", "z4c_psi4", "z4c_peak_convert", "z4c_test_wait_timeout",
-           "z4c_set_epilogue", "z4c_tile_shape")
+           "z4c_set_epilogue", "z4c_tile_shape", "z4c_set_prepass", "z4c_prepass_tma_blocks")
 Z4C_MAX_PUNCTURES = 64
 
 
@@ -89,6 +89,8 @@ def lib():
             "z4c_sync": (I, [P]),
             "z4c_test_wait_timeout": (I, [P, I]),
             "z4c_set_epilogue": (I, [P, I]),
+            "z4c_set_prepass": (I, [P, I]),
+            "z4c_prepass_tma_blocks": (I, [P]),
             "z4c_tile_shape": (I, [P, I, P, P, P]),
             "z4c_profile_steps": (I, [P, D, I, P]),
             "z4c_set_variant": (I, [P, I, I]),
@@ -366,6 +368,18 @@ class Z4c:
     def z4c_set_epilogue(self, kind):
         """FP32-RHS split schedules: 1 bulk-copy stage-update kernel, 0 plain."""
         _check(lib().z4c_set_epilogue(self.ctx, int(kind)), self.ctx, "z4c_set_epilogue")
+
+    def z4c_set_prepass(self, kind):
+        """FP32-RHS y/z pre-pass: 1 the z-walking kernel fed by TMA where the
+        blocks allow it (default), 0 the plane-tiled kernel."""
+        _check(lib().z4c_set_prepass(self.ctx, int(kind)), self.ctx, "z4c_set_prepass")
+
+    def z4c_prepass_tma_blocks(self) -> int:
+        """Blocks whose y/z pre-pass runs the TMA-fed kernel."""
+        n = lib().z4c_prepass_tma_blocks(self.ctx)
+        if n < 0:
+            _check(n, self.ctx, "z4c_prepass_tma_blocks")
+        return n
 
     def z4c_autotune(self, reps=3):
         sch, occ = ctypes.c_int(), ctypes.c_int()

@@ -165,3 +165,31 @@ def test_tile_shape_reports_the_variant(L):
     c = ctx(64, 64)
     assert shape(c) == (16, 8, 1)
     L.z4c_destroy(c)
+
+
+def test_prepass_kind_and_qualifying_blocks(L):
+    """z4c_set_prepass / z4c_prepass_tma_blocks (no CUDA call): FP32-RHS
+    blocks of order 4 or 6 whose rows, fields and offsets are multiples of
+    4 floats take the TMA-fed pre-pass by default, kind 0 switches it off,
+    FP64 blocks and a 26-cell storage row never take it."""
+    def ctx(n, g, order, prec):
+        ok, c = z4c.z4c_create(_mesh(), [_block(n=n, h=1.0 / n)], g, order, _params(prec))
+        assert ok == 0, ok
+        return c
+
+    c = ctx(32, 4, 6, 32)  # storage 40^3
+    assert L.z4c_prepass_tma_blocks(c) == 1
+    assert L.z4c_set_prepass(c, 0) == 0 and L.z4c_prepass_tma_blocks(c) == 0
+    assert L.z4c_set_prepass(c, 1) == 0 and L.z4c_prepass_tma_blocks(c) == 1
+    assert L.z4c_set_prepass(c, 2) == z4c.Z4C_ERR_BAD_ARG
+    L.z4c_destroy(c)
+    c = ctx(26, 3, 4, 32)  # storage 32^3, order 4
+    assert L.z4c_prepass_tma_blocks(c) == 1
+    L.z4c_destroy(c)
+    c = ctx(20, 3, 4, 32)  # storage rows of 26 floats
+    assert L.z4c_prepass_tma_blocks(c) == 0
+    L.z4c_destroy(c)
+    c = ctx(32, 4, 6, 64)  # FP64
+    assert L.z4c_prepass_tma_blocks(c) == 0
+    L.z4c_destroy(c)
+    assert L.z4c_prepass_tma_blocks(None) == z4c.Z4C_ERR_BAD_ARG

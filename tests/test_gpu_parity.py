@@ -352,6 +352,40 @@ def test_fp32_wide_tile_and_pair_kernels(oracle, nb, n):
         assert np.all(d <= 1e-4 * c + 1e-14), (b, d, c)
 
 
+@pytest.mark.parametrize("kind,order,nb,n", [
+    ("puncture", 6, (2, 1, 1), 32),            # Sommerfeld faces, two blocks
+    ("puncture", 4, (2, 1, 1), (26, 22, 18)),  # order 4, ragged y tiles and z chunk
+    ("gauge_wave", 6, (1, 2, 1), (24, 12, 20)),  # periodic, ragged
+])
+def test_fp32_tma_prepass_bit_identical(oracle, kind, order, nb, n):
+    """The z-walking y/z pre-pass fed by TMA tensor copies evaluates the same
+    stencils on the same FP32 values as the plane-tiled one: the RHS and two
+    RK4 steps are bit-identical under both, on the 16 x 8 (schedule 4) and
+    the wide-tile (schedule 5) RHS kernels.  Every block of these meshes
+    qualifies (z4c_prepass_tma_blocks), so the TMA path is the one run."""
+    w = H.small_workload(kind, order, nb, n)
+    m = H.oracle_mesh(oracle, w)
+    u = m.initial_data(w["id_kind"], w["id_par"])
+    m.fill_ghosts(u)
+    H.perturb(m, u, 91, 1e-3)
+    dt = 0.25 * float(w["h"][0])
+    for sch in (4, 5):
+        rhs, steps = {}, {}
+        for pre in (0, 1):
+            g = H.gpu_ctx(w, precision=32, schedule=sch)
+            g.z4c_set_variant(sch, 4)
+            g.z4c_set_prepass(pre)
+            assert g.z4c_prepass_tma_blocks() == (m.nblocks if pre else 0)
+            g.z4c_set_state(u, reg=1)
+            rhs[pre] = g.z4c_rhs(1).cpu().numpy().copy()
+            g.z4c_set_state(u)
+            g.z4c_rk4_step(dt, 2)
+            steps[pre] = g.z4c_get_state()
+            g.close()
+        assert np.array_equal(rhs[1], rhs[0]), sch
+        assert np.array_equal(steps[1], steps[0]), sch
+
+
 def test_autotune_keeps_state_and_picks_a_built_variant(oracle):
     """The autotuner runs only stage 1 (U0 unchanged) and leaves a valid
     variant; evolution after tuning still matches the oracle."""
