@@ -256,6 +256,16 @@ int z4c_sync(z4c_ctx *ctx);
  * word is cleared.  Touches no register. */
 int z4c_test_wait_timeout(z4c_ctx *ctx, int rounds);
 
+/* Failure-detection test aid for the TMA-fed y/z pre-pass (z4c_set_prepass):
+ * run it once on U0's FP32 shadow with a wait limit of zero try_wait
+ * attempts, so that every CTA gives up at its first wait on copies it has
+ * issued, waits a bounded time for those copies to land, sets the status
+ * word and returns; then z4c_sync().  Returns Z4C_ERR_TIMEOUT with its
+ * z4c_last_error text, the status word cleared and the context usable; it
+ * writes only the pre-pass derivative arrays, which every stage recomputes.
+ * Z4C_ERR_UNSUPPORTED when no block runs that kernel. */
+int z4c_test_prepass_timeout(z4c_ctx *ctx);
+
 /* Measurement aid: run nsteps RK4 steps with plain (not graph) launches,
  * each bracketed by CUDA events on the context's stream, and return the
  * average milliseconds per step spent in each kernel kind (4 doubles):

@@ -471,6 +471,25 @@ int z4c_test_wait_timeout(z4c_ctx *ctx, int rounds) {
   return z4c_sync(ctx);
 }
 
+int z4c_test_prepass_timeout(z4c_ctx *ctx) {
+  int r = ensure_bound(ctx);
+  if (r) return r;
+  if (z4c_prepass_tma_blocks(ctx) <= 0)
+    return fail(ctx, Z4C_ERR_UNSUPPORTED, "no block runs the TMA-fed pre-pass in this context");
+  r = ensure_shadow(ctx);
+  if (r) return r;
+  // stage 1 reads U0's shadow; the pre-pass writes only its derivative arrays
+  const StageArgs base = stage_args(ctx, 0);
+  for (int g = 0; g < NGRP; ++g) {
+    const Group &G = ctx->grp[g];
+    if (G.empty() || !G.f32 || !G.tma_pre) continue;
+    StageArgs a = group_args(ctx, base, true);
+    a.tmap32 = ctx->d_tmap(0);
+    CK(launch_prepass_tma_f32(G.order, a, ctx->at<Tile>(G.o_ztiles), (int)G.ztiles.size(), ctx->stream, 0u));
+  }
+  return z4c_sync(ctx);
+}
+
 int z4c_profile_steps(z4c_ctx *ctx, double dt, int nsteps, double *ms) {
   int r = ensure_bound(ctx);
   if (r) return r;

@@ -247,7 +247,10 @@ cudaError_t launch_prepass_f32(int order, const StageArgs &a, const Tile *wtiles
 // the same derivatives from the z-walking kernel fed by TMA tensor copies
 // (a.tmap32 set; orders with prepass_tma_built): bit-identical results
 bool prepass_tma_built(int order);
-cudaError_t launch_prepass_tma_f32(int order, const StageArgs &a, const Tile *ztiles, int n, cudaStream_t st);
+// (rounds: try_wait attempts per bounded wait; 0 makes every CTA give up at
+// its first wait, drain its copies and report, as a failure-path test)
+cudaError_t launch_prepass_tma_f32(int order, const StageArgs &a, const Tile *ztiles, int n, cudaStream_t st,
+                                   uint32_t rounds = 1u << 22);
 cudaError_t launch_fused_f64(int order, const StageArgs &a, const Tile *tiles, int ntiles, bool pre,
                              cudaStream_t st);
 cudaError_t launch_fused_f32(int order, const StageArgs &a, const Tile *tiles, int ntiles, bool pre,

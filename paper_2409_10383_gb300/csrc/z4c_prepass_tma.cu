@@ -161,7 +161,7 @@ __global__ void __launch_bounds__(PRE_TMA_PX *PRE_TMA_PY)
 }
 
 template <int ORD>
-cudaError_t go(const StageArgs &a, const Tile *tiles, int n, cudaStream_t st) {
+cudaError_t go(const StageArgs &a, const Tile *tiles, int n, uint32_t rounds, cudaStream_t st) {
   constexpr size_t smem = PreGeom<ORD>::SMEM;
   static bool attr_set = false;  // per process; the attribute is per function
   if (!attr_set) {
@@ -170,7 +170,7 @@ cudaError_t go(const StageArgs &a, const Tile *tiles, int n, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  dydz_tma_kernel<ORD><<<n, dim3(PRE_TMA_PX, PRE_TMA_PY), smem, st>>>(a, tiles, 1u << 22);
+  dydz_tma_kernel<ORD><<<n, dim3(PRE_TMA_PX, PRE_TMA_PY), smem, st>>>(a, tiles, rounds);
   return cudaGetLastError();
 }
 
@@ -178,10 +178,11 @@ cudaError_t go(const StageArgs &a, const Tile *tiles, int n, cudaStream_t st) {
 
 bool prepass_tma_built(int order) { return order == 4 || order == 6; }
 
-cudaError_t launch_prepass_tma_f32(int order, const StageArgs &a, const Tile *ztiles, int n, cudaStream_t st) {
+cudaError_t launch_prepass_tma_f32(int order, const StageArgs &a, const Tile *ztiles, int n, cudaStream_t st,
+                                   uint32_t rounds) {
   if (n <= 0) return cudaSuccess;
-  if (order == 6) return go<6>(a, ztiles, n, st);
-  if (order == 4) return go<4>(a, ztiles, n, st);
+  if (order == 6) return go<6>(a, ztiles, n, rounds, st);
+  if (order == 4) return go<4>(a, ztiles, n, rounds, st);
   return cudaErrorInvalidValue;
 }
 

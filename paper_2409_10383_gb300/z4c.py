@@ -28,7 +28,8 @@ EXPORTS = ("z4c_create", "z4c_create_batch", "z4c_set_initial_data_instance", "z
            "z4c_sync", "z4c_profile_steps", "z4c_set_variant", "z4c_autotune", "z4c_peak_fma", "z4c_constraints_static",
            "z4c_launches_per_step", "z4c_last_error", "z4c_destroy", "z4c_block_indicators",
            "z4c_track_punctures", "z4c_psi4", "z4c_peak_convert", "z4c_test_wait_timeout",
-           "z4c_set_epilogue", "z4c_tile_shape", "z4c_set_prepass", "z4c_prepass_tma_blocks")
+           "z4c_set_epilogue", "z4c_tile_shape", "z4c_set_prepass", "z4c_prepass_tma_blocks",
+           "z4c_test_prepass_timeout")
 Z4C_MAX_PUNCTURES = 64
 
 
@@ -91,6 +92,7 @@ def lib():
             "z4c_set_epilogue": (I, [P, I]),
             "z4c_set_prepass": (I, [P, I]),
             "z4c_prepass_tma_blocks": (I, [P]),
+            "z4c_test_prepass_timeout": (I, [P]),
             "z4c_tile_shape": (I, [P, I, P, P, P]),
             "z4c_profile_steps": (I, [P, D, I, P]),
             "z4c_set_variant": (I, [P, I, I]),
@@ -313,6 +315,13 @@ class Z4c:
         """Failure-detection aid: a kernel whose bounded mbarrier wait runs
         out.  Returns (status, z4c_last_error text)."""
         rc = lib().z4c_test_wait_timeout(self.ctx, int(rounds))
+        return rc, lib().z4c_last_error(self.ctx).decode()
+
+    def z4c_test_prepass_timeout(self):
+        """Failure-detection aid: the TMA-fed pre-pass with a zero wait
+        limit.  Returns (status, z4c_last_error text)."""
+        self._enter()
+        rc = lib().z4c_test_prepass_timeout(self.ctx)
         return rc, lib().z4c_last_error(self.ctx).decode()
 
     def z4c_block_indicators(self, reg=REG_U0):

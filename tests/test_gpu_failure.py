@@ -6,6 +6,11 @@
   kernel sets the status word and returns, and the host reports
   Z4C_ERR_TIMEOUT with its text.  The context stays usable: an RK4 step
   afterwards still matches the oracle.
+- The same for the y/z pre-pass fed by TMA: z4c_test_prepass_timeout runs
+  it with a zero wait limit, so every CTA gives up at its first wait on
+  copies it has issued, waits a bounded time for them to land, sets the
+  status word and returns; Z4C_ERR_TIMEOUT is reported and RK4 steps
+  afterwards are bit-identical to those of a fresh context.
 - A NaN planted on the host (z4c_set_state) in one interior cell: the
   constraint norms come out NaN and both constraint calls, the context's
   and the allocation-free one, return Z4C_ERR_NAN; evolving through it
@@ -41,6 +46,32 @@ def test_bounded_wait_times_out_and_context_survives(oracle):
     rc, _ = g.z4c_test_wait_timeout(0)
     assert rc == z4c.Z4C_ERR_BAD_ARG
     g.close()
+
+
+def test_tma_prepass_wait_gives_up_and_context_survives():
+    from paper_2409_10383_gb300 import z4c
+    w = H.small_workload("puncture", 6, (2, 1, 1), 32)
+    dt = 0.25 * float(w["h"][0])
+    ref = H.gpu_ctx(w, precision=32)
+    ref.z4c_set_initial_data(w["id_kind"], w["id_par"])
+    ref.z4c_rk4_step(dt, 2)
+    want = ref.z4c_get_state()
+    ref.close()
+    g = H.gpu_ctx(w, precision=32)
+    assert g.z4c_prepass_tma_blocks() == 2
+    g.z4c_set_initial_data(w["id_kind"], w["id_par"])
+    rc, msg = g.z4c_test_prepass_timeout()
+    assert rc == z4c.Z4C_ERR_TIMEOUT, (rc, msg)
+    assert "gave up" in msg, msg
+    g.z4c_sync()  # reported once: the status word is cleared
+    g.z4c_rk4_step(dt, 2)
+    assert np.array_equal(g.z4c_get_state(), want)
+    g.close()
+    # no block on that kernel: refused before any launch
+    f = H.gpu_ctx(w, precision=64)
+    rc, _ = f.z4c_test_prepass_timeout()
+    assert rc == z4c.Z4C_ERR_UNSUPPORTED
+    f.close()
 
 
 @pytest.mark.parametrize("precision", [64, 32])
