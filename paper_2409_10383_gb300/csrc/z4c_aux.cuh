@@ -90,12 +90,12 @@ __device__ __forceinline__ void somm_rhs(const StageArgs &a, const CellRef &c, c
   const R mir = -ir;
 #pragma unroll
   for (int f = 0; f < NF; ++f) {
-    // the FP32 shadow stores the gt diagonal minus one, i.e. u - u_inf there
+    // the FP32 shadow stores u - u_inf for every field (shadow_shifted)
     const R *p;
     R um;
     if constexpr (F32) {
       p = a.x32 + off + (int64_t)f * b.S;
-      um = (f == CHI || f == ALPHA) ? p[0] - R(1) : p[0];
+      um = p[0];
     } else {
       p = a.x64 + off + (int64_t)f * b.S;
       um = p[0] - uinf_of(f);
@@ -244,7 +244,7 @@ __global__ void initial_data_kernel(double *__restrict__ u0, const DevBlock *__r
 }
 
 
-// FP64 register -> FP32 shadow (diagonal of gt stored minus one)
+// FP64 register -> FP32 shadow (the shadow_shifted fields stored minus one)
 __global__ void to_shadow_kernel(const double *__restrict__ src, float *__restrict__ dst,
                                  const DevBlock *__restrict__ blocks) {
   const DevBlock &b = blocks[blockIdx.y];
@@ -254,7 +254,7 @@ __global__ void to_shadow_kernel(const double *__restrict__ src, float *__restri
     for (int f = 0; f < NF; ++f) {
       const int64_t o = b.off + (int64_t)f * b.S + c;
       const double v = src[o];
-      dst[o] = __double2float_rn((f == GXX || f == GYY || f == GZZ) ? v - 1.0 : v);
+      dst[o] = __double2float_rn(shadow_shifted(f) ? v - 1.0 : v);
     }
   }
 }

@@ -147,6 +147,13 @@ struct StageArgs {
   const void *tmap32; // FP32 y/z pre-pass fed by TMA: the tensor maps of x32, one per block (or null)
 };
 
+// Fields whose FP32 shadow holds the value minus one (their value at
+// infinity and in flat space: chi, the gt diagonal, alpha), so that FP32
+// keeps the relative precision of their deviation from 1.
+__host__ __device__ constexpr bool shadow_shifted(int f) {
+  return f == CHI || f == GXX || f == GYY || f == GZZ || f == ALPHA;
+}
+
 // fields with stored y/z first derivatives (their mixed second derivatives
 // are taken from them): chi, gt_ij, alpha, beta^i
 constexpr int NDS = 11;

@@ -25,8 +25,8 @@ __device__ __forceinline__ R ldg_(const R *p) {
 }
 
 // Stencil source: field f of the centre cell is at base[f * S].  Offsets
-// are in elements.  For the FP32 shadow the diagonal of gt is stored minus
-// one, so centre values add it back.
+// are in elements.  The FP32 shadow stores chi, the gt diagonal and alpha
+// minus one (shadow_shifted), so centre values add it back.
 template <class R, bool SHIFTED_DIAG>
 struct Src {
   const R *__restrict__ base;  // field 0 of the block (the same for the whole CTA)
@@ -35,7 +35,7 @@ struct Src {
   __device__ __forceinline__ R at(int f, int off) const { return ldg_(base + (c + (f * S + off))); }
   __device__ __forceinline__ R val(int f) const {
     R v = at(f, 0);
-    if (SHIFTED_DIAG && (f == GXX || f == GYY || f == GZZ)) v += R(1);
+    if (SHIFTED_DIAG && shadow_shifted(f)) v += R(1);
     return v;
   }
 };
@@ -342,7 +342,8 @@ struct is_pair<F2> : std::true_type {};
 // an FP32 array whose row starts are 8-byte aligned (every storage extent
 // and block offset even).  An even offset is one aligned 8-byte load; an odd
 // offset takes the upper half of the pair below and the lower half of the
-// pair above.  SHIFTED: the FP32 shadow's gt diagonal is stored minus one.
+// pair above.  SHIFTED: the FP32 shadow's shadow_shifted fields are stored
+// minus one.
 template <bool SHIFTED>
 struct SrcPair {
   const float *__restrict__ base;
@@ -357,7 +358,7 @@ struct SrcPair {
   }
   __device__ __forceinline__ F2 val(int f) const {
     F2 v = at(f, 0);
-    if (SHIFTED && (f == GXX || f == GYY || f == GZZ)) v += F2(1.0f);
+    if (SHIFTED && shadow_shifted(f)) v += F2(1.0f);
     return v;
   }
 };
@@ -1166,7 +1167,8 @@ struct GlobalField {
 // RK4 stage update of one cell and enforcement, then the stores.  FP64 mode:
 // FP64 fused multiply-adds of the FP64 RHS.  FP32 mode: the increment c k of
 // the FP32 RHS is formed in FP32 and added to the FP64 state / accumulator
-// in FP64; the next stage also goes to the FP32 shadow (gt diagonal minus 1).
+// in FP64; the next stage also goes to the FP32 shadow (the shadow_shifted
+// fields minus 1).
 // u0f / accf give field f of u0 and of the accumulator: GlobalField (read
 // where used), ArrayField (loaded beforehand, below) or a staged copy.
 template <class R, class U0F, class ACCF>
@@ -1225,7 +1227,7 @@ __device__ __forceinline__ void stage_epilogue_from(const StageArgs &a, int32_t 
     }
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
-      const double w = (f == GXX || f == GYY || f == GZZ) ? v[f] - 1.0 : v[f];
+      const double w = shadow_shifted(f) ? v[f] - 1.0 : v[f];
       a.next32[off + (int64_t)f * S] = d2f_int(w);
     }
   }

@@ -40,7 +40,7 @@ __host__ __device__ constexpr int d1idx(int f) {
        : (f >= GAMX && f <= GAMZ) ? 7 + (f - GAMX)
        : (f >= GXX && f <= GZZ) ? 10 + (f - GXX) : -1;
 }
-constexpr int SL_VAL = 0;            // 22 centre values (gt diagonal with the 1 added back)
+constexpr int SL_VAL = 0;            // 22 centre values (the shadow's minus one added back)
 constexpr int SL_D1 = 22;            // 16 fields x 3 directions
 constexpr int SL_D2 = 70;            // 11 fields (dslot) x 3 directions
 constexpr int SL_MIX = 103;          // 11 fields x (xy, xz, yz)
@@ -133,8 +133,8 @@ __device__ __forceinline__ void stage_field(const float *__restrict__ box, float
       x[2][m + KW] = box[qz + zi * TY * RW];
     }
   }
-  // centre value (the FP32 shadow stores the gt diagonal minus one)
-  ds[(SL_VAL + F) * STAGE_NT + tid] = (F == GXX || F == GYY || F == GZZ) ? c + 1.f : c;
+  // centre value (the FP32 shadow stores the shadow_shifted fields minus one)
+  ds[(SL_VAL + F) * STAGE_NT + tid] = shadow_shifted(F) ? c + 1.f : c;
   // first derivatives
   constexpr int I1 = d1idx(F);
   constexpr int Q = dslot(F);

@@ -34,10 +34,12 @@ def _gpu():
 
 
 def _round_like_shadow(m, u):
+    """The FP64 state rounded as the FP32 shadow stores it (chi, the gt
+    diagonal and alpha minus one), back in FP64."""
     v = u.copy()
     for blk in m.blocks(v):
         for f in range(22):
-            off = 1.0 if f in (1, 4, 6) else 0.0
+            off = 1.0 if f in (0, 1, 4, 6, 18) else 0.0
             blk[f] = (blk[f] - off).astype(np.float32).astype(np.float64) + off
     return v
 
