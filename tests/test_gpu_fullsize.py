@@ -33,13 +33,14 @@ def _gpu():
         pytest.skip("no GPU")
 
 
-def _round_like_shadow(m, u):
-    """The FP64 state rounded as the FP32 shadow stores it (chi, the gt
-    diagonal and alpha minus one), back in FP64."""
+def _round_like_shadow(m, u, shifted=(0, 1, 4, 6, 18)):
+    """The FP64 state rounded to FP32 with the fields in `shifted` stored
+    minus one (the FP32 shadow: chi, the gt diagonal and alpha), back in
+    FP64."""
     v = u.copy()
     for blk in m.blocks(v):
         for f in range(22):
-            off = 1.0 if f in (0, 1, 4, 6, 18) else 0.0
+            off = 1.0 if f in shifted else 0.0
             blk[f] = (blk[f] - off).astype(np.float32).astype(np.float64) + off
     return v
 
@@ -78,7 +79,13 @@ def _errors(m, u, got_flat, precision, cells):
             v = u * (1.0 + 2.0 ** -52 * np.random.default_rng(seed).uniform(-1.0, 1.0, u.shape))
             floor = np.maximum(floor, np.abs(m.rhs_cells(v, cells) - ref).max(axis=0) / D)
     else:
-        floor = np.abs(m.rhs_cells(_round_like_shadow(m, u), cells) - ref).max(axis=0) / D
+        # the shadow's rounding, and the rounding of chi and alpha at their
+        # own magnitude: the FP32 algebra multiplies by chi and alpha (1/chi,
+        # alpha R_ij, chi X^TF), whose products round there
+        floor = np.zeros_like(err)
+        for shifted in ((0, 1, 4, 6, 18), (1, 4, 6)):
+            v = _round_like_shadow(m, u, shifted)
+            floor = np.maximum(floor, np.abs(m.rhs_cells(v, cells) - ref).max(axis=0) / D)
     return err, 8 * floor + 1e-12
 
 
