@@ -237,7 +237,7 @@ def measure(z4c, torch, workload, prec, args, ws, local):
     # --no-autotune keeps the built-in default (FP64 schedule 2; FP32 split
     # schedule 4), e.g. for a profiler run whose serialised timings would
     # mislead the tuner
-    variant = ((2, 1) if prec == 64 else (args.fp32_schedule, 4)) if args.no_autotune else g.z4c_autotune(3)
+    variant = ((2, 1) if prec == 64 else (args.fp32_schedule, 4)) if args.no_autotune else g.z4c_autotune(8)
     if args.no_autotune:
         g.z4c_set_variant(*variant)
         if prec == 32:

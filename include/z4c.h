@@ -320,7 +320,9 @@ int z4c_prepass_tma_blocks(const z4c_ctx *ctx);
  * stage-update kernel (z4c_set_epilogue).
  * Each candidate runs reps + 1 times the ghost fill and stage 1 of RK4 (which
  * reads U0 and overwrites only the accumulator and stage A, so U0 keeps its
- * value); the fastest is kept, FP64 and FP32-RHS kernels tuned separately.
+ * value), with the Sommerfeld cells on a second stream beside the interior
+ * kernels as in the captured step; the fastest is kept, FP64 and FP32-RHS
+ * kernels tuned separately.
  * Reported (either pointer may be NULL): the FP32-RHS choice if the context
  * has FP32-RHS blocks, else the FP64 one.
  * Synchronous.  Call before z4c_rk4_step, or it re-captures its graph. */

@@ -78,6 +78,15 @@ int status_check(z4c_ctx *ctx) {
               "a bounded wait on bulk copies (mbarrier) gave up in a kernel; results of that launch are invalid");
 }
 
+// The side stream and events of the Sommerfeld branch (created once).
+int ensure_side(z4c_ctx *ctx) {
+  if (!ctx->fork_somm || ctx->side) return Z4C_OK;
+  CK(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
+  return Z4C_OK;
+}
+
 StageArgs group_args(const z4c_ctx *ctx, StageArgs a, bool f32) {
   if (!f32) {
     a.x32 = nullptr;
@@ -364,11 +373,8 @@ int z4c_rk4_step_batch(z4c_ctx *ctx, const double *dt_per_instance, int nsteps) 
   }
   if (!ctx->graph) {  // the step reads dt from the device table: one graph serves every dt
     cudaGraph_t g = nullptr;
-    if (ctx->fork_somm && !ctx->side) {  // before the capture begins
-      CK(cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking));
-      CK(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
-      CK(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
-    }
+    r = ensure_side(ctx);  // before the capture begins
+    if (r) return r;
     CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
     r = enqueue_step(ctx, ctx->fork_somm);
     cudaError_t e = cudaStreamEndCapture(ctx->stream, &g);
@@ -609,8 +615,12 @@ int z4c_autotune(z4c_ctx *ctx, int reps, int *schedule_out, int *occupancy_out) 
   if (r) return r;
   r = upload_dt(ctx);
   if (r) return r;
-  // stage 1 reads U0 (and its FP32 shadow) and writes ACC and stage A only
+  // stage 1 reads U0 (and its FP32 shadow) and writes ACC and stage A only;
+  // timed as the captured step runs it, the Sommerfeld cells on the side
+  // stream beside the interior kernels
   StageArgs a = stage_args(ctx, 0);
+  r = ensure_side(ctx);
+  if (r) return r;
   cudaEvent_t e0, e1;
   CK(cudaEventCreate(&e0));
   CK(cudaEventCreate(&e1));
@@ -648,7 +658,7 @@ int z4c_autotune(z4c_ctx *ctx, int reps, int *schedule_out, int *occupancy_out) 
         if (rep == 1) CK(cudaEventRecord(e0, ctx->stream));
         r = fill_ghosts(ctx, ctx->reg[0], ctx->has[1] ? ctx->d_sh(0) : nullptr);
         if (r) return r;
-        r = launch_stage(ctx, a);
+        r = launch_stage(ctx, a, ctx->fork_somm);
         if (r) return r;
       }
       CK(cudaEventRecord(e1, ctx->stream));
