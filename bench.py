@@ -61,11 +61,11 @@ FP64_DRAM_BYTES_PER_CELL = {6: (121649920 + 97539328) / 262144, 2: (114212608 + 
 FP32_OPS_PER_CELL_STAGE = {6: dict(fadd=1085, ffma=1274, fmul=507)}
 FP32_F64_RESIDUE_PER_CELL_STAGE = {6: dict(dadd=47, dfma=22, dmul=25)}
 # keyed by (order, schedule, tile): the RHS kernel as it stands (with its L2
-# prefetch of the rows 4 planes ahead) + split_epilogue_kernel on the same
-# tiles, one 64^3 block, RK stage 2 (which reads both u0 and the
-# accumulator).  Schedules 4 and 6 changed after their last capture, so
-# they report no traffic.
-FP32_DRAM_BYTES_PER_CELL = {(6, 5, "64x2"): (65959680 + 4796672 + 126971904 + 28759040) / 262144}
+# prefetch of the rows 4 planes ahead, chi / gt diagonal / alpha stored
+# minus one) + split_epilogue_kernel on the same tiles, one 64^3 block, RK
+# stage 2 (which reads both u0 and the accumulator).  Schedules 4 and 6
+# changed after their last capture, so they report no traffic.
+FP32_DRAM_BYTES_PER_CELL = {(6, 5, "64x2"): (65961472 + 2135552 + 126968064 + 25498880) / 262144}
 # algorithmic HBM bytes per zone-cycle (fused 3-register RK4, 22 FP64 fields;
 # the same for the FP32-RHS path, whose state stays FP64)
 ALG_BYTES_PER_ZONE_CYCLE = 352 * 8
