@@ -181,7 +181,9 @@ int z4c_scratch_bytes(const z4c_ctx *ctx, size_t *bytes);
  * passed as void*; a non-default stream enables CUDA-graph replay in
  * z4c_rk4_step).  u0, stage_a, stage_b, acc: z4c_state_bytes() each, 256-byte
  * aligned.  scratch: z4c_scratch_bytes(), 256-byte aligned.  Uploads the
- * descriptor tables into scratch (asynchronously on the stream). */
+ * descriptor tables into scratch, with the TMA tensor maps of the FP32
+ * shadows that the y/z pre-pass of qualifying blocks reads through (encoded
+ * here, as they hold the buffers' addresses), and waits for the copies. */
 int z4c_bind(z4c_ctx *ctx, void *u0, void *stage_a, void *stage_b, void *acc, void *scratch,
              void *cuda_stream);
 
