@@ -368,6 +368,8 @@ def measure(z4c, torch, workload, prec, args, ws, local):
     tx, ty, cpt = g.z4c_tile_shape(0)
     roof["variant"] = {"schedule": variant[0], "occupancy": variant[1],
                        "tile": f"{tx}x{ty}", "cells_per_thread": cpt}
+    if prec == 32:  # which y/z pre-pass the kept variant runs
+        roof["variant"]["prepass"] = "tma" if g.z4c_prepass_tma_blocks() > 0 else "plane"
     # the Weyl scalar Psi4 on the grid (Sec. 3.3 diagnostic, FP64): one
     # synchronous call = ghost fill + Psi4 at every interior cell
     psi4 = None

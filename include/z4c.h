@@ -318,8 +318,9 @@ int z4c_prepass_tma_blocks(const z4c_ctx *ctx);
  * schedule (1 or 2; for FP32-RHS blocks also 4, and 3, 5 and 6 where
  * blocks qualify; see z4c_params)
  * and, for the FP32-RHS fused kernel, the number of resident CTAs per SM its
- * registers are budgeted for (1, 2, 4), and for the split schedules the
- * stage-update kernel (z4c_set_epilogue).
+ * registers are budgeted for (1, 2, 4), for the split schedules the
+ * stage-update kernel (z4c_set_epilogue), and the y/z pre-pass kind
+ * (z4c_set_prepass) where blocks qualify for the TMA-fed one.
  * Each candidate runs reps + 1 times the ghost fill and stage 1 of RK4 (which
  * reads U0 and overwrites only the accumulator and stage A, so U0 keeps its
  * value), with the Sommerfeld cells on a second stream beside the interior

@@ -626,8 +626,11 @@ int z4c_autotune(z4c_ctx *ctx, int reps, int *schedule_out, int *occupancy_out) 
   CK(cudaEventCreate(&e1));
   struct Cand {
     int sched, occ;
-    bool tma = true;
+    bool tma = true;   // the bulk-copy stage update (split schedules)
+    bool pre = true;   // the y/z pre-pass fed by TMA (where blocks qualify)
   };
+  bool any_tma_pre = false;
+  for (const Group &G : ctx->grp) any_tma_pre = any_tma_pre || (G.f32 && G.tma_pre);
   for (int p = 0; p < 2; ++p) {  // tune each precision with the other fixed
     if (!ctx->has[p]) continue;
     std::vector<Cand> cands = {{1, 1}, {2, 1}};
@@ -645,14 +648,25 @@ int z4c_autotune(z4c_ctx *ctx, int reps, int *schedule_out, int *occupancy_out) 
         cands.push_back({6, 4, false});
         cands.push_back({6, 4, true});
       }
+      // every candidate with a pre-pass, also with the plane-tiled one
+      if (any_tma_pre) {
+        const size_t n = cands.size();
+        for (size_t q = 0; q < n; ++q)
+          if (cands[q].sched >= 2) {
+            Cand c = cands[q];
+            c.pre = false;
+            cands.push_back(c);
+          }
+      }
     }
     float best = 1e30f;
-    Cand pick = {ctx->sched[p], p == 1 ? ctx->occ[1] : 1, ctx->epi_tma};
+    Cand pick = {ctx->sched[p], p == 1 ? ctx->occ[1] : 1, ctx->epi_tma, ctx->pre_tma};
     for (const Cand &c : cands) {
       ctx->sched[p] = c.sched;
       if (p == 1) {
         ctx->occ[1] = c.occ;
         ctx->epi_tma = c.tma;
+        ctx->pre_tma = c.pre;
       }
       for (int rep = 0; rep <= reps; ++rep) {  // first pass untimed
         if (rep == 1) CK(cudaEventRecord(e0, ctx->stream));
@@ -674,6 +688,7 @@ int z4c_autotune(z4c_ctx *ctx, int reps, int *schedule_out, int *occupancy_out) 
     if (p == 1) {
       ctx->occ[1] = pick.occ;
       ctx->epi_tma = pick.tma;
+      ctx->pre_tma = pick.pre;
     }
   }
   cudaEventDestroy(e0);
