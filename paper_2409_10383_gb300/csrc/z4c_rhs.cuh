@@ -741,23 +741,52 @@ __device__ __forceinline__ void rhs_point(const SRC &s, const DV &dv, const int 
   k[THETA] = R(0.5) * al * (Rs - AA + two3 * K * K) - al * p.kappa1 * (R(2) + p.kappa2) * Theta;
 
   {
-    // d_j d_k beta^i, and d_j (d_k beta^k)
+    // d_j d_k beta^i, and d_j (d_k beta^k).  Scalar types: the second
+    // derivatives are taken unscaled, the stencil scales (and the factor 2
+    // of the off-diagonal pairs) folded into gt^jk once per cell, as for
+    // the Ricci tensor; cell pairs keep the scaled form.
+    constexpr bool foldb = !is_pair<R>::value;
     R ddb[3][6];
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      ddb[i][0] = dv.d2(BETAX + i, 0);
-      ddb[i][3] = dv.d2(BETAX + i, 1);
-      ddb[i][5] = dv.d2(BETAX + i, 2);
-      ddb[i][1] = dv.mix(BETAX + i, 0, 1);
-      ddb[i][2] = dv.mix(BETAX + i, 0, 2);
-      ddb[i][4] = dv.mix(BETAX + i, 1, 2);
+      if constexpr (foldb) {
+        ddb[i][0] = dv.d2raw(BETAX + i, 0);
+        ddb[i][3] = dv.d2raw(BETAX + i, 1);
+        ddb[i][5] = dv.d2raw(BETAX + i, 2);
+        ddb[i][1] = dv.mixraw(BETAX + i, 0, 1);
+        ddb[i][2] = dv.mixraw(BETAX + i, 0, 2);
+        ddb[i][4] = dv.mixraw(BETAX + i, 1, 2);
+      } else {
+        ddb[i][0] = dv.d2(BETAX + i, 0);
+        ddb[i][3] = dv.d2(BETAX + i, 1);
+        ddb[i][5] = dv.d2(BETAX + i, 2);
+        ddb[i][1] = dv.mix(BETAX + i, 0, 1);
+        ddb[i][2] = dv.mix(BETAX + i, 0, 2);
+        ddb[i][4] = dv.mix(BETAX + i, 1, 2);
+      }
     }
     R ddivb[3];
+    R gw[6];
+    if constexpr (foldb) {
+      const R s2 = dv.d2scale(), sm = dv.mixscale(), sm2 = sm + sm;
+      gw[0] = s2 * gi[0]; gw[1] = sm2 * gi[1]; gw[2] = sm2 * gi[2];
+      gw[3] = s2 * gi[3]; gw[4] = sm2 * gi[4]; gw[5] = s2 * gi[5];
+      ddivb[0] = fma(s2, ddb[0][0], sm * (ddb[1][1] + ddb[2][2]));
+      ddivb[1] = fma(s2, ddb[1][3], sm * (ddb[0][1] + ddb[2][4]));
+      ddivb[2] = fma(s2, ddb[2][5], sm * (ddb[0][2] + ddb[1][4]));
+    } else {
 #pragma unroll
-    for (int j = 0; j < 3; ++j) ddivb[j] = ddb[0][S6(j, 0)] + ddb[1][S6(j, 1)] + ddb[2][S6(j, 2)];
+      for (int j = 0; j < 3; ++j) ddivb[j] = ddb[0][S6(j, 0)] + ddb[1][S6(j, 1)] + ddb[2][S6(j, 2)];
+    }
 #pragma unroll
     for (int i = 0; i < 3; ++i) {
-      R t = trsym(ddb[i]) + two3 * Gd[i] * divb;
+      R t;
+      if constexpr (foldb)
+        t = gw[0] * ddb[i][0] + gw[3] * ddb[i][3] + gw[5] * ddb[i][5] + gw[1] * ddb[i][1] + gw[2] * ddb[i][2] +
+            gw[4] * ddb[i][4];
+      else
+        t = trsym(ddb[i]);
+      t += two3 * Gd[i] * divb;
       t -= Gd[0] * dbeta[0][i] + Gd[1] * dbeta[1][i] + Gd[2] * dbeta[2][i];
       R u = R(0), w = R(0), v = R(0), z = R(0);
 #pragma unroll
