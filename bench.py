@@ -44,9 +44,9 @@ L2_BYTES = 129 * 2 ** 20
 # (dadd, dfma, dmul; exact integers per cell) of a one-block 64^3 order-6
 # capture, stage-1 launch:
 # flops = dadd + dmul + 2 dfma.
-FP64_OPS_PER_CELL_STAGE = {6: dict(dadd=539, dfma=1385, dmul=482),
+FP64_OPS_PER_CELL_STAGE = {6: dict(dadd=537, dfma=1389, dmul=469),
                            # 2nd order, 2 ghosts: interior_pre_kernel<2,false,1,false,68>
-                           2: dict(dadd=355, dfma=925, dmul=468)}
+                           2: dict(dadd=353, dfma=928, dmul=456)}
 # The same method as the oracle writes it out (oracle/flopcount.py: the
 # oracle's RK4 step on a counting scalar type, per interior cell and stage):
 # 49-point mixed stencils, separate KO and advection, full index loops.
@@ -54,7 +54,7 @@ FP64_OPS_PER_CELL_STAGE = {6: dict(dadd=539, dfma=1385, dmul=482),
 # kernel time would read several times the FP64 peak.
 ORACLE_FLOPS_PER_CELL_STAGE = {6: 21266.0, 4: 14184.6, 2: 9146.7}
 # DRAM bytes (read + write) per interior cell of that launch
-FP64_DRAM_BYTES_PER_CELL = {6: (121649920 + 97539328) / 262144, 2: (114212608 + 64284928) / 262144}
+FP64_DRAM_BYTES_PER_CELL = {6: (121358336 + 91584512) / 262144, 2: (114248960 + 64636672) / 262144}
 # FP32-RHS split schedule (interior_pre_kernel<6,true,4,split,72> storing k
 # + split_epilogue_kernel): executed FP32 operations and the FP64 residue per
 # interior cell per stage, from the same kind of capture
