@@ -99,6 +99,15 @@ def test_sizes_and_unbound_calls(L):
     # kernel + stage-update kernel per stage
     assert L.z4c_launches_per_step(ctx) == 16
     L.z4c_destroy(ctx)
+    # a single block with the Sommerfeld boundary on every face: no ghost
+    # copies; pre-pass + RHS + stage update, and the FP32 Sommerfeld cells'
+    # RHS and stage-update kernels, per stage (FP64 cells: one kernel)
+    rc, ctx = z4c.z4c_create(_mesh(per=0), [_block()], 3, 4, _params(32))
+    assert rc == 0 and L.z4c_launches_per_step(ctx) == 4 * 5
+    L.z4c_destroy(ctx)
+    rc, ctx = z4c.z4c_create(_mesh(per=0), [_block()], 3, 4, _params(64))
+    assert rc == 0 and L.z4c_launches_per_step(ctx) == 4 * (1 + 1 + 1)  # pre-pass, fused, Sommerfeld
+    L.z4c_destroy(ctx)
     rc, ctx = z4c.z4c_create(_mesh(), [_block()], 3, 4, _params(64, schedule=1))
     assert rc == 0 and L.z4c_launches_per_step(ctx) == 8  # single fused kernel
     L.z4c_destroy(ctx)
